@@ -1,0 +1,227 @@
+"""Seeded synthetic disparity scenes: the input generator shared by the tests, the oracle runs and bench.py.
+
+This module only makes inputs.  It holds none of the occlusion method's arithmetic: it draws piecewise-planar
+disparity maps (a sloped background plane plus slanted rectangles and ellipses painted far-to-near, Gaussian
+noise, optional salt outliers) that stand in for the paper's workloads (SceneFlow, the synthetic hyperspectral
+database and the real CAMSI recording of Section 4, none of which are available here).
+
+Randomness is counter-based: every draw is splitmix64(seed + counter * golden_gamma), so a scene depends only on
+(config id, frame id) and on nothing else (no global RNG state, no library RNG whose stream could change between
+numpy versions).  Gaussians use the Box-Muller transform in float64; the map is rounded to float32 once, at the end.
+The float64 log/cos of different libms can differ in the last bit, so the same seed may give maps that differ in a
+few low-order bits between machines; every parity check generates its input on the machine it runs on.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser (Steele, Lea, Flood 2014) on a uint64 array; wraps modulo 2**64."""
+    z = (z ^ (z >> np.uint64(30))) * _MIX1
+    z = (z ^ (z >> np.uint64(27))) * _MIX2
+    return z ^ (z >> np.uint64(31))
+
+
+def seed_of(config_id: int, frame: int) -> int:
+    """Stream seed for (config id, frame id)."""
+    x = np.array([(int(config_id) << 32) | (int(frame) & 0xFFFFFFFF)], dtype=np.uint64)
+    return int(_mix(x + _GOLDEN)[0])
+
+
+class CounterRng:
+    """splitmix64 in counter mode: draw i of stream `key` is mix(seed ^ key*C + (i+1)*golden)."""
+
+    def __init__(self, seed: int, key: int = 0):
+        base = np.array([seed], dtype=np.uint64) ^ (np.array([key], dtype=np.uint64) * _MIX2)
+        self._base = base
+        self._next = 0
+
+    def bits(self, n: int, offset: int | None = None) -> np.ndarray:
+        start = self._next if offset is None else offset
+        idx = np.arange(start + 1, start + 1 + n, dtype=np.uint64)
+        if offset is None:
+            self._next += n
+        return _mix(self._base + idx * _GOLDEN)
+
+    def uniform(self, n: int, offset: int | None = None) -> np.ndarray:
+        """n float64 uniforms in (0, 1)."""
+        b = self.bits(n, offset)
+        return ((b >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+    def normal(self, n: int, offset: int | None = None) -> np.ndarray:
+        """n standard normals by Box-Muller (one pair of uniforms per draw, cosine branch)."""
+        start = self._next if offset is None else offset
+        u = self.uniform(2 * n, offset=2 * start)
+        if offset is None:
+            self._next += n
+        u1, u2 = u[0::2], u[1::2]
+        return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+    def scalar(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * float(self.uniform(1)[0])
+
+
+@dataclass(frozen=True)
+class SceneSpec:
+    """Statistics of one synthetic piecewise-planar scene."""
+    H: int
+    W: int
+    bg_base: tuple = (0.0, 8.0)          # background disparity at its lowest corner
+    bg_slope: tuple = (2.0, 8.0)         # total background change across the image, px
+    n_objects: int = 20
+    obj_disp: tuple = (8.0, 64.0)        # base disparity of an object
+    obj_size: tuple = (0.05, 0.25)       # object width/height; fractions of H if <= 1, else pixels
+    obj_slope: float = 2.0               # max disparity change across one object, px
+    d_max: float = 64.0                  # objects are clamped to [0, d_max] before noise
+    sigma: float = 0.25                  # Gaussian noise std, px
+    salt: float = 0.0                    # probability that a pixel is replaced by U[0, d_max]
+    quantum: float = 0.0                 # if > 0: round the noise-free map to multiples of this (dyadic maps)
+
+
+def make_scene(spec: SceneSpec, seed: int) -> np.ndarray:
+    """Draw one float32 [H][W] disparity map (row-major, x = column, y = row pointing down)."""
+    H, W = spec.H, spec.W
+    rng = CounterRng(seed, key=1)
+    ys = np.arange(H, dtype=np.float64)[:, None]
+    xs = np.arange(W, dtype=np.float64)[None, :]
+
+    # Background plane d0 + |gx|*fx + |gy|*fy, with fx, fy running 0->1 or 1->0 by a random sign.
+    d0 = rng.scalar(*spec.bg_base)
+    total = rng.scalar(*spec.bg_slope)
+    split = rng.scalar(0.0, 1.0)
+    gx, gy = total * split, total * (1.0 - split)
+    fx = xs / W if rng.scalar(0, 1) < 0.5 else 1.0 - xs / W
+    fy = ys / H if rng.scalar(0, 1) < 0.5 else 1.0 - ys / H
+    d = d0 + gx * fx + gy * fy
+    d = np.broadcast_to(d, (H, W)).copy()
+
+    # Objects: drawn first, painted in ascending base disparity (near objects last, so the map is z-consistent).
+    objs = []
+    for _ in range(spec.n_objects):
+        lo, hi = spec.obj_size
+        if hi <= 1.0:
+            lo, hi = lo * H, hi * H
+        ow, oh = rng.scalar(lo, hi), rng.scalar(lo, hi)
+        ocx, ocy = rng.scalar(0, W), rng.scalar(0, H)
+        base = rng.scalar(*spec.obj_disp)
+        t = rng.scalar(0.0, spec.obj_slope)
+        f = rng.scalar(0.0, 1.0)
+        sx = t * f * (1 if rng.scalar(0, 1) < 0.5 else -1)
+        sy = t * (1 - f) * (1 if rng.scalar(0, 1) < 0.5 else -1)
+        ellipse = rng.scalar(0, 1) < 0.5
+        objs.append((base, ow, oh, ocx, ocy, sx, sy, ellipse))
+    objs.sort(key=lambda o: o[0])
+    for base, ow, oh, ocx, ocy, sx, sy, ellipse in objs:
+        x0, x1 = max(0, int(math.floor(ocx - ow / 2))), min(W, int(math.ceil(ocx + ow / 2)) + 1)
+        y0, y1 = max(0, int(math.floor(ocy - oh / 2))), min(H, int(math.ceil(ocy + oh / 2)) + 1)
+        if x0 >= x1 or y0 >= y1:
+            continue
+        bx = xs[:, x0:x1]
+        by = ys[y0:y1, :]
+        rx, ry = (bx - ocx) / (ow / 2), (by - ocy) / (oh / 2)
+        if ellipse:
+            inside = rx * rx + ry * ry <= 1.0
+        else:
+            inside = (np.abs(rx) <= 1.0) & (np.abs(ry) <= 1.0)
+        plane = base + sx * rx / 2 + sy * ry / 2
+        plane = np.clip(plane, 0.0, spec.d_max)
+        region = d[y0:y1, x0:x1]
+        region[inside] = np.broadcast_to(plane, inside.shape)[inside]
+
+    if spec.quantum > 0:
+        d = np.round(d / spec.quantum) * spec.quantum
+    if spec.sigma > 0:
+        d = d + spec.sigma * CounterRng(seed, key=2).normal(H * W).reshape(H, W)
+    if spec.salt > 0:
+        r = CounterRng(seed, key=3).uniform(2 * H * W).reshape(H, W, 2)
+        hit = r[..., 0] < spec.salt
+        d = np.where(hit, r[..., 1] * spec.d_max, d)
+    return np.ascontiguousarray(d.astype(np.float32))
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Views of a camera array: baseline direction alpha (degrees, from +x toward +y, y pointing down) and baseline
+# ratio r (this camera's baseline over the axial neighbour's).
+
+def views_3x3():
+    """The eight peripheral cameras of a 3x3 array: axial at ratio 1, diagonal at ratio sqrt(2)."""
+    out = []
+    for k in range(8):
+        a = 45.0 * k
+        out.append((a, 1.0 if k % 2 == 0 else float(np.float32(math.sqrt(2.0)))))
+    return out
+
+
+def views_5x5_ring():
+    """24 views at 15 degree steps on the square rings of a 5x5 array: r = ring / max(|cos a|, |sin a|)."""
+    out = []
+    for k in range(24):
+        a = 15.0 * k
+        ring = 1.0 if k % 2 == 0 else 2.0
+        rad = math.radians(a)
+        out.append((a, float(np.float32(ring / max(abs(math.cos(rad)), abs(math.sin(rad)))))))
+    return out
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# The workloads.  Each returns a list of (name, D) frames and the view table.
+
+SPEC_STEREO = SceneSpec(H=192, W=256, bg_base=(2.0, 6.0), bg_slope=(2.0, 8.0), n_objects=6,
+                        obj_disp=(10.0, 40.0), obj_size=(12.0, 60.0), d_max=64.0, sigma=0.25)
+
+
+def spec_array(H: int, W: int) -> SceneSpec:
+    return SceneSpec(H=H, W=W, bg_base=(0.0, 8.0), bg_slope=(2.0, 8.0), n_objects=20, obj_disp=(8.0, 64.0),
+                     obj_size=(0.05, 0.25), d_max=64.0, sigma=0.25)
+
+
+def spec_stress(H: int = 2160, W: int = 4096) -> SceneSpec:
+    return SceneSpec(H=H, W=W, bg_base=(0.0, 16.0), bg_slope=(4.0, 16.0), n_objects=20, obj_disp=(16.0, 128.0),
+                     obj_size=(0.05, 0.25), d_max=128.0, sigma=0.5, salt=0.02)
+
+
+MIXED_SIZES = [(480, 640), (720, 1280), (1080, 1920), (2160, 4096)]
+
+
+@dataclass
+class Workload:
+    name: str
+    frames: list = field(default_factory=list)     # list of float32 [H][W] arrays
+    views: list = field(default_factory=list)      # list of (alpha_deg, ratio)
+
+    @property
+    def pixel_views(self) -> int:
+        return sum(int(f.size) for f in self.frames) * len(self.views)
+
+
+def stereo_pair(frame: int = 0) -> Workload:
+    """One 256x192 map, horizontal stereo pair (alpha = 0, ratio 1)."""
+    return Workload("stereo_256x192_1view", [make_scene(SPEC_STEREO, seed_of(1, frame))], [(0.0, 1.0)])
+
+
+def array_3x3(frame: int = 0, H: int = 1080, W: int = 1920) -> Workload:
+    """One center-view map of a 3x3 array, eight peripheral views."""
+    return Workload(f"array3x3_{W}x{H}_8views", [make_scene(spec_array(H, W), seed_of(2, frame))], views_3x3())
+
+
+def mixed_batch(n_frames: int = 64, sizes=None) -> Workload:
+    """n_frames maps of uneven resolution (equal counts of each size, seeded shuffle), eight views each."""
+    sizes = sizes or MIXED_SIZES
+    order = [sizes[i % len(sizes)] for i in range(n_frames)]
+    perm = np.argsort(CounterRng(seed_of(3, 1 << 20), key=4).uniform(n_frames), kind="stable")
+    frames = [make_scene(spec_array(*order[i]), seed_of(3, f)) for f, i in enumerate(perm)]
+    return Workload(f"mixed_{n_frames}frames_8views", frames, views_3x3())
+
+
+def stress_5x5(frame: int = 0, H: int = 2160, W: int = 4096) -> Workload:
+    """4096x2160 map with salt outliers, 24 views on the rings of a 5x5 array."""
+    return Workload(f"array5x5_{W}x{H}_24views", [make_scene(spec_stress(H, W), seed_of(4, frame))],
+                    views_5x5_ring())
