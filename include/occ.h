@@ -1,0 +1,168 @@
+/*
+ * occ.h -- C ABI of the GB300 (sm_103a) fast edge-aware occlusion detection library.
+ *
+ * The library computes, for a fused center-view disparity map D and the baseline direction of each peripheral
+ * camera, the center pixels that the peripheral camera does not see (Sippel, Seiler, Kaup, "Fast Edge-Aware
+ * Occlusion Detection in the Context of Multispectral Camera Arrays", ICIP 2024, Section 3):
+ *   Eq. 1   forward-difference edge maps E_x, E_y of D, the magnitude E and the angle A;
+ *   Eq. 2   candidates C: E > gamma and the gradient pointing along the baseline angle alpha;
+ *   Eq. 3   scan length L = ceil(2 (max D - min D));
+ *   Eq. 4   a scan line of 2h+1 samples (h = ceil(L/2)) along alpha through every candidate, with depth values V;
+ *           the warp W = G - V of each sample, and the sort of each scan line by (W, k);
+ *   Eq. 5   the occlusion count of every sorted sample against its N nearest sorted neighbours
+ *           (|W_p - W_q| < zeta and V_p + beta < V_q);
+ *   Eq. 6   the occlusion sum O (every scan line's counts accumulated per pixel) and the mask M = (O > 0).
+ *
+ * Readings of the paper's silent or garbled passages, applied everywhere below:
+ *   - alpha is the direction from the center camera to the peripheral camera, in degrees, measured from +x
+ *     (columns) toward +y (rows, pointing down); content moves by -r D along alpha, so W = G - V.
+ *   - The disparity test of Eq. 5 is V_p + beta < V_q (p is behind q by more than beta).
+ *   - The angle test of Eq. 2 is the sign test E_x cos(alpha) + E_y sin(alpha) > 0 (equivalent to
+ *     |wrap(atan2(E_y, E_x) - alpha)| < pi/2); cos and sin are rounded to binary32 after reducing alpha to
+ *     [0, 45] degrees, so multiples of 90 degrees give exact 0 and +-1.
+ *   - A peripheral camera with baseline ratio r (its baseline over the axial one) sees disparity r D: the whole
+ *     method runs on D_r = fl(r D); E and A outputs are those of D itself (r = 1).
+ *   - Scan line positions are rounded to the nearest pixel (ties away from zero); samples outside the image are
+ *     dropped; the sort key is (W ascending, k ascending); overlapping scan lines add up in O.
+ * All arithmetic that decides M and O is binary32, round-to-nearest, one operation at a time (no contraction),
+ * so M and O are reproducible bit for bit.
+ *
+ * Memory and streams.  Every device pointer is a plain CUDA device address on the context's device (for example
+ * torch.Tensor.data_ptr() of a CUDA tensor).  Calls are asynchronous on the given stream (a cudaStream_t passed as
+ * void*, NULL = the legacy default stream); outputs are complete when the stream reaches that point.  One context
+ * serves one host thread and one stream at a time.
+ *
+ * Errors.  Every entry point returns an int status.  Argument errors are detected on the host before any work is
+ * queued (OCC_ERR_INVALID_ARG).  Conditions only the device can see (non-finite input, candidate list overflow,
+ * a scan length above OCC_MAX_SCAN) set bits in a device status word that occ_get_status() reads; while that
+ * status is not OCC_OK the outputs of that call are unspecified.  No call aborts, traps or throws.
+ */
+#ifndef OCC_H
+#define OCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define OCC_OK 0
+#define OCC_ERR_INVALID_ARG 1     /* a host-checked argument is out of range */
+#define OCC_ERR_NONFINITE_INPUT 2 /* D holds a NaN or an infinity (the method is defined for finite maps) */
+#define OCC_ERR_CAPACITY 3        /* candidate list overflow, or the automatic L exceeds OCC_MAX_SCAN */
+#define OCC_ERR_TIMEOUT 4         /* a bounded device wait gave up */
+#define OCC_ERR_CUDA 5            /* a CUDA runtime call failed (allocation, launch, copy) */
+
+/* Limits. */
+#define OCC_MAX_VIEWS 64     /* views per call */
+#define OCC_MAX_SCAN 4094    /* largest scan length L (Eq. 3); 2h+1 <= 4095 samples per scan line */
+#define OCC_MAX_SIDE 65535   /* largest H and W */
+#define OCC_MAX_N 64         /* largest neighbour count N (Eq. 5) */
+
+typedef struct occ_ctx occ_ctx; /* opaque; owns the device scratch of one device */
+
+/* One peripheral view: baseline angle alpha in degrees (Eq. 2, Eq. 4) and baseline ratio r > 0. */
+typedef struct {
+    double alpha_deg;
+    float ratio;
+} occ_view;
+
+/* Parameters of Section 3.  gamma: edge threshold (Eq. 2).  zeta: distance threshold and beta: disparity threshold
+ * (Eq. 5).  L: scan length; L <= 0 computes it per view by Eq. 3 on the device.  N: neighbours compared per sorted
+ * sample (Eq. 5), even, 2 <= N <= OCC_MAX_N.  The paper fits gamma = 1.0, zeta = 2.0, beta = 0.5 on SceneFlow
+ * (Section 4.1) and gives no N; occ_default_params() returns those values with N = 8. */
+typedef struct {
+    float gamma;
+    float zeta;
+    float beta;
+    int32_t L;
+    int32_t N;
+} occ_params;
+
+/* Work counts of one view of the last occ_detect call: |C| (Eq. 2), scan line samples inside the image, (p, d)
+ * neighbour pairs tested (Eq. 5), and the scan length used (Eq. 3). */
+typedef struct {
+    int64_t candidates;
+    int64_t samples;
+    int64_t pair_tests;
+    int32_t L;
+    int32_t reserved;
+} occ_view_stats;
+
+/* Fills *p with gamma 1.0, zeta 2.0, beta 0.5, L 0 (automatic), N 8. */
+void occ_default_params(occ_params* p);
+
+/* The binary32 cos and sin of alpha_deg used by Eq. 2 and Eq. 4 (reduction to [0, 45] degrees, evaluation in
+ * double, one rounding).  Host only; never fails. */
+void occ_direction(double alpha_deg, float* c, float* s);
+
+/* Creates a context on CUDA device `device` and allocates its scratch: the candidate lists (max_candidates entries
+ * per view; <= 0 means max_pixels, which never overflows), the status word and the per-view counters.
+ * max_pixels >= 1 bounds H*W of later calls; 1 <= max_views <= OCC_MAX_VIEWS.  On success *out receives the
+ * context; on failure *out is NULL and the return is OCC_ERR_INVALID_ARG or OCC_ERR_CUDA. */
+int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views, int64_t max_candidates);
+
+/* Frees the context and all its device memory.  NULL is ignored.  The caller makes sure no queued work still
+ * uses the context (synchronise its stream first). */
+void occ_destroy(occ_ctx* ctx);
+
+/*
+ * The whole method of Section 3 (Eq. 1-6) for one frame and n_views views, queued on `stream`.
+ *   D      device, binary32 [H][pitch] row-major (x = column, y = row pointing down), 4-byte aligned, read only;
+ *          pitch (elements) >= W, or 0 for pitch = W.  1 <= H, W <= OCC_MAX_SIDE, H*W <= the context's max_pixels.
+ *   views  host, n_views entries (1 <= n_views <= the context's max_views), copied during the call;
+ *          alpha finite, ratio finite and > 0.
+ *   p      host, copied during the call; NULL means occ_default_params().  zeta > 0, all thresholds finite.
+ *   M      device, uint8 [n_views][H][W], required: 1 where O > 0, else 0 (Eq. 6).  Fully overwritten.
+ *   O      device, int32 [n_views][H][W], 4-byte aligned, or NULL: the occlusion sum of Eq. 5/6 per pixel.  Fully
+ *          overwritten.  When NULL the context uses scratch of its own, allocated on the first such call.
+ *   E, A   device, binary32 [H][W], or NULL: the edge magnitude and angle maps of D (r = 1), A = atan2(E_y, E_x).
+ * The caller owns D, M, O, E and A; none may overlap.  Returns OCC_OK once the work is queued, or
+ * OCC_ERR_INVALID_ARG / OCC_ERR_CUDA without queueing anything.  Device-detected errors surface through
+ * occ_get_status().  The stream must not be in graph capture on the first call that passes O = NULL.
+ */
+int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views,
+               int32_t n_views, const occ_params* p, uint8_t* M, int32_t* O, float* E, float* A, void* stream);
+
+/*
+ * occ_detect on host buffers: copies D (host, binary32 [H][W], pinned memory recommended) to the device, runs
+ * occ_detect, copies M (and O when O_host is not NULL) back to host memory, and waits for the stream.
+ * D_host, M_host [n_views][H][W] and O_host [n_views][H][W] are host pointers owned by the caller.  The device
+ * staging buffers are owned by the context and allocated on the first call.  Returns the status of the whole
+ * call, device-detected errors included (as occ_get_status() would).
+ */
+int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,
+                    int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream);
+
+/* Waits for `stream` and returns the device status of the last occ_detect call of this context: OCC_OK,
+ * OCC_ERR_NONFINITE_INPUT, OCC_ERR_CAPACITY or OCC_ERR_TIMEOUT (in that priority), or OCC_ERR_CUDA if the wait
+ * itself failed. */
+int occ_get_status(occ_ctx* ctx, void* stream);
+
+/* Copies the work counts of the first n_views views of the last occ_detect call into out (host).  Waits for the
+ * last stream used.  Returns OCC_ERR_INVALID_ARG if n_views exceeds the views of that call. */
+int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
+
+/* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the scan kernels
+ * of the three scan-line size classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6), and the mask (Eq. 6). */
+#define OCC_NUM_STAGES 5
+
+/* enable != 0: later occ_detect calls record a CUDA event on their stream before and after each stage, so that
+ * occ_get_timings() can report the device time of each stage.  Off by default.  Returns OCC_OK or
+ * OCC_ERR_INVALID_ARG. */
+int occ_set_profiling(occ_ctx* ctx, int enable);
+
+/* Device milliseconds of the first n (<= OCC_NUM_STAGES) stages of the last occ_detect call made with profiling on
+ * (0 for a stage that was not launched), written to ms (host).  Waits for that call's last event.  Returns
+ * OCC_ERR_INVALID_ARG if no profiled call was made. */
+int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
+
+/* A static, human-readable name of a status code. */
+const char* occ_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCC_H */

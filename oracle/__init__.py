@@ -76,6 +76,11 @@ def lib():
                                                  ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, i32p, u8p,
                                                  ctypes.POINTER(Stats)]
             L.ora_detect_view_region.restype = ctypes.c_int
+            L.ora_detect_view_masked.argtypes = [f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                                 ctypes.c_float, ctypes.POINTER(Params), ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, u8p, i32p, u8p,
+                                                 ctypes.POINTER(Stats)]
+            L.ora_detect_view_masked.restype = ctypes.c_int
             L.ora_candidates.argtypes = [f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_float,
                                          ctypes.c_float, i64p, ctypes.c_int64]
             L.ora_candidates.restype = ctypes.c_int64
@@ -140,6 +145,25 @@ def detect_view(D, alpha_deg: float, ratio: float = 1.0, params: Params | None =
     if rc != OK:
         raise ValueError(f"oracle detect failed: {rc}")
     return O, M, st.as_dict()
+
+
+def detect_view_masked(D, alpha_deg: float, ratio: float, params: Params | None, cand_mask):
+    """detect_view restricted to the candidates where cand_mask (uint8 [H][W]) is non-zero: O then holds exactly
+    their contributions.  Returns (O, stats)."""
+    D = _map(D)
+    H, W = D.shape
+    p = params or default_params()
+    mask = np.ascontiguousarray(cand_mask, dtype=np.uint8)
+    if mask.shape != (H, W):
+        raise ValueError("mask shape")
+    O = np.empty((H, W), dtype=np.int32)
+    st = Stats()
+    rc = lib().ora_detect_view_masked(_ptr(D, ctypes.c_float), H, W, float(alpha_deg), float(ratio),
+                                      ctypes.byref(p), 0, 0, W, H, _ptr(mask, ctypes.c_uint8),
+                                      _ptr(O, ctypes.c_int32), None, ctypes.byref(st))
+    if rc != OK:
+        raise ValueError(f"oracle detect failed: {rc}")
+    return O, st.as_dict()
 
 
 def detect(D, views, params: Params | None = None):

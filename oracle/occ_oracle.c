@@ -220,12 +220,13 @@ static int64_t count_occlusions(const ora_sample* srt, int32_t n, const ora_para
 /*
  * The whole method of Section 3 for one view: Eq. 1 -> Eq. 2 -> Eq. 3 -> Eq. 4 -> sort -> Eq. 5 -> Eq. 6.
  * D: [H][W] binary32.  O: [H][W] int32 (overwritten).  M: [H][W] uint8 (overwritten, may be NULL).
- * Only candidates inside [cx0, cx1) x [cy0, cy1) are processed (pass 0, 0, W, H for the whole map); the
- * region lets a test recompute a window of a large map from the candidates that can reach it.
+ * Only candidates inside [cx0, cx1) x [cy0, cy1) and, when cand_mask is not NULL, with cand_mask[y*W+x] != 0 are
+ * processed (pass 0, 0, W, H, NULL for the whole map).  The selection lets a test recompute a window of a large
+ * map from the candidates whose scan lines can reach it; it changes no arithmetic.
  */
-int ora_detect_view_region(const float* D, int32_t H, int32_t W, double alpha_deg, float r,
+int ora_detect_view_masked(const float* D, int32_t H, int32_t W, double alpha_deg, float r,
                            const ora_params* p, int32_t cx0, int32_t cy0, int32_t cx1, int32_t cy1,
-                           int32_t* O, uint8_t* M, ora_stats* st)
+                           const uint8_t* cand_mask, int32_t* O, uint8_t* M, ora_stats* st)
 {
     if (H < 1 || W < 1 || !p || !O) return ORA_ERR_ARG;
     if (p->N < 2 || (p->N % 2) != 0 || !(p->zeta > 0.0f) || !(r > 0.0f) || !isfinite(r)) return ORA_ERR_ARG;
@@ -247,6 +248,7 @@ int ora_detect_view_region(const float* D, int32_t H, int32_t W, double alpha_de
     if (cy1 > H) cy1 = H;
     for (int64_t y = cy0; y < cy1; y++) {
         for (int64_t x = cx0; x < cx1; x++) {
+            if (cand_mask && !cand_mask[y * (int64_t)W + x]) continue;
             if (!is_candidate(D, H, W, x, y, r, c, s, p->gamma)) continue;
             acc.candidates++;
             int32_t n = scanline(D, H, W, r, c, s, h, x, y, buf);
@@ -262,10 +264,17 @@ int ora_detect_view_region(const float* D, int32_t H, int32_t W, double alpha_de
     return ORA_OK;
 }
 
+int ora_detect_view_region(const float* D, int32_t H, int32_t W, double alpha_deg, float r,
+                           const ora_params* p, int32_t cx0, int32_t cy0, int32_t cx1, int32_t cy1,
+                           int32_t* O, uint8_t* M, ora_stats* st)
+{
+    return ora_detect_view_masked(D, H, W, alpha_deg, r, p, cx0, cy0, cx1, cy1, NULL, O, M, st);
+}
+
 int ora_detect_view(const float* D, int32_t H, int32_t W, double alpha_deg, float r, const ora_params* p,
                     int32_t* O, uint8_t* M, ora_stats* st)
 {
-    return ora_detect_view_region(D, H, W, alpha_deg, r, p, 0, 0, W, H, O, M, st);
+    return ora_detect_view_masked(D, H, W, alpha_deg, r, p, 0, 0, W, H, NULL, O, M, st);
 }
 
 /* The candidate list of Eq. 2 for one view, in row-major order, as y * W + x.  Returns the count, or -1 if

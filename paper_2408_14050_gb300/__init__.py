@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) fast edge-aware occlusion detection -- Python binding of the C ABI in include/occ.h.
+
+Sippel, Seiler, Kaup, "Fast Edge-Aware Occlusion Detection in the Context of Multispectral Camera Arrays"
+(ICIP 2024), Section 3: from a fused center-view disparity map D and the baseline angle alpha of each peripheral
+camera, the occlusion sum O (Eq. 5/6) and the mask M = (O > 0) of center pixels that camera does not see.
+
+This module only marshals arguments: every step runs in the CUDA kernels of the in-tree library
+_lib/libocc.so (built by build.py for sm_103a).  There is no CPU path; if the library cannot be loaded, every call
+raises.  Device memory and streams come from PyTorch (torch.Tensor.data_ptr(), torch.cuda.Stream.cuda_stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+OCC_OK = 0
+OCC_ERR_INVALID_ARG = 1
+OCC_ERR_NONFINITE_INPUT = 2
+OCC_ERR_CAPACITY = 3
+OCC_ERR_TIMEOUT = 4
+OCC_ERR_CUDA = 5
+OCC_MAX_VIEWS = 64
+OCC_MAX_SCAN = 4094
+OCC_MAX_SIDE = 65535
+OCC_MAX_N = 64
+
+OCC_NUM_STAGES = 5
+STAGES = ["candidates", "scan_256", "scan_1024", "scan_4096", "mask"]
+
+EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
+            "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_status_string"]
+
+
+class occ_view(ctypes.Structure):
+    """Baseline angle alpha in degrees (x toward y, y pointing down) and baseline ratio r."""
+    _fields_ = [("alpha_deg", ctypes.c_double), ("ratio", ctypes.c_float)]
+
+
+class occ_params(ctypes.Structure):
+    """gamma (Eq. 2), zeta and beta (Eq. 5), L (Eq. 3, <= 0 automatic), N (Eq. 5)."""
+    _fields_ = [("gamma", ctypes.c_float), ("zeta", ctypes.c_float), ("beta", ctypes.c_float),
+                ("L", ctypes.c_int32), ("N", ctypes.c_int32)]
+
+
+class occ_view_stats(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int64), ("samples", ctypes.c_int64), ("pair_tests", ctypes.c_int64),
+                ("L", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"candidates": int(self.candidates), "samples": int(self.samples),
+                "pair_tests": int(self.pair_tests), "L": int(self.L)}
+
+
+class OccError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {occ_status_string(status)} ({status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libocc.so (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; run paper_2408_14050_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.occ_default_params.argtypes = [ctypes.POINTER(occ_params)]
+        L.occ_default_params.restype = None
+        L.occ_direction.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]
+        L.occ_direction.restype = None
+        L.occ_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64, i32, i64]
+        L.occ_create.restype = ctypes.c_int
+        L.occ_destroy.argtypes = [vp]
+        L.occ_destroy.restype = None
+        L.occ_detect.argtypes = [vp, vp, i32, i32, i64, ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
+                                 vp, vp, vp, vp, vp]
+        L.occ_detect.restype = ctypes.c_int
+        L.occ_detect_host.argtypes = [vp, vp, i32, i32, ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
+                                      vp, vp, vp]
+        L.occ_detect_host.restype = ctypes.c_int
+        L.occ_get_status.argtypes = [vp, vp]
+        L.occ_get_status.restype = ctypes.c_int
+        L.occ_get_stats.argtypes = [vp, ctypes.POINTER(occ_view_stats), i32]
+        L.occ_get_stats.restype = ctypes.c_int
+        L.occ_set_profiling.argtypes = [vp, ctypes.c_int]
+        L.occ_set_profiling.restype = ctypes.c_int
+        L.occ_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
+        L.occ_get_timings.restype = ctypes.c_int
+        L.occ_status_string.argtypes = [ctypes.c_int]
+        L.occ_status_string.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Host-only helpers
+
+def occ_default_params(**overrides) -> occ_params:
+    p = occ_params()
+    load().occ_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def occ_direction(alpha_deg: float):
+    c, s = ctypes.c_float(), ctypes.c_float()
+    load().occ_direction(float(alpha_deg), ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def occ_status_string(status: int) -> str:
+    return load().occ_status_string(int(status)).decode()
+
+
+def _views(views):
+    arr = (occ_view * len(views))()
+    for i, (a, r) in enumerate(views):
+        arr[i].alpha_deg = float(a)
+        arr[i].ratio = float(r)
+    return arr
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Context and calls
+
+class Context:
+    """Owns one occ_ctx (device scratch of one device)."""
+
+    def __init__(self, handle, device, max_pixels, max_views):
+        self.handle = handle
+        self.device = device
+        self.max_pixels = max_pixels
+        self.max_views = max_views
+        self.last_views = 0
+
+    def close(self):
+        if self.handle:
+            load().occ_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def occ_create(device: int = 0, max_pixels: int = 1920 * 1080, max_views: int = 8, max_candidates: int = 0):
+    h = ctypes.c_void_p()
+    rc = load().occ_create(ctypes.byref(h), int(device), int(max_pixels), int(max_views), int(max_candidates))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_create")
+    return Context(h, device, max_pixels, max_views)
+
+
+def occ_destroy(ctx: Context):
+    ctx.close()
+
+
+def occ_detect(ctx: Context, D, views, params: occ_params | None = None, M=None, O=None, E=None, A=None,
+               stream=None, want_O: bool = True):
+    """Queue the method on device tensors.  D: float32 CUDA tensor [H][W] (row stride may exceed W).  Returns
+    (M uint8 [V][H][W], O int32 [V][H][W] or None).  Output tensors are allocated when not given."""
+    import torch
+    if D.dtype != torch.float32 or D.dim() != 2 or not D.is_cuda or D.stride(1) != 1:
+        raise ValueError("D must be a float32 CUDA tensor [H][W] with unit column stride")
+    H, W = D.shape
+    nv = len(views)
+    if M is None:
+        M = torch.empty((nv, H, W), dtype=torch.uint8, device=D.device)
+    if O is None and want_O:
+        O = torch.empty((nv, H, W), dtype=torch.int32, device=D.device)
+    for t, dt in ((M, torch.uint8), (O, torch.int32), (E, torch.float32), (A, torch.float32)):
+        if t is not None and (t.dtype != dt or not t.is_contiguous() or not t.is_cuda):
+            raise ValueError("outputs must be contiguous CUDA tensors of the documented dtypes")
+    rc = load().occ_detect(ctx.handle, _ptr(D), H, W, D.stride(0), _views(views), nv,
+                           ctypes.byref(params) if params is not None else None, _ptr(M), _ptr(O), _ptr(E), _ptr(A),
+                           _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_detect")
+    ctx.last_views = nv
+    return M, O
+
+
+def occ_detect_host(ctx: Context, D, views, params: occ_params | None = None, M=None, O=None, stream=None):
+    """The method on host buffers (numpy or CPU tensors; pinned memory is fastest): copies in, runs, copies M (and O
+    if given) back, waits.  Returns the status code."""
+    import numpy as np
+    H, W = D.shape
+    nv = len(views)
+    if M is None:
+        M = np.empty((nv, H, W), dtype=np.uint8)
+
+    def addr(x):
+        if x is None:
+            return None
+        if hasattr(x, "data_ptr"):
+            return ctypes.c_void_p(x.data_ptr())
+        return ctypes.c_void_p(x.ctypes.data)
+
+    rc = load().occ_detect_host(ctx.handle, addr(D), H, W, _views(views), nv,
+                                ctypes.byref(params) if params is not None else None, addr(M), addr(O),
+                                _stream_handle(stream))
+    ctx.last_views = nv
+    return rc, M, O
+
+
+def occ_get_status(ctx: Context, stream=None) -> int:
+    return int(load().occ_get_status(ctx.handle, _stream_handle(stream)))
+
+
+def occ_get_stats(ctx: Context, n_views: int | None = None):
+    n = ctx.last_views if n_views is None else n_views
+    out = (occ_view_stats * max(n, 1))()
+    rc = load().occ_get_stats(ctx.handle, out, n)
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_get_stats")
+    return [out[i].as_dict() for i in range(n)]
+
+
+def occ_set_profiling(ctx: Context, enable: bool = True):
+    rc = load().occ_set_profiling(ctx.handle, 1 if enable else 0)
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_set_profiling")
+
+
+def occ_get_timings(ctx: Context) -> dict:
+    """Device milliseconds of each stage of the last profiled occ_detect call."""
+    ms = (ctypes.c_float * OCC_NUM_STAGES)()
+    rc = load().occ_get_timings(ctx.handle, ms, OCC_NUM_STAGES)
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_get_timings")
+    return {name: float(ms[i]) for i, name in enumerate(STAGES)}

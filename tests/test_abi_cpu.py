@@ -1,0 +1,85 @@
+"""The C-ABI library without a GPU: it builds for sm_103a, loads, exports every entry point include/occ.h declares,
+and its host-only helpers agree with the oracle's independent restatement of the same definitions."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2408_14050_gb300 as occ
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "occ.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(occ_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_functions() == sorted(occ.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = occ.load()
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    nm = subprocess.run(["nm", "-D", "--defined-only", occ.library_path()], capture_output=True, text=True)
+    if nm.returncode == 0:
+        exported = set(re.findall(r"\bT (occ_[a-z_]+)$", nm.stdout, flags=re.M))
+        assert set(declared_functions()) <= exported
+
+
+def test_default_params():
+    p = occ.occ_default_params()
+    assert (p.gamma, p.zeta, p.beta, p.L, p.N) == (1.0, 2.0, 0.5, 0, 8)
+
+
+def test_status_strings():
+    for code in range(0, 6):
+        assert isinstance(occ.occ_status_string(code), str) and occ.occ_status_string(code)
+    assert occ.occ_status_string(99) == "unknown status"
+
+
+def test_direction_agrees_with_oracle():
+    rng = np.random.default_rng(3)
+    angles = np.concatenate([np.arange(-720, 721, 0.5), rng.uniform(-1e4, 1e4, 2000), [1e-300, -1e-300, 359.9999999]])
+    for a in angles:
+        c1, s1 = occ.occ_direction(a)
+        c2, s2 = oracle.direction(a)
+        assert np.float32(c1) == c2 and np.float32(s1) == s2, a
+
+
+def test_direction_exact_on_axes():
+    for a, (c, s) in {0: (1, 0), 90: (0, 1), 180: (-1, 0), 270: (0, -1)}.items():
+        assert occ.occ_direction(a) == (c, s)
+    r = float(np.float32(math.sqrt(0.5)))
+    assert occ.occ_direction(45) == (r, r)
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = occ.load().occ_create(ctypes.byref(h), 0, 1024, 1, 0)
+    assert rc == occ.OCC_ERR_CUDA and not h.value
+
+
+def test_invalid_arguments_rejected_before_any_device_work():
+    lib = occ.load()
+    h = ctypes.c_void_p()
+    assert lib.occ_create(None, 0, 1024, 1, 0) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_create(ctypes.byref(h), 0, 0, 1, 0) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_create(ctypes.byref(h), 0, 1024, 0, 0) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_create(ctypes.byref(h), 0, 1024, 65, 0) == occ.OCC_ERR_INVALID_ARG
+    v = (occ.occ_view * 1)()
+    assert lib.occ_detect(None, None, 4, 4, 0, v, 1, None, None, None, None, None, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_get_status(None, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_get_stats(None, None, 1) == occ.OCC_ERR_INVALID_ARG
+    lib.occ_destroy(None)
