@@ -24,7 +24,7 @@ struct occ_ctx {
     uint8_t* d_M_stage = nullptr;
     int32_t* d_O_stage = nullptr;
     int grid_edges = 0, grid_mask = 0;
-    int grid_scan[kNumClasses] = {0, 0, 0};
+    int grid_scan[kNumClasses + 1] = {0, 0, 0, 0};
     int32_t last_nv = 0;
     cudaStream_t last_stream = nullptr;
     bool profiling = false;
@@ -144,7 +144,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
 
     DeviceGuard g(device);
     if (!g.ok) { delete ctx; return OCC_ERR_CUDA; }
-    int bps_edges = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
+    int bps_edges = 0, bps_mask = 0, bps_scan[kNumClasses + 1] = {0, 0, 0, 0};
     ctx->hdr_bytes = sizeof(uint32_t) * HDR_WORDS + sizeof(unsigned long long) * 2 * (size_t)max_views;
     bool ok = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
               configure_kernels(&bps_edges, bps_scan, &bps_mask) == cudaSuccess &&
@@ -159,7 +159,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     ctx->d_stats = reinterpret_cast<unsigned long long*>(ctx->d_hdr + HDR_WORDS);
     ctx->grid_edges = ctx->num_sms * (bps_edges > 0 ? bps_edges : 1);
     ctx->grid_mask = ctx->num_sms * (bps_mask > 0 ? bps_mask : 1);
-    for (int c = 0; c < kNumClasses; c++) ctx->grid_scan[c] = ctx->num_sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
+    for (int c = 0; c <= kNumClasses; c++) ctx->grid_scan[c] = ctx->num_sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
     *out = ctx;
     return OCC_OK;
 }
@@ -247,8 +247,10 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
     auto mark = [&](int i) { return !prof || cudaEventRecord(ctx->ev[i], st) == cudaSuccess; };
     if (cudaMemsetAsync(ctx->d_hdr, 0, ctx->hdr_bytes, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (!mark(0) || launch_edges(a, grid_edges, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
+    const bool fast = (p.N / 2) <= kFastMaxHalf;
     for (int c = 0; c < kNumClasses; c++) {
-        if (run_cls[c] && launch_scan(a, c, ctx->grid_scan[c], st) != cudaSuccess) return OCC_ERR_CUDA;
+        const int id = (c == 0 && fast) ? kFastClass : c;
+        if (run_cls[c] && launch_scan(a, id, ctx->grid_scan[id], st) != cudaSuccess) return OCC_ERR_CUDA;
         if (!mark(2 + c)) return OCC_ERR_CUDA;
     }
     if (launch_mask(a, ctx->grid_mask, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;

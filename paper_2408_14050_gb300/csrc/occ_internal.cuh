@@ -34,6 +34,9 @@ enum : uint32_t {
 // Scan-length classes: one scan kernel instantiation per class, sized by the samples of one scan line (2h+1).
 constexpr int kNumClasses = 3;
 constexpr int kClassCap[kNumClasses] = {256, 1024, 4096};
+// Launch id of the register-resident scan kernel, which replaces class 0 when N <= 2 * kFastMaxHalf.
+constexpr int kFastClass = kNumClasses;
+constexpr int kFastMaxHalf = 4;
 
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
@@ -65,7 +68,8 @@ cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st);
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, int grid, cudaStream_t st);
 // Per-SM resident blocks of each kernel (for persistent grids); also sets the shared-memory opt-ins.
-cudaError_t configure_kernels(int* edges_blocks_per_sm, int scan_blocks_per_sm[kNumClasses],
+// scan_blocks_per_sm has kNumClasses + 1 entries (the last for the register-resident kernel).
+cudaError_t configure_kernels(int* edges_blocks_per_sm, int scan_blocks_per_sm[kNumClasses + 1],
                               int* mask_blocks_per_sm);
 
 }  // namespace occ
