@@ -208,7 +208,8 @@ def run_ours(args):
                 "frac": round(achieved / (alu_peak / 1e9), 4), "traffic": None, "kernel": f"k_scan ({dom})",
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz", "ops_per_launch": ops}
     else:
-        kbytes = {"candidates": 4 * H * W + 4 * H * W * V, "mask": 5 * H * W * V}.get(dom, step_bytes)
+        kbytes = {"candidates": 4 * H * W + 4 * H * W * V, "mask": 5 * H * W * V,
+                  "layout": 4 * H * W}.get(dom, step_bytes)
         achieved = kbytes / (mean_stage[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": dom,
@@ -253,7 +254,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * 5,
+            "gpu_launches": args.steps * 6,
             "clocks": clk,
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
             "work": {"samples_per_step": samples, "pair_tests_per_step": pairs,

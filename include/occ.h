@@ -117,10 +117,12 @@ void occ_destroy(occ_ctx* ctx);
  *   M      device, uint8 [n_views][H][W], required: 1 where O > 0, else 0 (Eq. 6).  Fully overwritten.
  *   O      device, int32 [n_views][H][W], 4-byte aligned, or NULL: the occlusion sum of Eq. 5/6 per pixel.  Fully
  *          overwritten.  When NULL the context uses scratch of its own, allocated on the first such call.
+ * The context also keeps copies of D laid out along the scan lines of steep and diagonal views; they are
+ * (re)allocated by the first call that needs more room than earlier calls did.
  *   E, A   device, binary32 [H][W], or NULL: the edge magnitude and angle maps of D (r = 1), A = atan2(E_y, E_x).
  * The caller owns D, M, O, E and A; none may overlap.  Returns OCC_OK once the work is queued, or
  * OCC_ERR_INVALID_ARG / OCC_ERR_CUDA without queueing anything.  Device-detected errors surface through
- * occ_get_status().  The stream must not be in graph capture on the first call that passes O = NULL.
+ * occ_get_status().  A call that allocates (see O and the layout copies above) must not run under stream capture.
  */
 int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views,
                int32_t n_views, const occ_params* p, uint8_t* M, int32_t* O, float* E, float* A, void* stream);
@@ -144,9 +146,10 @@ int occ_get_status(occ_ctx* ctx, void* stream);
  * last stream used.  Returns OCC_ERR_INVALID_ARG if n_views exceeds the views of that call. */
 int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
 
-/* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the scan kernels
- * of the three scan-line size classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6), and the mask (Eq. 6). */
-#define OCC_NUM_STAGES 5
+/* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the copies of D
+ * whose rows follow the scan lines of steep and diagonal views, the scan kernels of the three scan-line size
+ * classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6), and the mask (Eq. 6). */
+#define OCC_NUM_STAGES 6
 
 /* enable != 0: later occ_detect calls record a CUDA event on their stream before and after each stage, so that
  * occ_get_timings() can report the device time of each stage.  Off by default.  Returns OCC_OK or

@@ -27,8 +27,8 @@ OCC_MAX_SCAN = 4094
 OCC_MAX_SIDE = 65535
 OCC_MAX_N = 64
 
-OCC_NUM_STAGES = 5
-STAGES = ["candidates", "scan_256", "scan_1024", "scan_4096", "mask"]
+OCC_NUM_STAGES = 6
+STAGES = ["candidates", "layout", "scan_256", "scan_1024", "scan_4096", "mask"]
 
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
             "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_status_string"]

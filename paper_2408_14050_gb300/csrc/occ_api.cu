@@ -24,7 +24,9 @@ struct occ_ctx {
     uint8_t* d_M_stage = nullptr;
     int32_t* d_O_stage = nullptr;
     int grid_edges = 0, grid_mask = 0;
-    int grid_scan[kNumClasses + 1] = {0, 0, 0, 0};
+    int grid_scan[kNumClasses] = {0, 0, 0};
+    float* d_layout = nullptr;                 // T, A, B copies of D, grown on demand
+    size_t layout_bytes = 0;
     int32_t last_nv = 0;
     cudaStream_t last_stream = nullptr;
     bool profiling = false;
@@ -50,6 +52,23 @@ struct DeviceGuard {
 };
 
 bool is_finite_f(float x) { return std::isfinite(x); }
+
+// The copy of D whose rows follow a view's scan lines: rows of D for lines within 22.5 degrees of horizontal, the
+// transpose for lines within 22.5 degrees of vertical, and the two diagonal shears otherwise (y points down, so
+// direction (1, 1) keeps x - y fixed and (-1, 1) keeps x + y fixed).
+void choose_layout(ViewArg& v, int H)
+{
+    double th = std::atan2((double)v.s, (double)v.c) * (180.0 / M_PI);
+    if (th < 0.0) th += 180.0;
+    if (th >= 180.0) th -= 180.0;
+    v.layout = (th < 22.5 || th >= 157.5) ? LAYOUT_ROWS : (th < 67.5 ? LAYOUT_A : (th < 112.5 ? LAYOUT_T : LAYOUT_B));
+    switch (v.layout) {
+    case LAYOUT_T: v.rpx = 1; v.rpy = 0; v.r0 = 0; v.cpx = 0; v.cpy = 1; break;
+    case LAYOUT_A: v.rpx = 1; v.rpy = -1; v.r0 = H - 1; v.cpx = 0; v.cpy = 1; break;
+    case LAYOUT_B: v.rpx = 1; v.rpy = 1; v.r0 = 0; v.cpx = 0; v.cpy = 1; break;
+    default: v.rpx = 0; v.rpy = 1; v.r0 = 0; v.cpx = 1; v.cpy = 0; break;
+    }
+}
 
 }  // namespace
 
@@ -119,6 +138,7 @@ void occ_destroy(occ_ctx* ctx)
         cudaFree(ctx->d_D_stage);
         cudaFree(ctx->d_M_stage);
         cudaFree(ctx->d_O_stage);
+        cudaFree(ctx->d_layout);
         for (int i = 0; i <= OCC_NUM_STAGES; i++)
             if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     }
@@ -144,7 +164,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
 
     DeviceGuard g(device);
     if (!g.ok) { delete ctx; return OCC_ERR_CUDA; }
-    int bps_edges = 0, bps_mask = 0, bps_scan[kNumClasses + 1] = {0, 0, 0, 0};
+    int bps_edges = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
     ctx->hdr_bytes = sizeof(uint32_t) * HDR_WORDS + sizeof(unsigned long long) * 2 * (size_t)max_views;
     bool ok = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
               configure_kernels(&bps_edges, bps_scan, &bps_mask) == cudaSuccess &&
@@ -159,7 +179,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     ctx->d_stats = reinterpret_cast<unsigned long long*>(ctx->d_hdr + HDR_WORDS);
     ctx->grid_edges = ctx->num_sms * (bps_edges > 0 ? bps_edges : 1);
     ctx->grid_mask = ctx->num_sms * (bps_mask > 0 ? bps_mask : 1);
-    for (int c = 0; c <= kNumClasses; c++) ctx->grid_scan[c] = ctx->num_sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
+    for (int c = 0; c < kNumClasses; c++) ctx->grid_scan[c] = ctx->num_sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
     *out = ctx;
     return OCC_OK;
 }
@@ -191,6 +211,8 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
         if (!std::isfinite(al) || !is_finite_f(r) || !(r > 0.0f)) return OCC_ERR_INVALID_ARG;
         occ_direction(al, &a.view[v].c, &a.view[v].s);
         a.view[v].r = r;
+        choose_layout(a.view[v], H);
+        a.lay_need |= 1 << a.view[v].layout;
         int u = 0;
         while (u < a.nr && a.ratio[u] != r) u++;
         if (u == a.nr) a.ratio[a.nr++] = r;
@@ -207,6 +229,36 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
             return OCC_ERR_CUDA;
         }
         O = ctx->d_O_scratch;
+    }
+
+    // Layout copies: T is W x P, A and B are (W + H - 1) x P floats, P = H rounded up to 32.
+    const int64_t LP = ((int64_t)H + 31) / 32 * 32;
+    const int64_t rows_t = W, rows_ab = (int64_t)W + H - 1;
+    size_t need = 0;
+    int64_t off[kNumLayouts] = {0, 0, 0, 0};
+    for (int l = 1; l < kNumLayouts; l++)
+        if ((a.lay_need >> l) & 1) {
+            off[l] = (int64_t)need;
+            need += sizeof(float) * (size_t)((l == LAYOUT_T ? rows_t : rows_ab) * LP);
+        }
+    if (need > ctx->layout_bytes) {
+        cudaFree(ctx->d_layout);
+        ctx->d_layout = nullptr;
+        ctx->layout_bytes = 0;
+        if (cudaMalloc(&ctx->d_layout, need) != cudaSuccess) {
+            cudaGetLastError();
+            return OCC_ERR_CUDA;
+        }
+        ctx->layout_bytes = need;
+    }
+    a.lay[LAYOUT_ROWS] = D;
+    a.lay_pitch[LAYOUT_ROWS] = pitch;
+    for (int l = 1; l < kNumLayouts; l++) {
+        float* p_l = ((a.lay_need >> l) & 1) ? reinterpret_cast<float*>(reinterpret_cast<char*>(ctx->d_layout) + off[l])
+                                              : nullptr;
+        a.lay[l] = p_l;
+        a.lay_out[l] = p_l;
+        a.lay_pitch[l] = LP;
     }
 
     a.D = D;
@@ -247,11 +299,10 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
     auto mark = [&](int i) { return !prof || cudaEventRecord(ctx->ev[i], st) == cudaSuccess; };
     if (cudaMemsetAsync(ctx->d_hdr, 0, ctx->hdr_bytes, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (!mark(0) || launch_edges(a, grid_edges, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
-    const bool fast = (p.N / 2) <= kFastMaxHalf;
+    if (launch_layout(a, st) != cudaSuccess || !mark(2)) return OCC_ERR_CUDA;
     for (int c = 0; c < kNumClasses; c++) {
-        const int id = (c == 0 && fast) ? kFastClass : c;
-        if (run_cls[c] && launch_scan(a, id, ctx->grid_scan[id], st) != cudaSuccess) return OCC_ERR_CUDA;
-        if (!mark(2 + c)) return OCC_ERR_CUDA;
+        if (run_cls[c] && launch_scan(a, c, ctx->grid_scan[c], st) != cudaSuccess) return OCC_ERR_CUDA;
+        if (!mark(3 + c)) return OCC_ERR_CUDA;
     }
     if (launch_mask(a, ctx->grid_mask, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
     ctx->profiled_call = prof;

@@ -34,13 +34,16 @@ enum : uint32_t {
 // Scan-length classes: one scan kernel instantiation per class, sized by the samples of one scan line (2h+1).
 constexpr int kNumClasses = 3;
 constexpr int kClassCap[kNumClasses] = {256, 1024, 4096};
-// Launch id of the register-resident scan kernel, which replaces class 0 when N <= 2 * kFastMaxHalf.
-constexpr int kFastClass = kNumClasses;
-constexpr int kFastMaxHalf = 4;
+
+// Copies of D the scan kernel gathers from: the view's scan lines run along rows of its layout.
+enum : int { LAYOUT_ROWS = 0, LAYOUT_T = 1, LAYOUT_A = 2, LAYOUT_B = 3, kNumLayouts = 4 };
 
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
     int32_t ridx;    // index of r in Args::ratio
+    int32_t layout;  // LAYOUT_*
+    // Element (row, col) of the layout holding pixel (x, y): row = rpx x + rpy y + r0, col = cpx x + cpy y.
+    int32_t rpx, rpy, r0, cpx, cpy;
 };
 
 struct Args {
@@ -61,15 +64,19 @@ struct Args {
     uint8_t* M;                   // [nv][H][W]
     float* E;                     // [H][W] or null
     float* A;                     // [H][W] or null
+    const float* lay[kNumLayouts];  // LAYOUT_ROWS = D; the others built by k_layout
+    float* lay_out[kNumLayouts];
+    int64_t lay_pitch[kNumLayouts];
+    int32_t lay_need;             // bit l set: layout l is used by some view and must be built
 };
 
 // Launchers (occ_kernels.cu).  Each returns the cudaGetLastError() of its launch.
 cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st);
+cudaError_t launch_layout(const Args& a, cudaStream_t st);
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, int grid, cudaStream_t st);
 // Per-SM resident blocks of each kernel (for persistent grids); also sets the shared-memory opt-ins.
-// scan_blocks_per_sm has kNumClasses + 1 entries (the last for the register-resident kernel).
-cudaError_t configure_kernels(int* edges_blocks_per_sm, int scan_blocks_per_sm[kNumClasses + 1],
+cudaError_t configure_kernels(int* edges_blocks_per_sm, int scan_blocks_per_sm[kNumClasses],
                               int* mask_blocks_per_sm);
 
 }  // namespace occ

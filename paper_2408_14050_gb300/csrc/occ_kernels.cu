@@ -229,32 +229,83 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------------------------------------------------------
-// k_scan: Eq. 4, the warp, the sort and Eq. 5 / Eq. 6 for every candidate, one warp per candidate.
+// k_layout: copies of D in which the scan lines of steep and diagonal views run along rows, so that the gathers of
+// k_scan read consecutive addresses.  T[x][y] = D[y][x] (vertical lines), A[x-y+H-1][y] = D[y][x] (lines along
+// (1,1)), B[x+y][y] = D[y][x] (lines along (-1,1)).  Each block moves one 32x32 output tile through shared memory.
+
+constexpr int kLayoutThreadsX = 32, kLayoutThreadsY = 8;
+
+__global__ void __launch_bounds__(kLayoutThreadsX * kLayoutThreadsY) k_layout(const __grid_constant__ Args a)
+{
+    __shared__ float tile[32][66];
+    const int H = a.H, W = a.W;
+    const int tilesB = (H + 31) / 32;
+    // Blocks are numbered layout by layout: T (if needed), then A, then B.
+    int blk = blockIdx.x, which = -1;
+    for (int l = 1; l <= 3; l++) {
+        if (!((a.lay_need >> l) & 1)) continue;
+        const int rows = (l == 1) ? W : (W + H - 1);
+        const int nt = ((rows + 31) / 32) * tilesB;
+        if (blk < nt) { which = l; break; }
+        blk -= nt;
+    }
+    if (which < 0) return;
+    const int a0 = (blk / tilesB) * 32, b0 = (blk % tilesB) * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t P = a.lay_pitch[which];
+    float* out = a.lay_out[which];
+    const int rows = (which == 1) ? W : (W + H - 1);
+    // Source window: rows b0..b0+31 of D, columns x_start .. x_start + width - 1.
+    const int x_start = (which == 1) ? a0 : (which == 2 ? a0 - H + 1 + b0 : a0 - b0 - 31);
+    const int width = (which == 1) ? 32 : 63;
+    for (int i = ty; i < 32; i += kLayoutThreadsY) {
+        const int y = b0 + i;
+        for (int j = tx; j < width; j += 32) {
+            const int x = x_start + j;
+            tile[i][j] = (y < H && x >= 0 && x < W) ? __ldg(a.D + (int64_t)y * a.pitch + x) : 0.0f;
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += kLayoutThreadsY) {
+        const int row = a0 + r, col = b0 + tx;
+        if (row >= rows || col >= H) continue;
+        const int j = (which == 1) ? r : (which == 2 ? r + tx : r - tx + 31);
+        out[(int64_t)row * P + col] = tile[tx][j];
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------------
+// k_scan: Eq. 4, the warp, the sort and Eq. 5 / Eq. 6, one warp per candidate; lines of up to CAP samples.
 //
-// Sort.  floor(W) is monotone in W, so ordering the samples by (floor(W), W, k) is ordering them by (W, k): the
-// samples are counted into unit-width bins of W (shared-memory atomics), a warp prefix sum turns the counts into
-// bin offsets, and each sample's rank is its bin offset plus the number of samples of its own bin that precede it
-// in (W, k) order (bins hold one to a few samples).  Scan lines whose W span more bins than the buffer holds are
-// sorted by a bitonic network instead.
-//
-// Occlusion test.  For sorted positions r < q = r + d (d <= N/2) with |W_q - W_r| < zeta, sample r is hit when
-// V_r + beta < V_q and sample q when V_q + beta < V_r.  |fl(W_r - W_q)| = |fl(W_q - W_r)|, and because W is sorted
-// the walk of Eq. 5 from either end reaches the pair exactly when the other does, so every pair is tested once,
-// from its lower end; hits on the upper sample go to a shared-memory counter.
+// Gather.  Sample k of the scan line through the candidate lies at the nearest pixel to C + g (cos a, sin a),
+// g = k - h; its depth V = fl(r D) is read from the copy of D in which this view's lines run along rows.
+// Sort.  The valid samples split into maximal runs that are already ordered by (W, k) (a run ends where W drops).
+// A sample of run a precedes, in sorted order, exactly the samples of later runs with smaller W and of earlier
+// runs with W not larger than its own; the rank is its index plus the first count minus the number of samples of
+// earlier runs with larger W.  Runs whose W range does not straddle the sample's W contribute nothing or
+// everything, so only straddling runs need a binary search, and a sample that no other run straddles keeps its
+// index.  A line that is one run is already sorted; a line with more than kMaxRuns runs goes through a bitonic
+// network.
+// Occlusion test (Eq. 5).  Every pair of sorted positions (q, q+d), d <= N/2, is tested once from its lower end:
+// |fl(W_q - W_{q+d})| is symmetric, and |dW| grows with d in sorted order, so the pairs found this way are exactly
+// the ones the walk of Eq. 5 reaches from either end.  q is hit when V_q + beta < V_{q+d}, and q+d when
+// V_{q+d} + beta < V_q; hits on the upper end go to a shared counter.  Eq. 6: the counts are added to O.
+
+constexpr int kMaxRuns = 16;
 
 template <int CAP>
 struct ScanSmem {
-    static constexpr int kBins = 2 * CAP;
-    float uw[CAP];            // W of sample k (scan line order), valid for k in [k0, k0 + n)
-    float uv[CAP];            // V of sample k
-    int32_t upix[CAP];        // y * W + x of sample k
-    int32_t ubs[CAP];         // bin | (arrival slot << 16) of sample i = k - k0
-    int32_t bins[kBins + 1];  // counts, then exclusive offsets (bins[nb] = n)
-    float tw[CAP];            // W in (bin, arrival) order; later the forward-hit counts
-    int32_t ti[CAP];          // sample index in (bin, arrival) order; later the backward-hit counts
-    float sw[CAP];            // W in sorted order
-    float sv[CAP];            // V in sorted order
-    int32_t spix[CAP];        // pixel in sorted order (also the index buffer of the bitonic fallback)
+    float uw[CAP];      // W by k; after the sort, hit counters
+    float uv[CAP];      // V by k; after the sort, hit counters
+    int32_t upix[CAP];  // pixel by k
+    float sw[CAP];      // sorted W (hit counters when the line is one run)
+    float sv[CAP];      // sorted V (hit counters when the line is one run)
+    int32_t spix[CAP];  // sorted pixel (index buffer of the bitonic fallback)
+    int32_t runs[kMaxRuns + 2];
+    float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
+    float run_hi[kMaxRuns + 1];   // last (largest) W of each run
+    float lo_after[kMaxRuns + 2]; // min of run_lo over the runs after run b
+    float hi_before[kMaxRuns + 2];// max of run_hi over the runs before run b
 };
 
 // Number of (p, d) pairs with d in {-K..K}\{0} and 0 <= p+d < n, summed over p (Eq. 5's neighbour set).
@@ -308,38 +359,22 @@ __device__ int scan_views_of_class(const Args& a, int cls, int32_t* s_h, int32_t
     return ncls;
 }
 
-template <int CAP>
-__device__ __forceinline__ void bitonic_sort_warp(ScanSmem<CAP>& S, const float* uw, const float* uv,
-                                                  const int32_t* upix, int n, int lane)
+// First index in [lo, hi) whose value is > x (upper) or >= x (lower); a[lo..hi) is non-decreasing.
+__device__ __forceinline__ int upper_bound_f(const float* a, int lo, int hi, float x)
 {
-    int P = 32;
-    while (P < n) P <<= 1;
-    for (int i = lane; i < P; i += 32) {
-        S.sw[i] = (i < n) ? uw[i] : INFINITY;
-        S.spix[i] = (i < n) ? i : INT_MAX;
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] <= x) lo = m + 1; else hi = m;
     }
-    __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = lane; t < (P >> 1); t += 32) {
-                const int i = 2 * t - (t & (stride - 1));
-                const int j = i + stride;
-                const float wi = S.sw[i], wj = S.sw[j];
-                const int ii = S.spix[i], ij = S.spix[j];
-                const bool gt = (wi > wj) || (wi == wj && ii > ij);
-                if (gt == ((i & size) == 0)) {
-                    S.sw[i] = wj; S.sw[j] = wi;
-                    S.spix[i] = ij; S.spix[j] = ii;
-                }
-            }
-            __syncwarp();
-        }
+    return lo;
+}
+__device__ __forceinline__ int lower_bound_f(const float* a, int lo, int hi, float x)
+{
+    while (lo < hi) {
+        const int m = (lo + hi) >> 1;
+        if (a[m] < x) lo = m + 1; else hi = m;
     }
-    for (int q = lane; q < n; q += 32) {
-        const int idx = S.spix[q];
-        S.sv[q] = uv[idx];
-        S.spix[q] = upix[idx];
-    }
+    return lo;
 }
 
 template <int CAP, int WPB>
@@ -353,7 +388,6 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ScanSmem<CAP>& S = reinterpret_cast<ScanSmem<CAP>*>(smem_raw)[warp];
-
     if (threadIdx.x == 0) s_ncls = scan_views_of_class(a, cls, s_h, s_vid, s_pref);
     __syncthreads();
     const int ncls = s_ncls;
@@ -365,6 +399,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
     const int half = a.N >> 1;
     const float fW = (float)W, fH = (float)H;
     const float beta = a.beta, zeta = a.zeta;
+    const unsigned lt = (1u << lane) - 1u;
 
     int cur_v = -1;
     unsigned long long acc_n = 0, acc_p = 0;
@@ -374,33 +409,33 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         while (item >= s_pref[j + 1]) j++;
         const int v = s_vid[j];
         const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + (int64_t)(item - s_pref[j])];
+        const ViewArg va = a.view[v];
         const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
-        const float c = a.view[v].c, s = a.view[v].s, r = a.view[v].r;
-        const bool one = (r == 1.0f);
+        const bool one = (va.r == 1.0f);
         const int h = s_h[v];
         const int nk = 2 * h + 1;
+        const float* src = a.lay[va.layout];
+        const int64_t P = a.lay_pitch[va.layout];
 
         // Eq. 4: positions, bounds, V = D_r at the nearest pixel, W = g - V.
         int k0 = -1, kl = -1, n = 0;
-        float wmin = INFINITY, wmax = -INFINITY;
         for (int base = 0; base < nk; base += 32) {
             const int k = base + lane;
             bool ok = false;
             if (k < nk) {
                 const float g = (float)(k - h);
-                const float rx = roundf(__fadd_rn(__fmul_rn(c, g), fcx));
-                const float ry = roundf(__fadd_rn(__fmul_rn(s, g), fcy));
+                const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
+                const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
                 ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
                 if (ok) {
                     const int px = (int)rx, py = (int)ry;
-                    const float dv = __ldg(a.D + (int64_t)py * a.pitch + px);
-                    const float V = one ? dv : __fmul_rn(r, dv);
-                    const float Wk = __fsub_rn(g, V);
-                    S.uw[k] = Wk;
+                    const int row = va.rpx * px + va.rpy * py + va.r0;
+                    const int col = va.cpx * px + va.cpy * py;
+                    const float dv = __ldg(src + (int64_t)row * P + col);
+                    const float V = one ? dv : __fmul_rn(va.r, dv);
+                    S.uw[k] = __fsub_rn(g, V);
                     S.uv[k] = V;
                     S.upix[k] = py * W + px;
-                    wmin = fminf(wmin, Wk);
-                    wmax = fmaxf(wmax, Wk);
                 }
             }
             const unsigned b = __ballot_sync(kFull, ok);
@@ -416,97 +451,155 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
             __syncwarp();
             continue;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            wmin = fminf(wmin, __shfl_xor_sync(kFull, wmin, off));
-            wmax = fmaxf(wmax, __shfl_xor_sync(kFull, wmax, off));
-        }
         __syncwarp();
         const float* uw = S.uw + k0;
         const float* uv = S.uv + k0;
         const int32_t* upix = S.upix + k0;
 
-        const float fb0 = floorf(wmin);
-        const float span = __fsub_rn(floorf(wmax), fb0);
-        if (span < (float)ScanSmem<CAP>::kBins) {
-            const int nb = (int)span + 1;
-            for (int b = lane; b < nb; b += 32) S.bins[b] = 0;
-            __syncwarp();
-            // Count every sample into its bin; the returned count is its arrival slot inside the bin.
-            for (int i = lane; i < n; i += 32) {
-                const int b = (int)__fsub_rn(floorf(uw[i]), fb0);
-                const int slot = atomicAdd(&S.bins[b], 1);
-                S.ubs[i] = b | (slot << 16);
+        // Runs: a new run starts after every descent W[i+1] < W[i].
+        int R = 1;
+        for (int base = 0; base < n - 1; base += 32) {
+            const int i = base + lane;
+            const bool dsc = (i < n - 1) && (uw[i + 1] < uw[i]);
+            const unsigned b = __ballot_sync(kFull, dsc);
+            if (dsc) {
+                const int slot = R + __popc(b & lt);
+                if (slot <= kMaxRuns) S.runs[slot] = i + 1;
             }
-            __syncwarp();
-            // Exclusive prefix sum of the bin counts, 32 bins per step.
-            int carry = 0;
-            for (int b0 = 0; b0 < nb; b0 += 32) {
-                const int b = b0 + lane;
-                const int x = (b < nb) ? S.bins[b] : 0;
-                int incl = x;
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, off);
-                    if (lane >= off) incl += y;
-                }
-                if (b < nb) S.bins[b] = carry + incl - x;
-                carry += __shfl_sync(kFull, incl, 31);
-            }
-            if (lane == 0) S.bins[nb] = n;
-            __syncwarp();
-            for (int i = lane; i < n; i += 32) {
-                const int bs = S.ubs[i];
-                const int p = S.bins[bs & 0xFFFF] + (bs >> 16);
-                S.tw[p] = uw[i];
-                S.ti[p] = i;
-            }
-            __syncwarp();
-            // Rank = bin offset + samples of the same bin before this one in (W, k) order (k order = i order).
-            for (int i = lane; i < n; i += 32) {
-                const int b = S.ubs[i] & 0xFFFF;
-                const int st = S.bins[b], en = S.bins[b + 1];
-                const float wi = uw[i];
-                int rank = st;
-                for (int p = st; p < en; p++) {
-                    const float wp = S.tw[p];
-                    rank += (wp < wi) || (wp == wi && S.ti[p] < i);
-                }
-                S.sw[rank] = wi;
-                S.sv[rank] = uv[i];
-                S.spix[rank] = upix[i];
-            }
+            R += __popc(b);
+        }
+
+        const float* sw;
+        const float* sv;
+        const int32_t* spix;
+        int* cnt_own;
+        int* cnt_up;
+        if (R == 1) {
+            sw = uw; sv = uv; spix = upix;
+            cnt_own = reinterpret_cast<int*>(S.sv);
+            cnt_up = reinterpret_cast<int*>(S.sw);
         } else {
-            bitonic_sort_warp<CAP>(S, uw, uv, upix, n, lane);
+            sw = S.sw; sv = S.sv; spix = S.spix;
+            cnt_own = reinterpret_cast<int*>(S.uv);
+            cnt_up = reinterpret_cast<int*>(S.uw);
+            if (R <= kMaxRuns) {
+                if (lane == 0) {
+                    S.runs[0] = 0;
+                    S.runs[R] = n;
+                }
+                __syncwarp();
+                if (lane < R) {
+                    S.run_lo[lane] = uw[S.runs[lane]];
+                    S.run_hi[lane] = uw[S.runs[lane + 1] - 1];
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    float m = INFINITY;
+                    S.lo_after[R] = m;
+                    for (int b = R - 1; b >= 0; b--) {
+                        S.lo_after[b] = m;            // min run_lo over runs b+1 .. R-1
+                        m = fminf(m, S.run_lo[b]);
+                    }
+                    float x = -INFINITY;
+                    for (int b = 0; b < R; b++) {
+                        S.hi_before[b] = x;           // max run_hi over runs 0 .. b-1
+                        x = fmaxf(x, S.run_hi[b]);
+                    }
+                }
+                __syncwarp();
+                for (int i = lane; i < n; i += 32) {
+                    const float wi = uw[i];
+                    int ra = 0;
+                    while (ra + 1 < R && S.runs[ra + 1] <= i) ra++;
+                    int rank = i;
+                    if (S.lo_after[ra] < wi) {        // some later run has smaller W
+                        for (int b = ra + 1; b < R; b++) {
+                            if (S.run_lo[b] >= wi) continue;
+                            const int st = S.runs[b], en = S.runs[b + 1];
+                            rank += (S.run_hi[b] < wi) ? en - st : lower_bound_f(uw, st, en, wi) - st;
+                        }
+                    }
+                    if (S.hi_before[ra] > wi) {       // some earlier run has larger W
+                        for (int b = 0; b < ra; b++) {
+                            if (S.run_hi[b] <= wi) continue;
+                            const int st = S.runs[b], en = S.runs[b + 1];
+                            rank -= (S.run_lo[b] > wi) ? en - st : en - upper_bound_f(uw, st, en, wi);
+                        }
+                    }
+                    S.sw[rank] = wi;
+                    S.sv[rank] = uv[i];
+                    S.spix[rank] = upix[i];
+                }
+            } else {
+                // Many runs: bitonic sort of (W, index) over the next power of two.
+                int Pn = 32;
+                while (Pn < n) Pn <<= 1;
+                for (int i = lane; i < Pn; i += 32) {
+                    S.sw[i] = (i < n) ? uw[i] : INFINITY;
+                    S.spix[i] = (i < n) ? i : INT_MAX;
+                }
+                __syncwarp();
+                for (int size = 2; size <= Pn; size <<= 1) {
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        for (int t = lane; t < (Pn >> 1); t += 32) {
+                            const int i = 2 * t - (t & (stride - 1));
+                            const int jj = i + stride;
+                            const float wi = S.sw[i], wj = S.sw[jj];
+                            const int ii = S.spix[i], ij = S.spix[jj];
+                            const bool gt = (wi > wj) || (wi == wj && ii > ij);
+                            if (gt == ((i & size) == 0)) {
+                                S.sw[i] = wj; S.sw[jj] = wi;
+                                S.spix[i] = ij; S.spix[jj] = ii;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                for (int q = lane; q < n; q += 32) {
+                    const int idx = S.spix[q];
+                    S.sv[q] = uv[idx];
+                    S.spix[q] = upix[idx];
+                }
+            }
         }
         __syncwarp();
 
-        // Eq. 5, each pair once from its lower sorted end; forward hits in tw (as int), backward hits in ti.
-        int* fwd = reinterpret_cast<int*>(S.tw);
-        int* bwd = S.ti;
-        for (int q = lane; q < n; q += 32) bwd[q] = 0;
+        // Eq. 5, every pair once from its lower sorted end.
+        for (int q = lane; q < n; q += 32) cnt_up[q] = 0;
         __syncwarp();
         for (int q = lane; q < n; q += 32) {
-            const float wq = S.sw[q];
-            const float vq = S.sv[q];
+            const float wq = sw[q];
+            const float vq = sv[q];
             const float vbq = __fadd_rn(vq, beta);
             int o = 0;
-            const int dmax = min(half, n - 1 - q);
-            for (int d = 1; d <= dmax; d++) {
-                const float wd = S.sw[q + d];
-                if (!(fabsf(__fsub_rn(wq, wd)) < zeta)) break;
-                const float vd = S.sv[q + d];
-                o += (vbq < vd);
-                if (__fadd_rn(vd, beta) < vq) atomicAdd(&bwd[q + d], 1);
+            if (half <= 4) {
+#pragma unroll
+                for (int d = 1; d <= 4; d++) {
+                    if (d <= half && q + d < n) {
+                        const float wd = sw[q + d];
+                        const float vd = sv[q + d];
+                        const bool close = fabsf(__fsub_rn(wq, wd)) < zeta;
+                        o += (close && vbq < vd) ? 1 : 0;
+                        if (close && __fadd_rn(vd, beta) < vq) atomicAdd(&cnt_up[q + d], 1);
+                    }
+                }
+            } else {
+                for (int d = 1; d <= half && q + d < n; d++) {
+                    const float wd = sw[q + d];
+                    if (!(fabsf(__fsub_rn(wq, wd)) < zeta)) break;
+                    const float vd = sv[q + d];
+                    o += (vbq < vd) ? 1 : 0;
+                    if (__fadd_rn(vd, beta) < vq) atomicAdd(&cnt_up[q + d], 1);
+                }
             }
-            fwd[q] = o;
+            cnt_own[q] = o;
         }
         __syncwarp();
         // Eq. 6: add every sample's count to the occlusion sum of its pixel.
         int32_t* Ov = a.O + (int64_t)v * plane;
         for (int q = lane; q < n; q += 32) {
-            const int o = fwd[q] + bwd[q];
-            if (o) atomicAdd(Ov + S.spix[q], o);
+            const int o = cnt_own[q] + cnt_up[q];
+            if (o) atomicAdd(Ov + spix[q], o);
         }
 
         if (lane == 0) {
@@ -522,252 +615,6 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
             acc_p += pair_count(n, half);
         }
         __syncwarp();
-    }
-    if (lane == 0 && cur_v >= 0) {
-        atomicAdd(&a.stats[2 * cur_v], acc_n);
-        atomicAdd(&a.stats[2 * cur_v + 1], acc_p);
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------------
-// k_scan_fast: the scan kernel for scan lines of at most 256 samples and N <= 8 (the common case), one warp per
-// candidate, with the line held in registers: lane l owns the M = ceil((2h+1)/32) consecutive samples
-// k = l*M .. l*M+M-1.
-//
-// Sort.  The rank of sample i among the valid samples is rank_i = i + #{j > i : W_j < W_i} - #{j < i : W_j > W_i}
-// (ties go to the smaller k).  A suffix minimum and a prefix maximum of W (register scans plus one warp scan) bound
-// both counts: the right count is zero when min(W_{i+1..}) >= W_i and otherwise runs only while that minimum stays
-// below W_i, and symmetrically on the left.  Nearly sorted lines therefore cost two compares per sample, and a
-// line crossing an edge pays only for its actual inversions.
-//
-// Occlusion test.  After the scatter into sorted order each lane reloads M consecutive sorted samples plus the next
-// N/2, and tests every pair (p, p+d), d <= N/2, once: |fl(W_p - W_q)| is symmetric, and in sorted order |dW| only
-// grows with d, so testing every d <= N/2 without stopping counts exactly the neighbours Eq. 5's walk reaches.
-
-struct FastSmem {
-    float w[256];       // W by k
-    float pmax[256];    // prefix max of W by k (-inf outside the valid samples)
-    float smin[256];    // suffix min of W by k (+inf outside the valid samples)
-    float sw[256];      // sorted W
-    float sv[256];      // sorted V
-    int32_t spix[256];  // sorted pixel
-    int32_t ocnt[256];  // hits on a sorted sample from pairs tested by another lane
-};
-
-template <int M>
-__device__ __forceinline__ void line_fast(const Args& a, FastSmem& S, int lane, int v, uint32_t cw, int h,
-                                          int half, int& n_out)
-{
-    const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
-    const float c = a.view[v].c, s = a.view[v].s, r = a.view[v].r;
-    const bool one = (r == 1.0f);
-    const int nk = 2 * h + 1;
-    const float fW = (float)a.W, fH = (float)a.H;
-    const int W = a.W;
-
-    float w[M], vv[M];
-    int pix[M];
-    bool ok[M];
-    int nloc = 0;
-#pragma unroll
-    for (int t = 0; t < M; t++) {
-        const int k = lane * M + t;
-        ok[t] = false;
-        w[t] = INFINITY;
-        vv[t] = 0.0f;
-        pix[t] = 0;
-        if (k < nk) {
-            const float g = (float)(k - h);
-            const float rx = roundf(__fadd_rn(__fmul_rn(c, g), fcx));
-            const float ry = roundf(__fadd_rn(__fmul_rn(s, g), fcy));
-            if ((rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH)) {
-                const int px = (int)rx, py = (int)ry;
-                const float dv = __ldg(a.D + (int64_t)py * a.pitch + px);
-                vv[t] = one ? dv : __fmul_rn(r, dv);
-                w[t] = __fsub_rn(g, vv[t]);
-                pix[t] = py * W + px;
-                ok[t] = true;
-                nloc++;
-            }
-        }
-    }
-    // Valid samples form one interval [k0, k0 + n) of k.
-    int n = nloc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) n += __shfl_xor_sync(kFull, n, off);
-    int k0;
-    {
-        // first valid k: lowest lane with a valid sample, and its first valid slot
-        int myfirst = 1 << 30;
-#pragma unroll
-        for (int t = M - 1; t >= 0; t--)
-            if (ok[t]) myfirst = lane * M + t;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) myfirst = min(myfirst, __shfl_xor_sync(kFull, myfirst, off));
-        k0 = myfirst;
-    }
-    n_out = n;
-    if (n == 0) return;
-
-    // Prefix max (invalid = -inf) and suffix min (invalid = +inf) of W over k.
-    float pm[M], sm[M];
-    float run = -INFINITY;
-#pragma unroll
-    for (int t = 0; t < M; t++) {
-        run = fmaxf(run, ok[t] ? w[t] : -INFINITY);
-        pm[t] = run;
-    }
-    float incl = run;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const float y = __shfl_up_sync(kFull, incl, off);
-        if (lane >= off) incl = fmaxf(incl, y);
-    }
-    float excl = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) excl = -INFINITY;
-#pragma unroll
-    for (int t = 0; t < M; t++) pm[t] = fmaxf(pm[t], excl);
-    run = INFINITY;
-#pragma unroll
-    for (int t = M - 1; t >= 0; t--) {
-        run = fminf(run, ok[t] ? w[t] : INFINITY);
-        sm[t] = run;
-    }
-    incl = run;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const float y = __shfl_down_sync(kFull, incl, off);
-        if (lane + off < 32) incl = fminf(incl, y);
-    }
-    excl = __shfl_down_sync(kFull, incl, 1);
-    if (lane == 31) excl = INFINITY;
-#pragma unroll
-    for (int t = 0; t < M; t++) sm[t] = fminf(sm[t], excl);
-#pragma unroll
-    for (int t = 0; t < M; t++) {
-        const int k = lane * M + t;
-        S.w[k] = w[t];
-        S.pmax[k] = pm[t];
-        S.smin[k] = sm[t];
-    }
-    const float next_sm = __shfl_down_sync(kFull, sm[0], 1);   // smin at k = (lane+1)*M
-    const float prev_pm = __shfl_up_sync(kFull, pm[M - 1], 1);  // pmax at k = lane*M - 1
-    for (int i = lane; i < n; i += 32) S.ocnt[i] = 0;
-    __syncwarp();
-
-    // Rank and scatter into sorted order.
-#pragma unroll
-    for (int t = 0; t < M; t++) {
-        if (!ok[t]) continue;
-        const int k = lane * M + t;
-        const float wi = w[t];
-        int rank = k - k0;
-        const float smn = (t + 1 < M) ? sm[(t + 1 < M) ? t + 1 : 0] : (lane == 31 ? INFINITY : next_sm);
-        if (smn < wi) {
-            for (int j = k + 1; j < 32 * M && S.smin[j] < wi; j++) rank += (S.w[j] < wi);
-        }
-        const float pmx = (t > 0) ? pm[(t > 0) ? t - 1 : 0] : (lane == 0 ? -INFINITY : prev_pm);
-        if (pmx > wi) {
-            for (int j = k - 1; j >= 0 && S.pmax[j] > wi; j--) rank -= (S.w[j] > wi);
-        }
-        S.sw[rank] = wi;
-        S.sv[rank] = vv[t];
-        S.spix[rank] = pix[t];
-    }
-    __syncwarp();
-
-    // Eq. 5 on the sorted samples: lane l tests pairs whose lower end is one of its M positions.
-    const float beta = a.beta, zeta = a.zeta;
-    float w2[M + kFastMaxHalf], v2[M + kFastMaxHalf], vb2[M + kFastMaxHalf];
-#pragma unroll
-    for (int t = 0; t < M + kFastMaxHalf; t++) {
-        const int q = lane * M + t;
-        const bool in = q < n;
-        w2[t] = in ? S.sw[q] : INFINITY;
-        v2[t] = in ? S.sv[q] : 0.0f;
-        vb2[t] = __fadd_rn(v2[t], beta);
-    }
-    int o[M];
-#pragma unroll
-    for (int t = 0; t < M; t++) o[t] = 0;
-#pragma unroll
-    for (int t = 0; t < M; t++) {
-#pragma unroll
-        for (int d = 1; d <= kFastMaxHalf; d++) {
-            if (d > half) break;
-            const bool close = fabsf(__fsub_rn(w2[t], w2[t + d])) < zeta;
-            o[t] += (close && (vb2[t] < v2[t + d])) ? 1 : 0;
-            const bool hitp = close && (vb2[t + d] < v2[t]);
-            if (t + d < M) {
-                o[(t + d < M) ? t + d : 0] += hitp ? 1 : 0;
-            } else if (hitp) {
-                atomicAdd(&S.ocnt[lane * M + t + d], 1);
-            }
-        }
-    }
-    __syncwarp();
-    int32_t* Ov = a.O + (int64_t)v * ((int64_t)a.H * a.W);
-#pragma unroll
-    for (int t = 0; t < M; t++) {
-        const int q = lane * M + t;
-        if (q < n) {
-            const int tot = o[t] + S.ocnt[q];
-            if (tot) atomicAdd(Ov + S.spix[q], tot);
-        }
-    }
-    __syncwarp();
-}
-
-template <int WPB>
-__global__ void __launch_bounds__(WPB * 32) k_scan_fast(const __grid_constant__ Args a)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t s_h[kMaxViews];
-    __shared__ int32_t s_vid[kMaxViews];
-    __shared__ uint32_t s_pref[kMaxViews + 1];
-    __shared__ int s_ncls;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    FastSmem& S = reinterpret_cast<FastSmem*>(smem_raw)[warp];
-    if (threadIdx.x == 0) s_ncls = scan_views_of_class(a, 0, s_h, s_vid, s_pref);
-    __syncthreads();
-    const int ncls = s_ncls;
-    if (ncls == 0) return;
-    const uint32_t total = s_pref[ncls];
-    const int half = a.N >> 1;
-
-    int cur_v = -1;
-    unsigned long long acc_n = 0, acc_p = 0;
-    for (uint64_t item = (uint64_t)blockIdx.x * WPB + warp; item < total; item += (uint64_t)gridDim.x * WPB) {
-        int j = 0;
-        while (item >= s_pref[j + 1]) j++;
-        const int v = s_vid[j];
-        const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + (int64_t)(item - s_pref[j])];
-        const int h = s_h[v];
-        const int M = (2 * h + 1 + 31) >> 5;
-        int n = 0;
-        switch (M) {
-        case 1: line_fast<1>(a, S, lane, v, cw, h, half, n); break;
-        case 2: line_fast<2>(a, S, lane, v, cw, h, half, n); break;
-        case 3: line_fast<3>(a, S, lane, v, cw, h, half, n); break;
-        case 4: line_fast<4>(a, S, lane, v, cw, h, half, n); break;
-        case 5: line_fast<5>(a, S, lane, v, cw, h, half, n); break;
-        case 6: line_fast<6>(a, S, lane, v, cw, h, half, n); break;
-        case 7: line_fast<7>(a, S, lane, v, cw, h, half, n); break;
-        default: line_fast<8>(a, S, lane, v, cw, h, half, n); break;
-        }
-        if (lane == 0) {
-            if (v != cur_v) {
-                if (cur_v >= 0) {
-                    atomicAdd(&a.stats[2 * cur_v], acc_n);
-                    atomicAdd(&a.stats[2 * cur_v + 1], acc_p);
-                }
-                cur_v = v;
-                acc_n = acc_p = 0;
-            }
-            acc_n += (unsigned long long)n;
-            acc_p += pair_count(n, half);
-        }
     }
     if (lane == 0 && cur_v >= 0) {
         atomicAdd(&a.stats[2 * cur_v], acc_n);
@@ -812,15 +659,13 @@ constexpr size_t scan_smem()
     return sizeof(ScanSmem<CAP>) * WPB;
 }
 
-constexpr int kWpb0 = 8, kWpb1 = 4, kWpb2 = 1, kWpbFast = 8;
+constexpr int kWpb0 = 8, kWpb1 = 4, kWpb2 = 2;
 
 }  // namespace
 
 cudaError_t configure_kernels(int* edges_bps, int scan_bps[kNumClasses], int* mask_bps)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_scan_fast<kWpbFast>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(FastSmem) * kWpbFast))) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<256, kWpb0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<256, kWpb0>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<1024, kWpb1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -831,9 +676,6 @@ cudaError_t configure_kernels(int* edges_bps, int scan_bps[kNumClasses], int* ma
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[0], k_scan<256, kWpb0>, kWpb0 * 32,
                                                            scan_smem<256, kWpb0>())) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[kNumClasses], k_scan_fast<kWpbFast>,
-                                                           kWpbFast * 32, sizeof(FastSmem) * kWpbFast)) != cudaSuccess)
-        return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[1], k_scan<1024, kWpb1>, kWpb1 * 32,
                                                            scan_smem<1024, kWpb1>())) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[2], k_scan<4096, kWpb2>, kWpb2 * 32,
@@ -847,10 +689,29 @@ cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
+int layout_blocks(const Args& a)
+{
+    const int tilesB = (a.H + 31) / 32;
+    int n = 0;
+    for (int l = 1; l <= 3; l++) {
+        if (!((a.lay_need >> l) & 1)) continue;
+        const int rows = (l == 1) ? a.W : (a.W + a.H - 1);
+        n += ((rows + 31) / 32) * tilesB;
+    }
+    return n;
+}
+
+cudaError_t launch_layout(const Args& a, cudaStream_t st)
+{
+    const int nb = layout_blocks(a);
+    if (nb == 0) return cudaSuccess;
+    k_layout<<<nb, dim3(kLayoutThreadsX, kLayoutThreadsY), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st)
 {
     switch (cls) {
-    case kFastClass: k_scan_fast<kWpbFast><<<grid, kWpbFast * 32, sizeof(FastSmem) * kWpbFast, st>>>(a); break;
     case 0: k_scan<256, kWpb0><<<grid, kWpb0 * 32, scan_smem<256, kWpb0>(), st>>>(a, 0); break;
     case 1: k_scan<1024, kWpb1><<<grid, kWpb1 * 32, scan_smem<1024, kWpb1>(), st>>>(a, 1); break;
     default: k_scan<4096, kWpb2><<<grid, kWpb2 * 32, scan_smem<4096, kWpb2>(), st>>>(a, 2); break;
