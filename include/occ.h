@@ -161,6 +161,36 @@ int occ_set_profiling(occ_ctx* ctx, int enable);
  * OCC_ERR_INVALID_ARG if no profiled call was made. */
 int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
 
+/* Largest H * W * n_views that occ_detect_noalloc accepts: its fixed scratch holds one candidate entry per pixel and
+ * view (4 bytes each), e.g. one 1920x1080 map with 8 views. */
+#define OCC_NOALLOC_MAX_PIXEL_VIEWS 16777216
+
+/*
+ * occ_detect without a context and without any device allocation, for callers that cannot call cudaMalloc: code
+ * running where the allocator must not be touched (inside a custom allocator or memory-pool callback, a
+ * real-time loop that may not block on allocation or risk fragmentation, a host whose memory budget is fixed and
+ * fully reserved up front, or a framework that hands out only the tensors it manages).  The paper has no counterpart;
+ * this is a deployment variant of the same computation with the same results.
+ *
+ * Its scratch (the status word and per-view counters, 1.6 KB, and the candidate lists, 4 bytes per pixel and view)
+ * is one array of about 64 MiB built into the library: every GPU on which the library is used holds it until the
+ * process exits.  The call itself allocates and frees nothing.  Every call on a device
+ * shares that array and overwrites it, clearing first what must start at zero; two calls that may run at the same
+ * time on the GPU (different streams, or different host threads) race on it and give wrong results, so serialise
+ * them (one stream).  The first call on a device also looks up the array's device address and sets the kernels'
+ * shared-memory limits for that device (once, under a lock, with that device current): make that first call before
+ * any stream capture.
+ *
+ * Arguments are those of occ_detect on the current CUDA device (D, M, O device pointers, views and p host), except:
+ * O is required; there are no E / A outputs; status (device int32, or NULL) receives, in stream order, 0 when the
+ * device found nothing wrong, else a non-zero value (bit 0: non-finite input; bit 2: automatic L above OCC_MAX_SCAN),
+ * in which case M and O are unspecified.  Every view gathers from D directly.  Returns OCC_OK once the work is
+ * queued; OCC_ERR_INVALID_ARG for bad arguments; OCC_ERR_CAPACITY, before any work is queued, when H * W * n_views
+ * exceeds OCC_NOALLOC_MAX_PIXEL_VIEWS; OCC_ERR_CUDA if a launch fails.
+ */
+int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views, int32_t n_views,
+                       const occ_params* p, uint8_t* M, int32_t* O, int32_t* status, void* stream);
+
 /* A static, human-readable name of a status code. */
 const char* occ_status_string(int status);
 

@@ -30,8 +30,11 @@ OCC_MAX_N = 64
 OCC_NUM_STAGES = 6
 STAGES = ["candidates", "layout", "scan_256", "scan_1024", "scan_4096", "mask"]
 
+OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
+
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
-            "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_status_string"]
+            "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc",
+            "occ_status_string"]
 
 
 class occ_view(ctypes.Structure):
@@ -99,6 +102,9 @@ def load(build_if_missing: bool = True):
         L.occ_set_profiling.restype = ctypes.c_int
         L.occ_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
         L.occ_get_timings.restype = ctypes.c_int
+        L.occ_detect_noalloc.argtypes = [vp, i32, i32, i64, ctypes.POINTER(occ_view), i32,
+                                         ctypes.POINTER(occ_params), vp, vp, vp, vp]
+        L.occ_detect_noalloc.restype = ctypes.c_int
         L.occ_status_string.argtypes = [ctypes.c_int]
         L.occ_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -268,3 +274,15 @@ def occ_get_timings(ctx: Context) -> dict:
     if rc != OCC_OK:
         raise OccError(rc, "occ_get_timings")
     return {name: float(ms[i]) for i, name in enumerate(STAGES)}
+
+
+def occ_detect_noalloc(D, views, params: occ_params | None = None, M=None, O=None, status=None, stream=None) -> int:
+    """occ_detect on the current CUDA device without a context and without device allocation by the library (for
+    callers that cannot allocate).  D, M [V][H][W] uint8, O [V][H][W] int32 and status (int32, 1 element, or None)
+    are CUDA tensors owned by the caller.  Returns the host status code; the device status lands in `status`."""
+    if M is None or O is None:
+        raise ValueError("M and O must be given: this entry point allocates nothing")
+    H, W = D.shape
+    return int(load().occ_detect_noalloc(_ptr(D), H, W, D.stride(0), _views(views), len(views),
+                                         ctypes.byref(params) if params is not None else None, _ptr(M), _ptr(O),
+                                         _ptr(status), _stream_handle(stream)))
