@@ -227,7 +227,7 @@ def run_ours(args):
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz", "ops_per_launch": ops}
     else:
         kbytes = {"candidates": 4 * H * W + 4 * H * W * V, "mask": 5 * H * W * V,
-                  "layout": 4 * H * W}.get(dom, step_bytes)
+                  }.get(dom, step_bytes)
         achieved = kbytes / (mean_stage[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": None, "kernel": dom,

@@ -117,12 +117,10 @@ void occ_destroy(occ_ctx* ctx);
  *   M      device, uint8 [n_views][H][W], required: 1 where O > 0, else 0 (Eq. 6).  Fully overwritten.
  *   O      device, int32 [n_views][H][W], 4-byte aligned, or NULL: the occlusion sum of Eq. 5/6 per pixel.  Fully
  *          overwritten.  When NULL the context uses scratch of its own, allocated on the first such call.
- * The context also keeps copies of D laid out along the scan lines of steep and diagonal views; they are
- * (re)allocated by the first call that needs more room than earlier calls did.
  *   E, A   device, binary32 [H][W], or NULL: the edge magnitude and angle maps of D (r = 1), A = atan2(E_y, E_x).
  * The caller owns D, M, O, E and A; none may overlap.  Returns OCC_OK once the work is queued, or
  * OCC_ERR_INVALID_ARG / OCC_ERR_CUDA without queueing anything.  Device-detected errors surface through
- * occ_get_status().  A call that allocates (see O and the layout copies above) must not run under stream capture.
+ * occ_get_status().  A call that allocates (see O above) must not run under stream capture.
  */
 int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views,
                int32_t n_views, const occ_params* p, uint8_t* M, int32_t* O, float* E, float* A, void* stream);
@@ -146,9 +144,10 @@ int occ_get_status(occ_ctx* ctx, void* stream);
  * last stream used.  Returns OCC_ERR_INVALID_ARG if n_views exceeds the views of that call. */
 int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
 
-/* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the copies of D
- * whose rows follow the scan lines of steep and diagonal views, the scan kernels of the three scan-line size
- * classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6), and the mask (Eq. 6). */
+/* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the
+ * line-per-thread scan (Eq. 4-6 for the scan lines whose sort is a set of adjacent swaps; N <= 8), the warp scan
+ * kernels of the three scan-line size classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6 for the remaining
+ * lines), and the mask (Eq. 6). */
 #define OCC_NUM_STAGES 6
 
 /* enable != 0: later occ_detect calls record a CUDA event on their stream before and after each stage, so that
@@ -172,8 +171,8 @@ int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
  * fully reserved up front, or a framework that hands out only the tensors it manages).  The paper has no counterpart;
  * this is a deployment variant of the same computation with the same results.
  *
- * Its scratch (the status word and per-view counters, 1.6 KB, and the candidate lists, 4 bytes per pixel and view)
- * is one array of about 64 MiB built into the library: every GPU on which the library is used holds it until the
+ * Its scratch (the status word and per-view counters, 1.6 KB, a bit per pixel and view, and the candidate lists,
+ * 4 bytes per pixel and view) is one array of about 66 MiB built into the library: every GPU on which the library is used holds it until the
  * process exits.  The call itself allocates and frees nothing.  Every call on a device
  * shares that array and overwrites it, clearing first what must start at zero; two calls that may run at the same
  * time on the GPU (different streams, or different host threads) race on it and give wrong results, so serialise

@@ -28,7 +28,7 @@ OCC_MAX_SIDE = 65535
 OCC_MAX_N = 64
 
 OCC_NUM_STAGES = 6
-STAGES = ["candidates", "layout", "scan_256", "scan_1024", "scan_4096", "mask"]
+STAGES = ["candidates", "scan_lines", "scan_256", "scan_1024", "scan_4096", "mask"]
 
 OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
 

@@ -2,6 +2,7 @@
 // validation, the binary32 direction of each view, the launch sequence of one detect call, status and statistics.
 #include <cmath>
 #include <cstdlib>
+#include <climits>
 #include <cstring>
 #include <new>
 
@@ -25,8 +26,9 @@ struct occ_ctx {
     int32_t* d_O_stage = nullptr;
     int grid_edges = 0, grid_mask = 0;
     int grid_scan[kNumClasses] = {0, 0, 0};
-    float* d_layout = nullptr;                 // T, A, B copies of D, grown on demand
-    size_t layout_bytes = 0;
+    int grid_lines = 0;
+    uint32_t* d_fb = nullptr;                  // [max_views][fb_words] lines left to the warp scan kernel
+    int64_t fb_words = 0;
     int32_t last_nv = 0;
     cudaStream_t last_stream = nullptr;
     bool profiling = false;
@@ -52,23 +54,6 @@ struct DeviceGuard {
 };
 
 bool is_finite_f(float x) { return std::isfinite(x); }
-
-// The copy of D whose rows follow a view's scan lines: rows of D for lines within 22.5 degrees of horizontal, the
-// transpose for lines within 22.5 degrees of vertical, and the two diagonal shears otherwise (y points down, so
-// direction (1, 1) keeps x - y fixed and (-1, 1) keeps x + y fixed).
-void choose_layout(ViewArg& v, int H)
-{
-    double th = std::atan2((double)v.s, (double)v.c) * (180.0 / M_PI);
-    if (th < 0.0) th += 180.0;
-    if (th >= 180.0) th -= 180.0;
-    v.layout = (th < 22.5 || th >= 157.5) ? LAYOUT_ROWS : (th < 67.5 ? LAYOUT_A : (th < 112.5 ? LAYOUT_T : LAYOUT_B));
-    switch (v.layout) {
-    case LAYOUT_T: v.rpx = 1; v.rpy = 0; v.r0 = 0; v.cpx = 0; v.cpy = 1; break;
-    case LAYOUT_A: v.rpx = 1; v.rpy = -1; v.r0 = H - 1; v.cpx = 0; v.cpy = 1; break;
-    case LAYOUT_B: v.rpx = 1; v.rpy = 1; v.r0 = 0; v.cpx = 0; v.cpy = 1; break;
-    default: v.rpx = 0; v.rpy = 1; v.r0 = 0; v.cpx = 1; v.cpy = 0; break;
-    }
-}
 
 }  // namespace
 
@@ -138,7 +123,7 @@ void occ_destroy(occ_ctx* ctx)
         cudaFree(ctx->d_D_stage);
         cudaFree(ctx->d_M_stage);
         cudaFree(ctx->d_O_stage);
-        cudaFree(ctx->d_layout);
+        cudaFree(ctx->d_fb);
         for (int i = 0; i <= OCC_NUM_STAGES; i++)
             if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     }
@@ -164,12 +149,14 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
 
     DeviceGuard g(device);
     if (!g.ok) { delete ctx; return OCC_ERR_CUDA; }
-    int bps_edges = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
+    int bps_edges = 0, bps_lines = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
+    ctx->fb_words = (ctx->cand_cap + 31) / 32;
     ctx->hdr_bytes = sizeof(uint32_t) * HDR_WORDS + sizeof(unsigned long long) * 2 * (size_t)max_views;
     bool ok = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
-              configure_kernels(&bps_edges, bps_scan, &bps_mask) == cudaSuccess &&
+              configure_kernels(&bps_edges, &bps_lines, bps_scan, &bps_mask) == cudaSuccess &&
               cudaMalloc(&ctx->d_hdr, ctx->hdr_bytes) == cudaSuccess &&
               cudaMalloc(&ctx->d_cand, sizeof(uint32_t) * (size_t)ctx->cand_cap * (size_t)max_views) == cudaSuccess &&
+              cudaMalloc(&ctx->d_fb, sizeof(uint32_t) * (size_t)ctx->fb_words * (size_t)max_views) == cudaSuccess &&
               cudaMemset(ctx->d_hdr, 0, ctx->hdr_bytes) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -179,6 +166,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     ctx->d_stats = reinterpret_cast<unsigned long long*>(ctx->d_hdr + HDR_WORDS);
     ctx->grid_edges = ctx->num_sms * (bps_edges > 0 ? bps_edges : 1);
     ctx->grid_mask = ctx->num_sms * (bps_mask > 0 ? bps_mask : 1);
+    ctx->grid_lines = ctx->num_sms * (bps_lines > 0 ? bps_lines : 1);
     for (int c = 0; c < kNumClasses; c++) ctx->grid_scan[c] = ctx->num_sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
     *out = ctx;
     return OCC_OK;
@@ -211,8 +199,6 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
         if (!std::isfinite(al) || !is_finite_f(r) || !(r > 0.0f)) return OCC_ERR_INVALID_ARG;
         occ_direction(al, &a.view[v].c, &a.view[v].s);
         a.view[v].r = r;
-        choose_layout(a.view[v], H);
-        a.lay_need |= 1 << a.view[v].layout;
         int u = 0;
         while (u < a.nr && a.ratio[u] != r) u++;
         if (u == a.nr) a.ratio[a.nr++] = r;
@@ -229,36 +215,6 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
             return OCC_ERR_CUDA;
         }
         O = ctx->d_O_scratch;
-    }
-
-    // Layout copies: T is W x P, A and B are (W + H - 1) x P floats, P = H rounded up to 32.
-    const int64_t LP = ((int64_t)H + 31) / 32 * 32;
-    const int64_t rows_t = W, rows_ab = (int64_t)W + H - 1;
-    size_t need = 0;
-    int64_t off[kNumLayouts] = {0, 0, 0, 0};
-    for (int l = 1; l < kNumLayouts; l++)
-        if ((a.lay_need >> l) & 1) {
-            off[l] = (int64_t)need;
-            need += sizeof(float) * (size_t)((l == LAYOUT_T ? rows_t : rows_ab) * LP);
-        }
-    if (need > ctx->layout_bytes) {
-        cudaFree(ctx->d_layout);
-        ctx->d_layout = nullptr;
-        ctx->layout_bytes = 0;
-        if (cudaMalloc(&ctx->d_layout, need) != cudaSuccess) {
-            cudaGetLastError();
-            return OCC_ERR_CUDA;
-        }
-        ctx->layout_bytes = need;
-    }
-    a.lay[LAYOUT_ROWS] = D;
-    a.lay_pitch[LAYOUT_ROWS] = pitch;
-    for (int l = 1; l < kNumLayouts; l++) {
-        float* p_l = ((a.lay_need >> l) & 1) ? reinterpret_cast<float*>(reinterpret_cast<char*>(ctx->d_layout) + off[l])
-                                              : nullptr;
-        a.lay[l] = p_l;
-        a.lay_out[l] = p_l;
-        a.lay_pitch[l] = LP;
     }
 
     a.D = D;
@@ -295,11 +251,21 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
     const int64_t edge_blocks = (quads + 255) / 256;
     const int grid_edges = (int)(edge_blocks < ctx->grid_edges ? edge_blocks : ctx->grid_edges);
 
+    // Lines go to the line-per-thread kernel first (N/2 <= kLineMaxHalf); the warp kernels then take the lines it
+    // flagged.  Larger N: the warp kernels take every line.
+    const bool lines = (p.N / 2) <= kLineMaxHalf;
+    a.fb = lines ? ctx->d_fb : nullptr;
+    a.fb_words = ctx->fb_words;
+    const bool wide = (int64_t)(H - 1) * pitch + W > (int64_t)INT32_MAX;
+
     const bool prof = ctx->profiling;
     auto mark = [&](int i) { return !prof || cudaEventRecord(ctx->ev[i], st) == cudaSuccess; };
     if (cudaMemsetAsync(ctx->d_hdr, 0, ctx->hdr_bytes, st) != cudaSuccess) return OCC_ERR_CUDA;
+    if (lines && cudaMemsetAsync(ctx->d_fb, 0, sizeof(uint32_t) * (size_t)ctx->fb_words * n_views, st) != cudaSuccess)
+        return OCC_ERR_CUDA;
     if (!mark(0) || launch_edges(a, grid_edges, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
-    if (launch_layout(a, st) != cudaSuccess || !mark(2)) return OCC_ERR_CUDA;
+    if (lines && launch_scan_lines(a, ctx->grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
+    if (!mark(2)) return OCC_ERR_CUDA;
     for (int c = 0; c < kNumClasses; c++) {
         if (run_cls[c] && launch_scan(a, c, ctx->grid_scan[c], st) != cudaSuccess) return OCC_ERR_CUDA;
         if (!mark(3 + c)) return OCC_ERR_CUDA;

@@ -1,5 +1,5 @@
 // occ_internal.cuh -- layout of the context scratch and the launch arguments shared by the kernels
-// (occ_kernels.cu) and the host side of the C ABI (occ_api.cu).  Not part of the public interface.
+// (occ_kernels.cu) and the host side of the C ABI (occ_api.cu, occ_noalloc.cu).  Not part of the public interface.
 #pragma once
 
 #include <cstdint>
@@ -11,8 +11,8 @@ namespace occ {
 
 constexpr int kMaxViews = OCC_MAX_VIEWS;
 
-// Words of the per-context device header (uint32).  The host clears the whole header with one memset at the start
-// of every detect call; the kernels then fill it in stream order.
+// Words of the per-call device header (uint32).  The host clears the header (and the statistics after it) with one
+// memset at the start of every detect call; the kernels then fill it in stream order.
 enum : int {
     HDR_STATUS = 0,                  // status bits (ST_*)
     HDR_MAX = 1,                     // max D, order-preserving encoding (atomicMax)
@@ -31,19 +31,15 @@ enum : uint32_t {
     ST_INTERNAL = 16u,       // a self-check failed (never expected)
 };
 
-// Scan-length classes: one scan kernel instantiation per class, sized by the samples of one scan line (2h+1).
+// Scan-length classes of the warp scan kernel, sized by the samples of one scan line (2h+1).
 constexpr int kNumClasses = 3;
 constexpr int kClassCap[kNumClasses] = {256, 1024, 4096};
-
-// Copies of D the scan kernel gathers from: the view's scan lines run along rows of its layout.
-enum : int { LAYOUT_ROWS = 0, LAYOUT_T = 1, LAYOUT_A = 2, LAYOUT_B = 3, kNumLayouts = 4 };
+// The line-per-thread scan kernel keeps N/2 sorted neighbours in registers; larger N use the warp kernel only.
+constexpr int kLineMaxHalf = 4;
 
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
     int32_t ridx;    // index of r in Args::ratio
-    int32_t layout;  // LAYOUT_*
-    // Element (row, col) of the layout holding pixel (x, y): row = rpx x + rpy y + r0, col = cpx x + cpy y.
-    int32_t rpx, rpy, r0, cpx, cpy;
 };
 
 struct Args {
@@ -58,25 +54,24 @@ struct Args {
     float ratio[kMaxViews];
     uint32_t* cand;               // [nv][cand_cap] packed (y << 16) | x
     int64_t cand_cap;
+    uint32_t* fb;                 // [nv][fb_words] bit per candidate: left to the warp kernel (null: all are)
+    int64_t fb_words;
     uint32_t* hdr;                // HDR_WORDS
     unsigned long long* stats;    // [nv][2]: samples, pair tests
     int32_t* O;                   // [nv][H][W]
     uint8_t* M;                   // [nv][H][W]
     float* E;                     // [H][W] or null
     float* A;                     // [H][W] or null
-    const float* lay[kNumLayouts];  // LAYOUT_ROWS = D; the others built by k_layout
-    float* lay_out[kNumLayouts];
-    int64_t lay_pitch[kNumLayouts];
-    int32_t lay_need;             // bit l set: layout l is used by some view and must be built
 };
 
 // Launchers (occ_kernels.cu).  Each returns the cudaGetLastError() of its launch.
 cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st);
-cudaError_t launch_layout(const Args& a, cudaStream_t st);
+// The line-per-thread scan over every view; wide = true when H * pitch does not fit in int32.
+cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, int grid, cudaStream_t st);
 // Per-SM resident blocks of each kernel (for persistent grids); also sets the shared-memory opt-ins.
-cudaError_t configure_kernels(int* edges_blocks_per_sm, int scan_blocks_per_sm[kNumClasses],
-                              int* mask_blocks_per_sm);
+cudaError_t configure_kernels(int* edges_blocks_per_sm, int* lines_blocks_per_sm,
+                              int scan_blocks_per_sm[kNumClasses], int* mask_blocks_per_sm);
 
 }  // namespace occ

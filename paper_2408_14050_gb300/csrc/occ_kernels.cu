@@ -229,84 +229,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------------------------------------------------------
-// k_layout: copies of D in which the scan lines of steep and diagonal views run along rows, so that the gathers of
-// k_scan read consecutive addresses.  T[x][y] = D[y][x] (vertical lines), A[x-y+H-1][y] = D[y][x] (lines along
-// (1,1)), B[x+y][y] = D[y][x] (lines along (-1,1)).  Each block moves one 32x32 output tile through shared memory.
-
-constexpr int kLayoutThreadsX = 32, kLayoutThreadsY = 8;
-
-__global__ void __launch_bounds__(kLayoutThreadsX * kLayoutThreadsY) k_layout(const __grid_constant__ Args a)
-{
-    __shared__ float tile[32][66];
-    const int H = a.H, W = a.W;
-    const int tilesB = (H + 31) / 32;
-    // Blocks are numbered layout by layout: T (if needed), then A, then B.
-    int blk = blockIdx.x, which = -1;
-    for (int l = 1; l <= 3; l++) {
-        if (!((a.lay_need >> l) & 1)) continue;
-        const int rows = (l == 1) ? W : (W + H - 1);
-        const int nt = ((rows + 31) / 32) * tilesB;
-        if (blk < nt) { which = l; break; }
-        blk -= nt;
-    }
-    if (which < 0) return;
-    const int a0 = (blk / tilesB) * 32, b0 = (blk % tilesB) * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int64_t P = a.lay_pitch[which];
-    float* out = a.lay_out[which];
-    const int rows = (which == 1) ? W : (W + H - 1);
-    // Source window: rows b0..b0+31 of D, columns x_start .. x_start + width - 1.
-    const int x_start = (which == 1) ? a0 : (which == 2 ? a0 - H + 1 + b0 : a0 - b0 - 31);
-    const int width = (which == 1) ? 32 : 63;
-    for (int i = ty; i < 32; i += kLayoutThreadsY) {
-        const int y = b0 + i;
-        for (int j = tx; j < width; j += 32) {
-            const int x = x_start + j;
-            tile[i][j] = (y < H && x >= 0 && x < W) ? __ldg(a.D + (int64_t)y * a.pitch + x) : 0.0f;
-        }
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += kLayoutThreadsY) {
-        const int row = a0 + r, col = b0 + tx;
-        if (row >= rows || col >= H) continue;
-        const int j = (which == 1) ? r : (which == 2 ? r + tx : r - tx + 31);
-        out[(int64_t)row * P + col] = tile[tx][j];
-    }
-}
-
-// ------------------------------------------------------------------------------------------------------------------
-// k_scan: Eq. 4, the warp, the sort and Eq. 5 / Eq. 6, one warp per candidate; lines of up to CAP samples.
-//
-// Gather.  Sample k of the scan line through the candidate lies at the nearest pixel to C + g (cos a, sin a),
-// g = k - h; its depth V = fl(r D) is read from the copy of D in which this view's lines run along rows.
-// Sort.  The valid samples split into maximal runs that are already ordered by (W, k) (a run ends where W drops).
-// A sample of run a precedes, in sorted order, exactly the samples of later runs with smaller W and of earlier
-// runs with W not larger than its own; the rank is its index plus the first count minus the number of samples of
-// earlier runs with larger W.  Runs whose W range does not straddle the sample's W contribute nothing or
-// everything, so only straddling runs need a binary search, and a sample that no other run straddles keeps its
-// index.  A line that is one run is already sorted; a line with more than kMaxRuns runs goes through a bitonic
-// network.
-// Occlusion test (Eq. 5).  Every pair of sorted positions (q, q+d), d <= N/2, is tested once from its lower end:
-// |fl(W_q - W_{q+d})| is symmetric, and |dW| grows with d in sorted order, so the pairs found this way are exactly
-// the ones the walk of Eq. 5 reaches from either end.  q is hit when V_q + beta < V_{q+d}, and q+d when
-// V_{q+d} + beta < V_q; hits on the upper end go to a shared counter.  Eq. 6: the counts are added to O.
-
-constexpr int kMaxRuns = 16;
-
-template <int CAP>
-struct ScanSmem {
-    float uw[CAP];      // W by k; after the sort, hit counters
-    float uv[CAP];      // V by k; after the sort, hit counters
-    int32_t upix[CAP];  // pixel by k
-    float sw[CAP];      // sorted W (hit counters when the line is one run)
-    float sv[CAP];      // sorted V (hit counters when the line is one run)
-    int32_t spix[CAP];  // sorted pixel (index buffer of the bitonic fallback)
-    int32_t runs[kMaxRuns + 2];
-    float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
-    float run_hi[kMaxRuns + 1];   // last (largest) W of each run
-    float lo_after[kMaxRuns + 2]; // min of run_lo over the runs after run b
-    float hi_before[kMaxRuns + 2];// max of run_hi over the runs before run b
-};
+// Shared by the scan kernels.
 
 // Number of (p, d) pairs with d in {-K..K}\{0} and 0 <= p+d < n, summed over p (Eq. 5's neighbour set).
 __device__ __forceinline__ unsigned long long pair_count(int n, int K)
@@ -317,8 +240,9 @@ __device__ __forceinline__ unsigned long long pair_count(int n, int K)
 }
 
 // Thread 0 of a scan block: the scan length of every view (Eq. 3 on D_r unless L is fixed), and the list and
-// candidate-count prefix of the views whose scan lines (2h+1 samples) fall into size class `cls`.  Returns the number
-// of such views.  A view whose automatic L exceeds OCC_MAX_SCAN sets ST_SCAN_TOO_LONG and is skipped.
+// candidate-count prefix of the views whose scan lines (2h+1 samples) fall into size class `cls` (every view when
+// cls < 0).  Returns the number of such views.  A view whose automatic L exceeds OCC_MAX_SCAN sets ST_SCAN_TOO_LONG
+// and is skipped.
 __device__ int scan_views_of_class(const Args& a, int cls, int32_t* s_h, int32_t* s_vid, uint32_t* s_pref)
 {
     const uint32_t st = a.hdr[HDR_STATUS];
@@ -349,7 +273,7 @@ __device__ int scan_views_of_class(const Args& a, int cls, int32_t* s_h, int32_t
         if (blockIdx.x == 0) a.hdr[HDR_L + v] = (uint32_t)L;
         const int nk = 2 * h + 1;
         const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
-        if (c != cls) continue;
+        if (cls >= 0 && c != cls) continue;
         uint32_t cnt = a.hdr[HDR_COUNT + v];
         if ((int64_t)cnt > a.cand_cap) cnt = (uint32_t)a.cand_cap;
         s_vid[ncls] = v;
@@ -358,6 +282,285 @@ __device__ int scan_views_of_class(const Args& a, int cls, int32_t* s_h, int32_t
     }
     return ncls;
 }
+
+// ------------------------------------------------------------------------------------------------------------------
+// k_scan_lines: Eq. 4 - Eq. 6 with one thread per candidate, for N <= 2 * kLineMaxHalf.
+//
+// A one-slot buffer that always emits the smaller of the buffered and the arriving sample turns a sequence into
+// sorted order exactly when no sample has to move back by more than one place -- the usual effect of noise, which
+// lowers a W just below its predecessor's.  A scan line that crosses an edge breaks into a few such stretches
+// ("macro-runs"): where a whole run of foreground samples falls behind the background, the buffer's output would go
+// backwards, and a new macro-run starts there.  The thread walks its line twice:
+//   1. positions, gather of V, W = g - V (Eq. 4 and the warp) for every k: the range of samples inside the image and
+//      the start of the second macro-run.  A line of more than two macro-runs is flagged for the warp scan kernel
+//      (nothing has been added to O yet).
+//   2. the samples again, each macro-run through its own one-slot buffer, the two streams merged by (W, k): this is
+//      the sorted order of the whole line.  Every emitted sample is tested (Eq. 5) against the N/2 samples emitted
+//      just before it, kept in registers with their running counts, each pair once for both of its ends; a sample
+//      whose N/2 successors have all been emitted is final and its count goes to O (Eq. 6).
+
+constexpr int kLineThreads = 256;
+
+struct LineSample {
+    float w, v;
+    int p, k;
+};
+
+template <bool kWide>
+__device__ __forceinline__ bool line_sample(const Args& a, const ViewArg& va, float fcx, float fcy, int h, int k,
+                                            LineSample& out)
+{
+    const float g = (float)(k - h);
+    const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
+    const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
+    if (!((rx >= 0.0f) && (rx < (float)a.W) && (ry >= 0.0f) && (ry < (float)a.H))) return false;
+    const int px = (int)rx, py = (int)ry;
+    const float dv = kWide ? __ldg(a.D + (int64_t)py * a.pitch + px) : __ldg(a.D + (py * (int)a.pitch + px));
+    out.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
+    out.w = __fsub_rn(g, out.v);
+    out.p = py * a.W + px;
+    out.k = k;
+    return true;
+}
+
+__device__ __forceinline__ bool before(const LineSample& x, const LineSample& y)
+{
+    return x.w < y.w || (x.w == y.w && x.k < y.k);
+}
+
+// Pass 1.  Returns the number of macro-runs (1 or 2; 3 means "more than two"), the first and last valid k, the
+// start of the second macro-run and the number of valid samples.
+template <bool kWide>
+__device__ __forceinline__ int line_runs(const Args& a, const ViewArg& va, float fcx, float fcy, int h, int& k0,
+                                         int& k1, int& ksplit, int& n)
+{
+    const int nk = 2 * h + 1;
+    int runs = 0;
+    bool hb = false;
+    LineSample buf{0.f, 0.f, 0, 0}, last{-INFINITY, 0.f, 0, -1}, s;
+    k0 = -1; k1 = -1; ksplit = -1; n = 0;
+    for (int k = 0; k < nk; k++) {
+        if (!line_sample<kWide>(a, va, fcx, fcy, h, k, s)) continue;
+        if (k0 < 0) k0 = k;
+        k1 = k;
+        n++;
+        if (!hb) {
+            hb = true;
+            buf = s;
+            runs = 1;
+            continue;
+        }
+        if (before(s, buf)) {
+            if (before(s, last)) {          // s would be emitted out of order: it starts a new macro-run
+                if (++runs > 2) return 3;
+                ksplit = k;
+                buf = s;
+                last.w = -INFINITY;
+                last.k = -1;
+                continue;
+            }
+            last = s;
+        } else {
+            last = buf;
+            buf = s;
+        }
+    }
+    // The valid samples form one interval of k (positions are monotone in g); if not, the warp kernel reports it.
+    if (n > 0 && k1 - k0 + 1 != n) return 3;
+    return runs;
+}
+
+// Pass 2.  Adds the counts of the line to O.  Each macro-run is read through its own one-slot buffer (a cursor: next
+// k, last k, the buffered sample); the merge emits the smaller head, and the chosen cursor reads at most one sample
+// per step, so every lane of a warp does the same work whichever run it advances.
+template <bool kWide>
+__device__ __forceinline__ void line_counts(const Args& a, const ViewArg& va, int32_t* Ov, float fcx, float fcy,
+                                            int h, int half, int k0, int k1, int ksplit, int runs)
+{
+    const float zeta = a.zeta, beta = a.beta;
+    // Cursor A: [k0, ea]; cursor B: [ksplit, k1] (empty for a single run).  Buffers pre-filled with the first sample.
+    const int ea = (runs == 2) ? ksplit - 1 : k1;
+    int kna = k0 + 1, knb = (runs == 2) ? ksplit + 1 : k1 + 2;
+    const int eb_ = k1;
+    bool hba = true, hbb = (runs == 2);
+    LineSample bufa, bufb{0.f, 0.f, 0, 0}, s;
+    line_sample<kWide>(a, va, fcx, fcy, h, k0, bufa);
+    if (runs == 2) line_sample<kWide>(a, va, fcx, fcy, h, ksplit, bufb);
+    LineSample ha{0.f, 0.f, 0, 0}, hbh{0.f, 0.f, 0, 0};
+    bool has_a = false, has_b = false;
+    // First heads of both cursors.
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        int& kn = c ? knb : kna;
+        const int ke = c ? eb_ : ea;
+        bool& hb = c ? hbb : hba;
+        LineSample& buf = c ? bufb : bufa;
+        LineSample& head = c ? hbh : ha;
+        bool& has = c ? has_b : has_a;
+        if (hb && kn <= ke) {
+            line_sample<kWide>(a, va, fcx, fcy, h, kn, s);
+            kn++;
+            if (before(s, buf)) {
+                head = s;
+            } else {
+                head = buf;
+                buf = s;
+            }
+            has = true;
+        } else if (hb) {
+            head = buf;
+            hb = false;
+            has = true;
+        }
+    }
+    // Window of the last N/2 emitted samples, slot 0 the most recent: W, V, V + beta, pixel, count so far.
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+    float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+    int p0 = 0, p1 = 0, p2 = 0, p3 = 0;
+    int o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+    int wn = 0;
+    while (has_a || has_b) {
+        const bool ta = has_a && (!has_b || before(ha, hbh));
+        const LineSample e = ta ? ha : hbh;
+        // Advance the chosen cursor.
+        int kn = ta ? kna : knb;
+        const int ke = ta ? ea : eb_;
+        bool hb = ta ? hba : hbb;
+        LineSample buf = ta ? bufa : bufb;
+        LineSample head = buf;
+        bool has = false;
+        if (kn <= ke) {
+            line_sample<kWide>(a, va, fcx, fcy, h, kn, s);
+            kn++;
+            const bool sb = before(s, buf);
+            head = sb ? s : buf;
+            if (!sb) buf = s;
+            has = true;
+        } else if (hb) {
+            hb = false;
+            has = true;
+        }
+        if (ta) { kna = kn; hba = hb; bufa = buf; ha = head; has_a = has; }
+        else { knb = kn; hbb = hb; bufb = buf; hbh = head; has_b = has; }
+
+        const float eb = __fadd_rn(e.v, beta);
+        int eo = 0;
+#define OCC_PAIR(J)                                                                                 \
+        if (J < half && wn > J) {                                                                   \
+            const bool close = fabsf(__fsub_rn(e.w, w##J)) < zeta;                                  \
+            eo += (close && eb < v##J) ? 1 : 0;                                                     \
+            o##J += (close && b##J < e.v) ? 1 : 0;                                                  \
+        }
+        OCC_PAIR(0) OCC_PAIR(1) OCC_PAIR(2) OCC_PAIR(3)
+#undef OCC_PAIR
+        // The oldest sample leaves the window once N/2 samples follow it: its count is final.
+        if (wn == half) {
+            const int ol = half == 1 ? o0 : (half == 2 ? o1 : (half == 3 ? o2 : o3));
+            const int pl = half == 1 ? p0 : (half == 2 ? p1 : (half == 3 ? p2 : p3));
+            if (ol) atomicAdd(Ov + pl, ol);
+        } else {
+            wn++;
+        }
+        w3 = w2; v3 = v2; b3 = b2; p3 = p2; o3 = o2;
+        w2 = w1; v2 = v1; b2 = b1; p2 = p1; o2 = o1;
+        w1 = w0; v1 = v0; b1 = b0; p1 = p0; o1 = o0;
+        w0 = e.w; v0 = e.v; b0 = eb; p0 = e.p; o0 = eo;
+    }
+    if (wn > 0 && o0) atomicAdd(Ov + p0, o0);
+    if (wn > 1 && o1) atomicAdd(Ov + p1, o1);
+    if (wn > 2 && o2) atomicAdd(Ov + p2, o2);
+    if (wn > 3 && o3) atomicAdd(Ov + p3, o3);
+}
+
+template <bool kWide>
+__global__ void __launch_bounds__(kLineThreads) k_scan_lines(const __grid_constant__ Args a)
+{
+    __shared__ int32_t s_h[kMaxViews];
+    __shared__ int32_t s_vid[kMaxViews];
+    __shared__ uint32_t s_pref[kMaxViews + 1];
+    __shared__ unsigned long long s_st[2 * kMaxViews];
+    __shared__ int s_ncls;
+    if (threadIdx.x == 0) s_ncls = scan_views_of_class(a, -1, s_h, s_vid, s_pref);
+    for (int i = threadIdx.x; i < 2 * kMaxViews; i += blockDim.x) s_st[i] = 0;
+    __syncthreads();
+    const int ncls = s_ncls;
+    if (ncls == 0) return;
+    const uint32_t total = s_pref[ncls];
+    const int64_t plane = (int64_t)a.H * a.W;
+    const int half = a.N >> 1;
+
+    int cur_v = -1;
+    unsigned long long acc_n = 0, acc_p = 0;
+    for (uint64_t item = (uint64_t)blockIdx.x * kLineThreads + threadIdx.x; item < total;
+         item += (uint64_t)gridDim.x * kLineThreads) {
+        int j = 0;
+        while (item >= s_pref[j + 1]) j++;
+        const int v = s_vid[j];
+        const int64_t idx = (int64_t)(item - s_pref[j]);
+        const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + idx];
+        const ViewArg va = a.view[v];
+        const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
+        int32_t* Ov = a.O + (int64_t)v * plane;
+        const int h = s_h[v];
+        int k0, k1, ksplit, n;
+        const int runs = line_runs<kWide>(a, va, fcx, fcy, h, k0, k1, ksplit, n);
+        if (runs > 2) {
+            atomicOr(&a.fb[(int64_t)v * a.fb_words + (idx >> 5)], 1u << (idx & 31));
+            continue;
+        }
+        if (runs > 0) line_counts<kWide>(a, va, Ov, fcx, fcy, h, half, k0, k1, ksplit, runs);
+        if (v != cur_v) {
+            if (cur_v >= 0) {
+                atomicAdd(&s_st[2 * cur_v], acc_n);
+                atomicAdd(&s_st[2 * cur_v + 1], acc_p);
+            }
+            cur_v = v;
+            acc_n = acc_p = 0;
+        }
+        acc_n += (unsigned long long)n;
+        acc_p += pair_count(n, half);
+    }
+    if (cur_v >= 0) {
+        atomicAdd(&s_st[2 * cur_v], acc_n);
+        atomicAdd(&s_st[2 * cur_v + 1], acc_p);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * a.nv; i += blockDim.x)
+        if (s_st[i]) atomicAdd(&a.stats[i], s_st[i]);
+}
+
+// ------------------------------------------------------------------------------------------------------------------
+// k_scan: Eq. 4 - Eq. 6 with one warp per candidate, for lines of up to CAP samples; any line, any N.  When the
+// line-per-thread kernel ran first, only the candidates it flagged are processed here.
+//
+// Sort.  The valid samples split into maximal runs already ordered by (W, k) (a run ends where W drops).  A sample
+// of run a precedes, in sorted order, exactly the samples of later runs with smaller W and of earlier runs with W
+// not larger than its own; its rank is its index plus the first count minus the number of samples of earlier runs
+// with larger W.  Runs whose W range does not straddle the sample's W contribute nothing or everything, so only
+// straddling runs need a binary search, and a sample that no other run straddles keeps its index.  A line that is
+// one run is already sorted; a line with more than kMaxRuns runs goes through a bitonic network.
+// Occlusion test (Eq. 5).  Every pair of sorted positions (q, q+d), d <= N/2, is tested once from its lower end:
+// |fl(W_q - W_{q+d})| is symmetric, and |dW| grows with d in sorted order, so the pairs found this way are exactly
+// the ones the walk of Eq. 5 reaches from either end.  q is hit when V_q + beta < V_{q+d}, and q+d when
+// V_{q+d} + beta < V_q; hits on the upper end go to a shared counter.  Eq. 6: the counts are added to O.
+
+constexpr int kMaxRuns = 16;
+
+template <int CAP>
+struct ScanSmem {
+    float uw[CAP];      // W by k; after the sort, hit counters
+    float uv[CAP];      // V by k; after the sort, hit counters
+    int32_t upix[CAP];  // pixel by k
+    float sw[CAP];      // sorted W (hit counters when the line is one run)
+    float sv[CAP];      // sorted V (hit counters when the line is one run)
+    int32_t spix[CAP];  // sorted pixel (index buffer of the bitonic fallback)
+    int32_t runs[kMaxRuns + 2];
+    float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
+    float run_hi[kMaxRuns + 1];   // last (largest) W of each run
+    float lo_after[kMaxRuns + 2]; // min of run_lo over the runs after run b
+    float hi_before[kMaxRuns + 2];// max of run_hi over the runs before run b
+};
 
 // First index in [lo, hi) whose value is > x (upper) or >= x (lower); a[lo..hi) is non-decreasing.
 __device__ __forceinline__ int upper_bound_f(const float* a, int lo, int hi, float x)
@@ -408,14 +611,14 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         int j = 0;
         while (item >= s_pref[j + 1]) j++;
         const int v = s_vid[j];
-        const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + (int64_t)(item - s_pref[j])];
+        const int64_t idx = (int64_t)(item - s_pref[j]);
+        if (a.fb && !((a.fb[(int64_t)v * a.fb_words + (idx >> 5)] >> (idx & 31)) & 1u)) continue;
+        const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + idx];
         const ViewArg va = a.view[v];
         const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
         const bool one = (va.r == 1.0f);
         const int h = s_h[v];
         const int nk = 2 * h + 1;
-        const float* src = a.lay[va.layout];
-        const int64_t P = a.lay_pitch[va.layout];
 
         // Eq. 4: positions, bounds, V = D_r at the nearest pixel, W = g - V.
         int k0 = -1, kl = -1, n = 0;
@@ -429,9 +632,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                 ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
                 if (ok) {
                     const int px = (int)rx, py = (int)ry;
-                    const int row = va.rpx * px + va.rpy * py + va.r0;
-                    const int col = va.cpx * px + va.cpy * py;
-                    const float dv = __ldg(src + (int64_t)row * P + col);
+                    const float dv = __ldg(a.D + (int64_t)py * a.pitch + px);
                     const float V = one ? dv : __fmul_rn(va.r, dv);
                     S.uw[k] = __fsub_rn(g, V);
                     S.uv[k] = V;
@@ -663,7 +864,7 @@ constexpr int kWpb0 = 8, kWpb1 = 4, kWpb2 = 2;
 
 }  // namespace
 
-cudaError_t configure_kernels(int* edges_bps, int scan_bps[kNumClasses], int* mask_bps)
+cudaError_t configure_kernels(int* edges_bps, int* lines_bps, int scan_bps[kNumClasses], int* mask_bps)
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_scan<256, kWpb0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -673,6 +874,9 @@ cudaError_t configure_kernels(int* edges_bps, int scan_bps[kNumClasses], int* ma
     if ((e = cudaFuncSetAttribute(k_scan<4096, kWpb2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<4096, kWpb2>())) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(edges_bps, k_edges, kEdgeThreads, 0)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false>, kLineThreads, 0)) !=
+        cudaSuccess)
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[0], k_scan<256, kWpb0>, kWpb0 * 32,
                                                            scan_smem<256, kWpb0>())) != cudaSuccess) return e;
@@ -689,23 +893,10 @@ cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int layout_blocks(const Args& a)
+cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st)
 {
-    const int tilesB = (a.H + 31) / 32;
-    int n = 0;
-    for (int l = 1; l <= 3; l++) {
-        if (!((a.lay_need >> l) & 1)) continue;
-        const int rows = (l == 1) ? a.W : (a.W + a.H - 1);
-        n += ((rows + 31) / 32) * tilesB;
-    }
-    return n;
-}
-
-cudaError_t launch_layout(const Args& a, cudaStream_t st)
-{
-    const int nb = layout_blocks(a);
-    if (nb == 0) return cudaSuccess;
-    k_layout<<<nb, dim3(kLayoutThreadsX, kLayoutThreadsY), 0, st>>>(a);
+    if (wide) k_scan_lines<true><<<grid, kLineThreads, 0, st>>>(a);
+    else k_scan_lines<false><<<grid, kLineThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

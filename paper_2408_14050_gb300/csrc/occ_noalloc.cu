@@ -1,6 +1,7 @@
 // occ_noalloc.cu -- occ_detect_noalloc: the detection of occ_detect for callers that must not allocate device
 // memory (see include/occ.h).  Its scratch is one file-scope device array, sized once at build time; no call here
 // allocates or frees anything.
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -13,11 +14,12 @@ using namespace occ;
 namespace {
 
 // The scratch every call shares: the detection header (status word, min/max of D, per-view counts), the per-view
-// statistics, then the candidate lists, [n_views][H*W] entries of the current call.  One array per device that loads
-// the library; it lives until the process exits.
+// statistics, the bit per candidate marking lines left to the warp kernels, then the candidate lists, [n_views][H*W]
+// entries of the current call.  One array per device that loads the library; it lives until the process exits.
 constexpr size_t kHeaderWords = HDR_WORDS;
 constexpr size_t kStatsWords = 2 * 2 * OCC_MAX_VIEWS;  // [views][2] unsigned long long, counted in uint32 words
-constexpr size_t kScratchWords = kHeaderWords + kStatsWords + (size_t)OCC_NOALLOC_MAX_PIXEL_VIEWS;
+constexpr size_t kFlagWords = OCC_NOALLOC_MAX_PIXEL_VIEWS / 32 + OCC_MAX_VIEWS;
+constexpr size_t kScratchWords = kHeaderWords + kStatsWords + kFlagWords + (size_t)OCC_NOALLOC_MAX_PIXEL_VIEWS;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
@@ -29,6 +31,7 @@ struct DeviceSetup {
     uint32_t* scratch = nullptr;   // device address of g_noalloc_scratch on this device
     int grid_edges = 0, grid_mask = 0;
     int grid_scan[kNumClasses] = {0, 0, 0};
+    int grid_lines = 0;
 };
 
 DeviceSetup g_setup[kMaxDevices];
@@ -39,9 +42,9 @@ void setup_device(int dev, DeviceSetup& s)
 {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    int sms = 0, bps_edges = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
+    int sms = 0, bps_edges = 0, bps_lines = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = configure_kernels(&bps_edges, bps_scan, &bps_mask);
+    if (e == cudaSuccess) e = configure_kernels(&bps_edges, &bps_lines, bps_scan, &bps_mask);
     if (e != cudaSuccess) {
         cudaGetLastError();
         s.err = e;
@@ -50,6 +53,7 @@ void setup_device(int dev, DeviceSetup& s)
     s.scratch = static_cast<uint32_t*>(ptr);
     s.grid_edges = sms * (bps_edges > 0 ? bps_edges : 1);
     s.grid_mask = sms * (bps_mask > 0 ? bps_mask : 1);
+    s.grid_lines = sms * (bps_lines > 0 ? bps_lines : 1);
     for (int c = 0; c < kNumClasses; c++) s.grid_scan[c] = sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
     s.err = cudaSuccess;
 }
@@ -86,9 +90,6 @@ extern "C" int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t 
         if (!std::isfinite(al) || !std::isfinite(r) || !(r > 0.0f)) return OCC_ERR_INVALID_ARG;
         occ_direction(al, &a.view[v].c, &a.view[v].s);
         a.view[v].r = r;
-        // Every view gathers straight from D (rows of D, no relayout copies: those would need memory).
-        a.view[v].layout = LAYOUT_ROWS;
-        a.view[v].rpx = 0; a.view[v].rpy = 1; a.view[v].r0 = 0; a.view[v].cpx = 1; a.view[v].cpy = 0;
         int u = 0;
         while (u < a.nr && a.ratio[u] != r) u++;
         if (u == a.nr) a.ratio[a.nr++] = r;
@@ -116,21 +117,24 @@ extern "C" int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t 
     a.N = p.N;
     a.hdr = hdr;
     a.stats = reinterpret_cast<unsigned long long*>(hdr + kHeaderWords);
-    a.cand = hdr + kHeaderWords + kStatsWords;
+    const bool lines = (p.N / 2) <= kLineMaxHalf;
+    a.fb_words = (plane + 31) / 32;
+    a.fb = lines ? hdr + kHeaderWords + kStatsWords : nullptr;
+    a.cand = hdr + kHeaderWords + kStatsWords + kFlagWords;
     a.cand_cap = plane;
     a.O = O;
     a.M = M;
-    a.lay[LAYOUT_ROWS] = D;
-    a.lay_pitch[LAYOUT_ROWS] = pitch;
-    a.lay_need = 1 << LAYOUT_ROWS;
+    const bool wide = (int64_t)(H - 1) * pitch + W > (int64_t)INT32_MAX;
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    // The header and statistics keep the previous call's values: clear them (the lists need no clearing).
-    if (cudaMemsetAsync(hdr, 0, sizeof(uint32_t) * (kHeaderWords + kStatsWords), st) != cudaSuccess) return OCC_ERR_CUDA;
+    // The header, statistics and line flags keep the previous call's values: clear them (the lists need no clearing).
+    const size_t clear_words = kHeaderWords + kStatsWords + (lines ? (size_t)(a.fb_words * n_views) : 0);
+    if (cudaMemsetAsync(hdr, 0, sizeof(uint32_t) * clear_words, st) != cudaSuccess) return OCC_ERR_CUDA;
     const int64_t quads = (int64_t)H * ((W + 3) / 4);
     const int64_t edge_blocks = (quads + 255) / 256;
     const int grid_edges = (int)(edge_blocks < s.grid_edges ? edge_blocks : s.grid_edges);
     if (launch_edges(a, grid_edges, st) != cudaSuccess) return OCC_ERR_CUDA;
+    if (lines && launch_scan_lines(a, s.grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
     bool run_cls[kNumClasses] = {true, true, true};
     if (a.Lover > 0) {
         const int nk = 2 * ((a.Lover + 1) / 2) + 1;
