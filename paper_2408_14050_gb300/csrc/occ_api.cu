@@ -28,6 +28,7 @@ struct occ_ctx {
     int grid_scan[kNumClasses] = {0, 0, 0};
     int grid_lines = 0;
     uint32_t* d_fb = nullptr;                  // [max_views][fb_words] lines left to the warp scan kernel
+    int32_t* d_ptab = nullptr;                 // [max_views][kTabLen] scan-line position tables
     int64_t fb_words = 0;
     int32_t last_nv = 0;
     cudaStream_t last_stream = nullptr;
@@ -124,6 +125,7 @@ void occ_destroy(occ_ctx* ctx)
         cudaFree(ctx->d_M_stage);
         cudaFree(ctx->d_O_stage);
         cudaFree(ctx->d_fb);
+        cudaFree(ctx->d_ptab);
         for (int i = 0; i <= OCC_NUM_STAGES; i++)
             if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     }
@@ -157,6 +159,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
               cudaMalloc(&ctx->d_hdr, ctx->hdr_bytes) == cudaSuccess &&
               cudaMalloc(&ctx->d_cand, sizeof(uint32_t) * (size_t)ctx->cand_cap * (size_t)max_views) == cudaSuccess &&
               cudaMalloc(&ctx->d_fb, sizeof(uint32_t) * (size_t)ctx->fb_words * (size_t)max_views) == cudaSuccess &&
+              cudaMalloc(&ctx->d_ptab, sizeof(int32_t) * (size_t)kTabLen * (size_t)max_views) == cudaSuccess &&
               cudaMemset(ctx->d_hdr, 0, ctx->hdr_bytes) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -255,6 +258,7 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
     // flagged.  Larger N: the warp kernels take every line.
     const bool lines = (p.N / 2) <= kLineMaxHalf;
     a.fb = lines ? ctx->d_fb : nullptr;
+    a.ptab = ctx->d_ptab;
     a.fb_words = ctx->fb_words;
     const bool wide = (int64_t)(H - 1) * pitch + W > (int64_t)INT32_MAX;
 
@@ -263,7 +267,9 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
     if (cudaMemsetAsync(ctx->d_hdr, 0, ctx->hdr_bytes, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (lines && cudaMemsetAsync(ctx->d_fb, 0, sizeof(uint32_t) * (size_t)ctx->fb_words * n_views, st) != cudaSuccess)
         return OCC_ERR_CUDA;
-    if (!mark(0) || launch_edges(a, grid_edges, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
+    if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, grid_edges, st) != cudaSuccess ||
+        !mark(1))
+        return OCC_ERR_CUDA;
     if (lines && launch_scan_lines(a, ctx->grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (!mark(2)) return OCC_ERR_CUDA;
     for (int c = 0; c < kNumClasses; c++) {

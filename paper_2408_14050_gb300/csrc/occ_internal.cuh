@@ -36,6 +36,9 @@ constexpr int kNumClasses = 3;
 constexpr int kClassCap[kNumClasses] = {256, 1024, 4096};
 // The line-per-thread scan kernel keeps N/2 sorted neighbours in registers; larger N use the warp kernel only.
 constexpr int kLineMaxHalf = 4;
+// Position tables: per view, for g = -kTabHalf .. kTabHalf, round(fl(cos a * g)) and round(fl(sin a * g)).
+constexpr int kTabHalf = (OCC_MAX_SCAN + 1) / 2;
+constexpr int kTabLen = 2 * kTabHalf + 1;
 
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
@@ -54,6 +57,7 @@ struct Args {
     float ratio[kMaxViews];
     uint32_t* cand;               // [nv][cand_cap] packed (y << 16) | x
     int64_t cand_cap;
+    int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact; null: no tables
     uint32_t* fb;                 // [nv][fb_words] bit per candidate: left to the warp kernel (null: all are)
     int64_t fb_words;
     uint32_t* hdr;                // HDR_WORDS
@@ -66,6 +70,7 @@ struct Args {
 
 // Launchers (occ_kernels.cu).  Each returns the cudaGetLastError() of its launch.
 cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st);
+cudaError_t launch_tables(const Args& a, cudaStream_t st);
 // The line-per-thread scan over every view; wide = true when H * pitch does not fit in int32.
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);

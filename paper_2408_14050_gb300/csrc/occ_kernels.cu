@@ -284,20 +284,44 @@ __device__ int scan_views_of_class(const Args& a, int cls, int32_t* s_h, int32_t
 }
 
 // ------------------------------------------------------------------------------------------------------------------
+// k_tables: per view and g = -kTabHalf .. kTabHalf, the offsets round(fl(cos a * g)) and round(fl(sin a * g)) of
+// the scan line's pixel from the candidate.  For a candidate at integer x, round(fl(fl(cos a * g) + x)) equals
+// x + round(fl(cos a * g)) unless fl(cos a * g) lies within half an ulp of x + fl(cos a * g) from a half-integer:
+// that ulp is at most 2^-7 for the coordinates this library accepts (x < 2^16, |g| <= 2047), so entries whose
+// fraction lies within 2^-8 of 0.5 are marked kTabExact and computed without the table.
+
+constexpr int32_t kTabExact = (int32_t)0x80008000;
+
+__global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Args a)
+{
+    const int64_t total = (int64_t)a.nv * kTabLen;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < total; i += (int64_t)gridDim.x * 256) {
+        const int v = (int)(i / kTabLen);
+        const float g = (float)((int)(i - (int64_t)v * kTabLen) - kTabHalf);
+        const float tx = __fmul_rn(a.view[v].c, g), ty = __fmul_rn(a.view[v].s, g);
+        const float fx = tx - floorf(tx), fy = ty - floorf(ty);   // exact: the fraction of a binary32 value
+        const bool risky = fabsf(fx - 0.5f) <= 0.00390625f || fabsf(fy - 0.5f) <= 0.00390625f;
+        const int dx = (int)roundf(tx), dy = (int)roundf(ty);
+        a.ptab[i] = risky ? kTabExact : (int32_t)((uint32_t)(dx & 0xFFFF) | ((uint32_t)dy << 16));
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------------
 // k_scan_lines: Eq. 4 - Eq. 6 with one thread per candidate, for N <= 2 * kLineMaxHalf.
 //
 // A one-slot buffer that always emits the smaller of the buffered and the arriving sample turns a sequence into
 // sorted order exactly when no sample has to move back by more than one place -- the usual effect of noise, which
 // lowers a W just below its predecessor's.  A scan line that crosses an edge breaks into a few such stretches
 // ("macro-runs"): where a whole run of foreground samples falls behind the background, the buffer's output would go
-// backwards, and a new macro-run starts there.  The thread walks its line twice:
-//   1. positions, gather of V, W = g - V (Eq. 4 and the warp) for every k: the range of samples inside the image and
-//      the start of the second macro-run.  A line of more than two macro-runs is flagged for the warp scan kernel
-//      (nothing has been added to O yet).
-//   2. the samples again, each macro-run through its own one-slot buffer, the two streams merged by (W, k): this is
-//      the sorted order of the whole line.  Every emitted sample is tested (Eq. 5) against the N/2 samples emitted
-//      just before it, kept in registers with their running counts, each pair once for both of its ends; a sample
-//      whose N/2 successors have all been emitted is final and its count goes to O (Eq. 6).
+// backwards, and a new macro-run starts there.
+//   Pass 1 (every candidate of a batch): positions, gather of V, W = g - V (Eq. 4 and the warp) for every k; the
+//     range of samples inside the image and the start of the second macro-run.  Lines of more than two macro-runs
+//     are flagged for the warp scan kernel.
+//   Pass 2, single macro-run lines, then two-macro-run lines (compacted, so that each warp runs one kind): the
+//     samples again through one-slot buffers (two buffers merged by (W, k) for two macro-runs), which gives the
+//     sorted order of the line.  Every emitted sample is tested (Eq. 5) against the N/2 samples emitted just before
+//     it, kept in registers with their running counts, each pair once for both of its ends; a sample whose N/2
+//     successors have all been emitted is final and its count goes to O (Eq. 6).
 
 constexpr int kLineThreads = 256;
 
@@ -306,15 +330,32 @@ struct LineSample {
     int p, k;
 };
 
+struct LineJob {
+    int x, y;       // candidate
+    int v;          // view
+    int k0, k1;     // first / last k inside the image
+    int ks;         // start of the second macro-run
+};
+
+// Sample k of a line; `bounded` = false when k is known to lie inside the image.
 template <bool kWide>
-__device__ __forceinline__ bool line_sample(const Args& a, const ViewArg& va, float fcx, float fcy, int h, int k,
-                                            LineSample& out)
+__device__ __forceinline__ bool line_sample(const Args& a, const ViewArg& va, const int32_t* tab, int cx, int cy,
+                                            int h, int k, bool bounded, LineSample& out)
 {
+    const int t = tab[k - h + kTabHalf];
+    int px, py;
     const float g = (float)(k - h);
-    const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
-    const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
-    if (!((rx >= 0.0f) && (rx < (float)a.W) && (ry >= 0.0f) && (ry < (float)a.H))) return false;
-    const int px = (int)rx, py = (int)ry;
+    if (t != kTabExact) {
+        px = cx + (int)(int16_t)(t & 0xFFFF);
+        py = cy + (t >> 16);
+    } else {
+        const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
+        const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
+        if (bounded && !((rx >= 0.0f) && (rx < (float)a.W) && (ry >= 0.0f) && (ry < (float)a.H))) return false;
+        px = (int)rx;
+        py = (int)ry;
+    }
+    if (bounded && !((unsigned)px < (unsigned)a.W && (unsigned)py < (unsigned)a.H)) return false;
     const float dv = kWide ? __ldg(a.D + (int64_t)py * a.pitch + px) : __ldg(a.D + (py * (int)a.pitch + px));
     out.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
     out.w = __fsub_rn(g, out.v);
@@ -328,24 +369,22 @@ __device__ __forceinline__ bool before(const LineSample& x, const LineSample& y)
     return x.w < y.w || (x.w == y.w && x.k < y.k);
 }
 
-// Pass 1.  Returns the number of macro-runs (1 or 2; 3 means "more than two"), the first and last valid k, the
-// start of the second macro-run and the number of valid samples.
+// Pass 1.  Returns the number of macro-runs (1 or 2; 3 means "more than two" or a gap in the valid range), the
+// first and last valid k, the start of the second macro-run and the number of valid samples.
 template <bool kWide>
-__device__ __forceinline__ int line_runs(const Args& a, const ViewArg& va, float fcx, float fcy, int h, int& k0,
-                                         int& k1, int& ksplit, int& n)
+__device__ __forceinline__ int line_runs(const Args& a, const ViewArg& va, const int32_t* tab, int cx, int cy, int h,
+                                         int& k0, int& k1, int& ks, int& n)
 {
     const int nk = 2 * h + 1;
     int runs = 0;
-    bool hb = false;
     LineSample buf{0.f, 0.f, 0, 0}, last{-INFINITY, 0.f, 0, -1}, s;
-    k0 = -1; k1 = -1; ksplit = -1; n = 0;
+    k0 = -1; k1 = -1; ks = -1; n = 0;
     for (int k = 0; k < nk; k++) {
-        if (!line_sample<kWide>(a, va, fcx, fcy, h, k, s)) continue;
+        if (!line_sample<kWide>(a, va, tab, cx, cy, h, k, true, s)) continue;
         if (k0 < 0) k0 = k;
         k1 = k;
         n++;
-        if (!hb) {
-            hb = true;
+        if (runs == 0) {
             buf = s;
             runs = 1;
             continue;
@@ -353,7 +392,7 @@ __device__ __forceinline__ int line_runs(const Args& a, const ViewArg& va, float
         if (before(s, buf)) {
             if (before(s, last)) {          // s would be emitted out of order: it starts a new macro-run
                 if (++runs > 2) return 3;
-                ksplit = k;
+                ks = k;
                 buf = s;
                 last.w = -INFINITY;
                 last.k = -1;
@@ -370,116 +409,276 @@ __device__ __forceinline__ int line_runs(const Args& a, const ViewArg& va, float
     return runs;
 }
 
-// Pass 2.  Adds the counts of the line to O.  Each macro-run is read through its own one-slot buffer (a cursor: next
-// k, last k, the buffered sample); the merge emits the smaller head, and the chosen cursor reads at most one sample
-// per step, so every lane of a warp does the same work whichever run it advances.
-template <bool kWide>
-__device__ __forceinline__ void line_counts(const Args& a, const ViewArg& va, int32_t* Ov, float fcx, float fcy,
-                                            int h, int half, int k0, int k1, int ksplit, int runs)
+// Eq. 5 / Eq. 6 over the emitted (sorted) stream: a window of the last N/2 samples, slot 0 the most recent.
+struct LineWindow {
+    float w0, w1, w2, w3, v0, v1, v2, v3, b0, b1, b2, b3;
+    int p0, p1, p2, p3, o0, o1, o2, o3;
+    int wn;
+};
+
+__device__ __forceinline__ void window_init(LineWindow& W)
 {
-    const float zeta = a.zeta, beta = a.beta;
-    // Cursor A: [k0, ea]; cursor B: [ksplit, k1] (empty for a single run).  Buffers pre-filled with the first sample.
-    const int ea = (runs == 2) ? ksplit - 1 : k1;
-    int kna = k0 + 1, knb = (runs == 2) ? ksplit + 1 : k1 + 2;
-    const int eb_ = k1;
-    bool hba = true, hbb = (runs == 2);
-    LineSample bufa, bufb{0.f, 0.f, 0, 0}, s;
-    line_sample<kWide>(a, va, fcx, fcy, h, k0, bufa);
-    if (runs == 2) line_sample<kWide>(a, va, fcx, fcy, h, ksplit, bufb);
-    LineSample ha{0.f, 0.f, 0, 0}, hbh{0.f, 0.f, 0, 0};
-    bool has_a = false, has_b = false;
-    // First heads of both cursors.
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        int& kn = c ? knb : kna;
-        const int ke = c ? eb_ : ea;
-        bool& hb = c ? hbb : hba;
-        LineSample& buf = c ? bufb : bufa;
-        LineSample& head = c ? hbh : ha;
-        bool& has = c ? has_b : has_a;
-        if (hb && kn <= ke) {
-            line_sample<kWide>(a, va, fcx, fcy, h, kn, s);
-            kn++;
-            if (before(s, buf)) {
-                head = s;
-            } else {
-                head = buf;
-                buf = s;
-            }
-            has = true;
-        } else if (hb) {
-            head = buf;
-            hb = false;
-            has = true;
-        }
+    W.w0 = W.w1 = W.w2 = W.w3 = 0.f;
+    W.v0 = W.v1 = W.v2 = W.v3 = 0.f;
+    W.b0 = W.b1 = W.b2 = W.b3 = 0.f;
+    W.p0 = W.p1 = W.p2 = W.p3 = 0;
+    W.o0 = W.o1 = W.o2 = W.o3 = 0;
+    W.wn = 0;
+}
+
+__device__ __forceinline__ void window_push(LineWindow& W, const LineSample& e, int half, float zeta, float beta,
+                                            int32_t* Ov)
+{
+    const float eb = __fadd_rn(e.v, beta);
+    int eo = 0;
+#define OCC_PAIR(J)                                                                                 \
+    if (J < half && W.wn > J) {                                                                     \
+        const bool close = fabsf(__fsub_rn(e.w, W.w##J)) < zeta;                                    \
+        eo += (close && eb < W.v##J) ? 1 : 0;                                                       \
+        W.o##J += (close && W.b##J < e.v) ? 1 : 0;                                                  \
     }
-    // Window of the last N/2 emitted samples, slot 0 the most recent: W, V, V + beta, pixel, count so far.
-    float w0 = 0.f, w1 = 0.f, w2 = 0.f, w3 = 0.f;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
-    float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
-    int p0 = 0, p1 = 0, p2 = 0, p3 = 0;
-    int o0 = 0, o1 = 0, o2 = 0, o3 = 0;
-    int wn = 0;
+    OCC_PAIR(0) OCC_PAIR(1) OCC_PAIR(2) OCC_PAIR(3)
+#undef OCC_PAIR
+    // The oldest sample leaves the window once N/2 samples follow it: its count is final.
+    if (W.wn == half) {
+        const int ol = half == 1 ? W.o0 : (half == 2 ? W.o1 : (half == 3 ? W.o2 : W.o3));
+        const int pl = half == 1 ? W.p0 : (half == 2 ? W.p1 : (half == 3 ? W.p2 : W.p3));
+        if (ol) atomicAdd(Ov + pl, ol);
+    } else {
+        W.wn++;
+    }
+    W.w3 = W.w2; W.v3 = W.v2; W.b3 = W.b2; W.p3 = W.p2; W.o3 = W.o2;
+    W.w2 = W.w1; W.v2 = W.v1; W.b2 = W.b1; W.p2 = W.p1; W.o2 = W.o1;
+    W.w1 = W.w0; W.v1 = W.v0; W.b1 = W.b0; W.p1 = W.p0; W.o1 = W.o0;
+    W.w0 = e.w; W.v0 = e.v; W.b0 = eb; W.p0 = e.p; W.o0 = eo;
+}
+
+__device__ __forceinline__ void window_flush(const LineWindow& W, int32_t* Ov)
+{
+    if (W.wn > 0 && W.o0) atomicAdd(Ov + W.p0, W.o0);
+    if (W.wn > 1 && W.o1) atomicAdd(Ov + W.p1, W.o1);
+    if (W.wn > 2 && W.o2) atomicAdd(Ov + W.p2, W.o2);
+    if (W.wn > 3 && W.o3) atomicAdd(Ov + W.p3, W.o3);
+}
+
+// Pass 2 for a single macro-run [k0, k1].
+template <bool kWide>
+__device__ __forceinline__ void line_counts1(const Args& a, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
+                                             int cy, int h, int half, int k0, int k1)
+{
+    LineWindow Wn;
+    window_init(Wn);
+    LineSample buf, s;
+    line_sample<kWide>(a, va, tab, cx, cy, h, k0, false, buf);
+    for (int k = k0 + 1; k <= k1; k++) {
+        line_sample<kWide>(a, va, tab, cx, cy, h, k, false, s);
+        const bool sb = before(s, buf);
+        const LineSample e = sb ? s : buf;
+        if (!sb) buf = s;
+        window_push(Wn, e, half, a.zeta, a.beta, Ov);
+    }
+    window_push(Wn, buf, half, a.zeta, a.beta, Ov);
+    window_flush(Wn, Ov);
+}
+
+// Pass 2 for two macro-runs [k0, ks - 1] and [ks, k1], each read through its own one-slot buffer; the merge emits
+// the smaller head, and the chosen run reads at most one sample per step.
+template <bool kWide>
+__device__ __forceinline__ void line_counts2(const Args& a, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
+                                             int cy, int h, int half, int k0, int k1, int ks)
+{
+    LineWindow Wn;
+    window_init(Wn);
+    // Run A: next k, last k, buffer, head; run B likewise.
+    int kna = k0 + 1, knb = ks + 1;
+    const int ea = ks - 1, eb = k1;
+    LineSample bufa, bufb, ha, hb, s;
+    bool hba = true, hbb = true;
+    line_sample<kWide>(a, va, tab, cx, cy, h, k0, false, bufa);
+    line_sample<kWide>(a, va, tab, cx, cy, h, ks, false, bufb);
+    bool has_a = true, has_b = true;
+    // First heads.
+    if (kna <= ea) {
+        line_sample<kWide>(a, va, tab, cx, cy, h, kna++, false, s);
+        if (before(s, bufa)) ha = s; else { ha = bufa; bufa = s; }
+    } else {
+        ha = bufa;
+        hba = false;
+    }
+    if (knb <= eb) {
+        line_sample<kWide>(a, va, tab, cx, cy, h, knb++, false, s);
+        if (before(s, bufb)) hb = s; else { hb = bufb; bufb = s; }
+    } else {
+        hb = bufb;
+        hbb = false;
+    }
     while (has_a || has_b) {
-        const bool ta = has_a && (!has_b || before(ha, hbh));
-        const LineSample e = ta ? ha : hbh;
-        // Advance the chosen cursor.
+        const bool ta = has_a && (!has_b || before(ha, hb));
+        const LineSample e = ta ? ha : hb;
         int kn = ta ? kna : knb;
-        const int ke = ta ? ea : eb_;
-        bool hb = ta ? hba : hbb;
+        const int ke = ta ? ea : eb;
+        bool hbuf = ta ? hba : hbb;
         LineSample buf = ta ? bufa : bufb;
         LineSample head = buf;
         bool has = false;
         if (kn <= ke) {
-            line_sample<kWide>(a, va, fcx, fcy, h, kn, s);
+            line_sample<kWide>(a, va, tab, cx, cy, h, kn, false, s);
             kn++;
             const bool sb = before(s, buf);
             head = sb ? s : buf;
             if (!sb) buf = s;
             has = true;
-        } else if (hb) {
-            hb = false;
+        } else if (hbuf) {
+            hbuf = false;
             has = true;
         }
-        if (ta) { kna = kn; hba = hb; bufa = buf; ha = head; has_a = has; }
-        else { knb = kn; hbb = hb; bufb = buf; hbh = head; has_b = has; }
-
-        const float eb = __fadd_rn(e.v, beta);
-        int eo = 0;
-#define OCC_PAIR(J)                                                                                 \
-        if (J < half && wn > J) {                                                                   \
-            const bool close = fabsf(__fsub_rn(e.w, w##J)) < zeta;                                  \
-            eo += (close && eb < v##J) ? 1 : 0;                                                     \
-            o##J += (close && b##J < e.v) ? 1 : 0;                                                  \
-        }
-        OCC_PAIR(0) OCC_PAIR(1) OCC_PAIR(2) OCC_PAIR(3)
-#undef OCC_PAIR
-        // The oldest sample leaves the window once N/2 samples follow it: its count is final.
-        if (wn == half) {
-            const int ol = half == 1 ? o0 : (half == 2 ? o1 : (half == 3 ? o2 : o3));
-            const int pl = half == 1 ? p0 : (half == 2 ? p1 : (half == 3 ? p2 : p3));
-            if (ol) atomicAdd(Ov + pl, ol);
-        } else {
-            wn++;
-        }
-        w3 = w2; v3 = v2; b3 = b2; p3 = p2; o3 = o2;
-        w2 = w1; v2 = v1; b2 = b1; p2 = p1; o2 = o1;
-        w1 = w0; v1 = v0; b1 = b0; p1 = p0; o1 = o0;
-        w0 = e.w; v0 = e.v; b0 = eb; p0 = e.p; o0 = eo;
+        if (ta) { kna = kn; hba = hbuf; bufa = buf; ha = head; has_a = has; }
+        else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; }
+        window_push(Wn, e, half, a.zeta, a.beta, Ov);
     }
-    if (wn > 0 && o0) atomicAdd(Ov + p0, o0);
-    if (wn > 1 && o1) atomicAdd(Ov + p1, o1);
-    if (wn > 2 && o2) atomicAdd(Ov + p2, o2);
-    if (wn > 3 && o3) atomicAdd(Ov + p3, o3);
+    window_flush(Wn, Ov);
+}
+
+// Pass 1 with the next sample's load issued before the current one is used.
+template <bool kWide>
+__device__ __forceinline__ int line_runs_p(const Args& a, const ViewArg& va, const int32_t* tab, int cx, int cy, int h,
+                                           int& k0, int& k1, int& ks, int& n)
+{
+    const int nk = 2 * h + 1;
+    int runs = 0;
+    LineSample buf{0.f, 0.f, 0, 0}, last{-INFINITY, 0.f, 0, -1};
+    k0 = -1; k1 = -1; ks = -1; n = 0;
+    // Position of sample k: pixel index and element offset in D (pixel -1 outside the image).
+    auto pos = [&](int k, int& pix, int64_t& off) {
+        const int t = tab[k - h + kTabHalf];
+        int px, py;
+        pix = -1;
+        off = 0;
+        if (t != kTabExact) {
+            px = cx + (int)(int16_t)(t & 0xFFFF);
+            py = cy + (t >> 16);
+        } else {
+            const float g = (float)(k - h);
+            const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
+            const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
+            if (!((rx >= 0.0f) && (rx < (float)a.W) && (ry >= 0.0f) && (ry < (float)a.H))) return;
+            px = (int)rx;
+            py = (int)ry;
+        }
+        if (!((unsigned)px < (unsigned)a.W && (unsigned)py < (unsigned)a.H)) return;
+        pix = py * a.W + px;
+        off = kWide ? (int64_t)py * a.pitch + px : (int64_t)(py * (int)a.pitch + px);
+    };
+    int pn;
+    int64_t on;
+    pos(0, pn, on);
+    float dn = (pn >= 0) ? __ldg(a.D + on) : 0.0f;
+    for (int k = 0; k < nk; k++) {
+        const int p = pn;
+        const float dv = dn;
+        if (k + 1 < nk) {
+            pos(k + 1, pn, on);
+            dn = (pn >= 0) ? __ldg(a.D + on) : 0.0f;
+        }
+        if (p < 0) continue;
+        LineSample s;
+        s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
+        s.w = __fsub_rn((float)(k - h), s.v);
+        s.p = p;
+        s.k = k;
+        if (k0 < 0) k0 = k;
+        k1 = k;
+        n++;
+        if (runs == 0) {
+            buf = s;
+            runs = 1;
+            continue;
+        }
+        if (before(s, buf)) {
+            if (before(s, last)) {          // s would be emitted out of order: it starts a new macro-run
+                if (++runs > 2) return 3;
+                ks = k;
+                buf = s;
+                last.w = -INFINITY;
+                last.k = -1;
+                continue;
+            }
+            last = s;
+        } else {
+            last = buf;
+            buf = s;
+        }
+    }
+    // The valid samples form one interval of k (positions are monotone in g); if not, the warp kernel reports it.
+    if (n > 0 && k1 - k0 + 1 != n) return 3;
+    return runs;
+}
+
+// Pass 2 for a single macro-run [k0, k1], loads one sample ahead.
+template <bool kWide>
+__device__ __forceinline__ void line_counts1_p(const Args& a, const ViewArg& va, const int32_t* tab, int32_t* Ov,
+                                               int cx, int cy, int h, int half, int k0, int k1)
+{
+    LineWindow Wn;
+    window_init(Wn);
+    auto pos = [&](int k, int& pix, int64_t& off) {
+        const int t = tab[k - h + kTabHalf];
+        int px, py;
+        if (t != kTabExact) {
+            px = cx + (int)(int16_t)(t & 0xFFFF);
+            py = cy + (t >> 16);
+        } else {
+            const float g = (float)(k - h);
+            px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
+            py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
+        }
+        pix = py * a.W + px;
+        off = kWide ? (int64_t)py * a.pitch + px : (int64_t)(py * (int)a.pitch + px);
+    };
+    auto make = [&](int k, int p, float dv) -> LineSample {
+        LineSample s;
+        s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
+        s.w = __fsub_rn((float)(k - h), s.v);
+        s.p = p;
+        s.k = k;
+        return s;
+    };
+    int pn;
+    int64_t on;
+    pos(k0, pn, on);
+    float dn = __ldg(a.D + on);
+    LineSample buf = make(k0, pn, dn);
+    if (k0 + 1 <= k1) {
+        pos(k0 + 1, pn, on);
+        dn = __ldg(a.D + on);
+    }
+    for (int k = k0 + 1; k <= k1; k++) {
+        const int p = pn;
+        const float dv = dn;
+        if (k + 1 <= k1) {
+            pos(k + 1, pn, on);
+            dn = __ldg(a.D + on);
+        }
+        const LineSample s = make(k, p, dv);
+        const bool sb = before(s, buf);
+        const LineSample e = sb ? s : buf;
+        if (!sb) buf = s;
+        window_push(Wn, e, half, a.zeta, a.beta, Ov);
+    }
+    window_push(Wn, buf, half, a.zeta, a.beta, Ov);
+    window_flush(Wn, Ov);
 }
 
 template <bool kWide>
 __global__ void __launch_bounds__(kLineThreads) k_scan_lines(const __grid_constant__ Args a)
 {
+    constexpr int kWarps = kLineThreads / 32;
+    constexpr int kQ = 64;                  // per-warp queue of jobs of each kind
     __shared__ int32_t s_h[kMaxViews];
     __shared__ int32_t s_vid[kMaxViews];
     __shared__ uint32_t s_pref[kMaxViews + 1];
     __shared__ unsigned long long s_st[2 * kMaxViews];
+    __shared__ LineJob s_q[kWarps][2][kQ];
     __shared__ int s_ncls;
     if (threadIdx.x == 0) s_ncls = scan_views_of_class(a, -1, s_h, s_vid, s_pref);
     for (int i = threadIdx.x; i < 2 * kMaxViews; i += blockDim.x) s_st[i] = 0;
@@ -489,38 +688,77 @@ __global__ void __launch_bounds__(kLineThreads) k_scan_lines(const __grid_consta
     const uint32_t total = s_pref[ncls];
     const int64_t plane = (int64_t)a.H * a.W;
     const int half = a.N >> 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    LineJob* q1 = s_q[warp][0];
+    LineJob* q2 = s_q[warp][1];
+    int n1 = 0, n2 = 0;   // queue lengths (warp-uniform)
+
+    auto run1 = [&](const LineJob& jb) {
+        line_counts1_p<kWide>(a, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen, a.O + (int64_t)jb.v * plane, jb.x,
+                              jb.y, s_h[jb.v], half, jb.k0, jb.k1);
+    };
+    auto run2 = [&](const LineJob& jb) {
+        line_counts2<kWide>(a, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen, a.O + (int64_t)jb.v * plane, jb.x,
+                            jb.y, s_h[jb.v], half, jb.k0, jb.k1, jb.ks);
+    };
 
     int cur_v = -1;
     unsigned long long acc_n = 0, acc_p = 0;
-    for (uint64_t item = (uint64_t)blockIdx.x * kLineThreads + threadIdx.x; item < total;
-         item += (uint64_t)gridDim.x * kLineThreads) {
-        int j = 0;
-        while (item >= s_pref[j + 1]) j++;
-        const int v = s_vid[j];
-        const int64_t idx = (int64_t)(item - s_pref[j]);
-        const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + idx];
-        const ViewArg va = a.view[v];
-        const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
-        int32_t* Ov = a.O + (int64_t)v * plane;
-        const int h = s_h[v];
-        int k0, k1, ksplit, n;
-        const int runs = line_runs<kWide>(a, va, fcx, fcy, h, k0, k1, ksplit, n);
-        if (runs > 2) {
-            atomicOr(&a.fb[(int64_t)v * a.fb_words + (idx >> 5)], 1u << (idx & 31));
-            continue;
-        }
-        if (runs > 0) line_counts<kWide>(a, va, Ov, fcx, fcy, h, half, k0, k1, ksplit, runs);
-        if (v != cur_v) {
-            if (cur_v >= 0) {
-                atomicAdd(&s_st[2 * cur_v], acc_n);
-                atomicAdd(&s_st[2 * cur_v + 1], acc_p);
+    const uint64_t stride = (uint64_t)gridDim.x * kLineThreads;
+    for (uint64_t b0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; b0 < total; b0 += stride) {
+        // Pass 1 for 32 lines, one per lane.
+        const uint64_t item = b0 + lane;
+        int runs = 0;
+        LineJob jb{0, 0, 0, 0, 0, 0};
+        if (item < total) {
+            int j = 0;
+            while (item >= s_pref[j + 1]) j++;
+            const int v = s_vid[j];
+            const int64_t idx = (int64_t)(item - s_pref[j]);
+            const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + idx];
+            jb.x = (int)(cw & 0xFFFFu);
+            jb.y = (int)(cw >> 16);
+            jb.v = v;
+            int n;
+            runs = line_runs_p<kWide>(a, a.view[v], a.ptab + (int64_t)v * kTabLen, jb.x, jb.y, s_h[v], jb.k0, jb.k1,
+                                      jb.ks, n);
+            if (runs > 2) {
+                atomicOr(&a.fb[(int64_t)v * a.fb_words + (idx >> 5)], 1u << (idx & 31));
+            } else if (runs > 0) {
+                if (v != cur_v) {
+                    if (cur_v >= 0) {
+                        atomicAdd(&s_st[2 * cur_v], acc_n);
+                        atomicAdd(&s_st[2 * cur_v + 1], acc_p);
+                    }
+                    cur_v = v;
+                    acc_n = acc_p = 0;
+                }
+                acc_n += (unsigned long long)n;
+                acc_p += pair_count(n, half);
             }
-            cur_v = v;
-            acc_n = acc_p = 0;
         }
-        acc_n += (unsigned long long)n;
-        acc_p += pair_count(n, half);
+        // Queue the lines by kind (warp-level compaction).
+        const unsigned m1 = __ballot_sync(kFull, runs == 1), m2 = __ballot_sync(kFull, runs == 2);
+        if (runs == 1) q1[n1 + __popc(m1 & lt)] = jb;
+        if (runs == 2) q2[n2 + __popc(m2 & lt)] = jb;
+        n1 += __popc(m1);
+        n2 += __popc(m2);
+        __syncwarp();
+        // Pass 2 for full warps of one kind.
+        if (n1 >= 32) {
+            run1(q1[n1 - 32 + lane]);
+            n1 -= 32;
+        }
+        if (n2 >= 32) {
+            run2(q2[n2 - 32 + lane]);
+            n2 -= 32;
+        }
+        __syncwarp();
     }
+    // Drain the queues.
+    if (lane < n1) run1(q1[lane]);
+    if (lane < n2) run2(q2[lane]);
     if (cur_v >= 0) {
         atomicAdd(&s_st[2 * cur_v], acc_n);
         atomicAdd(&s_st[2 * cur_v + 1], acc_p);
@@ -890,6 +1128,13 @@ cudaError_t configure_kernels(int* edges_bps, int* lines_bps, int scan_bps[kNumC
 cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st)
 {
     k_edges<<<grid, kEdgeThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tables(const Args& a, cudaStream_t st)
+{
+    const int64_t total = (int64_t)a.nv * kTabLen;
+    k_tables<<<(int)((total + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -14,12 +14,14 @@ using namespace occ;
 namespace {
 
 // The scratch every call shares: the detection header (status word, min/max of D, per-view counts), the per-view
-// statistics, the bit per candidate marking lines left to the warp kernels, then the candidate lists, [n_views][H*W]
-// entries of the current call.  One array per device that loads the library; it lives until the process exits.
+// statistics, the bit per candidate marking lines left to the warp kernels, the scan-line position tables, then the
+// candidate lists, [n_views][H*W] entries of the current call.  One array per device that loads the library; it lives until the process exits.
 constexpr size_t kHeaderWords = HDR_WORDS;
 constexpr size_t kStatsWords = 2 * 2 * OCC_MAX_VIEWS;  // [views][2] unsigned long long, counted in uint32 words
 constexpr size_t kFlagWords = OCC_NOALLOC_MAX_PIXEL_VIEWS / 32 + OCC_MAX_VIEWS;
-constexpr size_t kScratchWords = kHeaderWords + kStatsWords + kFlagWords + (size_t)OCC_NOALLOC_MAX_PIXEL_VIEWS;
+constexpr size_t kTabWords = (size_t)kTabLen * OCC_MAX_VIEWS;
+constexpr size_t kScratchWords =
+    kHeaderWords + kStatsWords + kFlagWords + kTabWords + (size_t)OCC_NOALLOC_MAX_PIXEL_VIEWS;
 
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kScratchWords];
 
@@ -120,7 +122,8 @@ extern "C" int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t 
     const bool lines = (p.N / 2) <= kLineMaxHalf;
     a.fb_words = (plane + 31) / 32;
     a.fb = lines ? hdr + kHeaderWords + kStatsWords : nullptr;
-    a.cand = hdr + kHeaderWords + kStatsWords + kFlagWords;
+    a.ptab = reinterpret_cast<int32_t*>(hdr + kHeaderWords + kStatsWords + kFlagWords);
+    a.cand = hdr + kHeaderWords + kStatsWords + kFlagWords + kTabWords;
     a.cand_cap = plane;
     a.O = O;
     a.M = M;
@@ -133,6 +136,7 @@ extern "C" int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t 
     const int64_t quads = (int64_t)H * ((W + 3) / 4);
     const int64_t edge_blocks = (quads + 255) / 256;
     const int grid_edges = (int)(edge_blocks < s.grid_edges ? edge_blocks : s.grid_edges);
+    if (lines && launch_tables(a, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (launch_edges(a, grid_edges, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (lines && launch_scan_lines(a, s.grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
     bool run_cls[kNumClasses] = {true, true, true};
