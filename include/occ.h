@@ -56,6 +56,7 @@ extern "C" {
 
 /* Limits. */
 #define OCC_MAX_VIEWS 64     /* views per call */
+#define OCC_MAX_FRAMES 1024  /* frames per occ_detect_batched call */
 #define OCC_MAX_SCAN 4094    /* largest scan length L (Eq. 3); 2h+1 <= 4095 samples per scan line */
 #define OCC_MAX_SIDE 65535   /* largest H and W */
 #define OCC_MAX_N 64         /* largest neighbour count N (Eq. 5) */
@@ -135,13 +136,31 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
 int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,
                     int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream);
 
+/*
+ * The method for n_frames frames of possibly different sizes and the same views, queued as one batch: a handful of
+ * launches for the whole batch (the candidate pass over every frame, one plan, one persistent launch of each scan
+ * kernel over every frame, view and candidate, one mask pass), with results identical to n_frames occ_detect calls.
+ * No call allocates, so the batch can be captured into a CUDA graph and replayed.
+ *   D[f]   device, binary32 [H[f]][W[f]] row-major (pitch = W[f]); H, W, D, M, O are host arrays of n_frames
+ *          entries; 1 <= n_frames <= OCC_MAX_FRAMES; the sum of H[f] * W[f] must not exceed the context's max_pixels.
+ *   M[f]   device, uint8 [n_views][H[f]][W[f]]; O[f] device, int32 [n_views][H[f]][W[f]]: both required.
+ * Each frame's candidate lists get the context's per-pixel share of its capacity (all of a frame's pixels with the
+ * default max_candidates, so they never overflow).  occ_get_status reports the OR of every frame's conditions;
+ * occ_get_stats sums candidates, samples and pair tests over the frames and reports the largest L.  Returns OCC_OK
+ * once queued, OCC_ERR_INVALID_ARG or OCC_ERR_CUDA.
+ */
+int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H, const int32_t* W,
+                       const occ_view* views, int32_t n_views, const occ_params* p, uint8_t* const* M,
+                       int32_t* const* O, void* stream);
+
 /* Waits for `stream` and returns the device status of the last occ_detect call of this context: OCC_OK,
  * OCC_ERR_NONFINITE_INPUT, OCC_ERR_CAPACITY or OCC_ERR_TIMEOUT (in that priority), or OCC_ERR_CUDA if the wait
  * itself failed. */
 int occ_get_status(occ_ctx* ctx, void* stream);
 
-/* Copies the work counts of the first n_views views of the last occ_detect call into out (host).  Waits for the
- * last stream used.  Returns OCC_ERR_INVALID_ARG if n_views exceeds the views of that call. */
+/* Copies the work counts of the first n_views views of the last occ_detect / occ_detect_batched call into out (host;
+ * summed over the frames of a batch, L the largest).  Waits for the last stream used.  Returns OCC_ERR_INVALID_ARG if
+ * n_views exceeds the views of that call. */
 int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
 
 /* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the
@@ -171,9 +190,8 @@ int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
  * fully reserved up front, or a framework that hands out only the tensors it manages).  The paper has no counterpart;
  * this is a deployment variant of the same computation with the same results.
  *
- * Its scratch (the status word and per-view counters, 1.6 KB, scan-line position tables, 1 MiB, a bit per pixel
- * and view, and the candidate lists, 4 bytes per pixel and view) is one array of about 67 MiB built into the
- * library: every GPU on which the library is used holds it until the
+ * Its scratch (headers, counters and plan, 4 KB, scan-line position tables, 1 MiB, a bit per pixel and view, and
+ * the candidate lists, 4 bytes per pixel and view) is one array of about 67 MiB built into the library: every GPU on which the library is used holds it until the
  * process exits.  The call itself allocates and frees nothing.  Every call on a device
  * shares that array and overwrites it, clearing first what must start at zero; two calls that may run at the same
  * time on the GPU (different streams, or different host threads) race on it and give wrong results, so serialise

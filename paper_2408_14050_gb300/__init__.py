@@ -32,8 +32,10 @@ STAGES = ["candidates", "scan_lines", "scan_256", "scan_1024", "scan_4096", "mas
 
 OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
 
+OCC_MAX_FRAMES = 1024
+
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
-            "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc",
+            "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc",
             "occ_status_string"]
 
 
@@ -94,6 +96,10 @@ def load(build_if_missing: bool = True):
         L.occ_detect_host.argtypes = [vp, vp, i32, i32, ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
                                       vp, vp, vp]
         L.occ_detect_host.restype = ctypes.c_int
+        L.occ_detect_batched.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                         ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
+                                         ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        L.occ_detect_batched.restype = ctypes.c_int
         L.occ_get_status.argtypes = [vp, vp]
         L.occ_get_status.restype = ctypes.c_int
         L.occ_get_stats.argtypes = [vp, ctypes.POINTER(occ_view_stats), i32]
@@ -223,6 +229,34 @@ def occ_detect(ctx: Context, D, views, params: occ_params | None = None, M=None,
         raise OccError(rc, "occ_detect")
     ctx.last_views = nv
     return M, O
+
+
+def occ_detect_batched(ctx: Context, Ds, views, params: occ_params | None = None, Ms=None, Os=None, stream=None):
+    """Queue the method for a list of float32 CUDA maps [H][W] (contiguous) with the same views, as one batch.
+    Returns (Ms, Os): lists of uint8 / int32 [V][H][W] tensors (allocated when not given)."""
+    import torch
+    nf = len(Ds)
+    nv = len(views)
+    for D in Ds:
+        if D.dtype != torch.float32 or D.dim() != 2 or not D.is_cuda or not D.is_contiguous():
+            raise ValueError("every map must be a contiguous float32 CUDA tensor [H][W]")
+    if Ms is None:
+        Ms = [torch.empty((nv, *D.shape), dtype=torch.uint8, device=D.device) for D in Ds]
+    if Os is None:
+        Os = [torch.empty((nv, *D.shape), dtype=torch.int32, device=D.device) for D in Ds]
+    vp = ctypes.c_void_p
+    d_arr = (vp * nf)(*[D.data_ptr() for D in Ds])
+    m_arr = (vp * nf)(*[M.data_ptr() for M in Ms])
+    o_arr = (vp * nf)(*[O.data_ptr() for O in Os])
+    h_arr = (ctypes.c_int32 * nf)(*[D.shape[0] for D in Ds])
+    w_arr = (ctypes.c_int32 * nf)(*[D.shape[1] for D in Ds])
+    rc = load().occ_detect_batched(ctx.handle, nf, d_arr, h_arr, w_arr, _views(views), nv,
+                                   ctypes.byref(params) if params is not None else None, m_arr, o_arr,
+                                   _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_detect_batched")
+    ctx.last_views = nv
+    return Ms, Os
 
 
 def occ_detect_host(ctx: Context, D, views, params: occ_params | None = None, M=None, O=None, stream=None):

@@ -1,8 +1,9 @@
-// occ_api.cu -- host side of the C ABI declared in include/occ.h: context and scratch ownership, argument
-// validation, the binary32 direction of each view, the launch sequence of one detect call, status and statistics.
+// occ_api.cu -- host side of the C ABI declared in include/occ.h: argument validation, the binary32 direction of each
+// view, the context and its scratch, the launch sequence shared by every entry point (run_frames), status and
+// statistics.
+#include <climits>
 #include <cmath>
 #include <cstdlib>
-#include <climits>
 #include <cstring>
 #include <new>
 
@@ -12,25 +13,18 @@ using namespace occ;
 
 struct occ_ctx {
     int device = 0;
-    int num_sms = 0;
     int64_t max_pixels = 0;
     int32_t max_views = 0;
-    int64_t cand_cap = 0;
-    uint32_t* d_hdr = nullptr;                 // HDR_WORDS words, followed by the per-view statistics
-    unsigned long long* d_stats = nullptr;     // [max_views][2] (inside the d_hdr allocation)
-    size_t hdr_bytes = 0;                      // header + statistics, cleared by one memset per call
-    uint32_t* d_cand = nullptr;                // [max_views][cand_cap]
+    int64_t cand_cap = 0;                      // list entries per view for a frame of max_pixels pixels
+    Scratch sc{};
+    void* d_block = nullptr;                   // one allocation for headers, statistics, tables and plan
+    uint32_t* d_cand = nullptr;
+    uint32_t* d_fb = nullptr;
     int32_t* d_O_scratch = nullptr;            // [max_views][max_pixels], allocated on first use
     float* d_D_stage = nullptr;                // occ_detect_host staging, allocated on first use
     uint8_t* d_M_stage = nullptr;
     int32_t* d_O_stage = nullptr;
-    int grid_edges = 0, grid_mask = 0;
-    int grid_scan[kNumClasses] = {0, 0, 0};
-    int grid_lines = 0;
-    uint32_t* d_fb = nullptr;                  // [max_views][fb_words] lines left to the warp scan kernel
-    int32_t* d_ptab = nullptr;                 // [max_views][kTabLen] scan-line position tables
-    int64_t fb_words = 0;
-    int32_t last_nv = 0;
+    int32_t last_nf = 0, last_nv = 0;
     cudaStream_t last_stream = nullptr;
     bool profiling = false;
     bool profiled_call = false;
@@ -56,7 +50,134 @@ struct DeviceGuard {
 
 bool is_finite_f(float x) { return std::isfinite(x); }
 
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
 }  // namespace
+
+namespace occ {
+
+int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p_in, Args& a)
+{
+    occ_params p;
+    if (p_in) p = *p_in; else occ_default_params(&p);
+    if (!views || n_views < 1 || n_views > OCC_MAX_VIEWS) return OCC_ERR_INVALID_ARG;
+    if (p.N < 2 || p.N > OCC_MAX_N || (p.N & 1) || !is_finite_f(p.gamma) || !is_finite_f(p.beta) ||
+        !is_finite_f(p.zeta) || !(p.zeta > 0.0f) || p.L > OCC_MAX_SCAN)
+        return OCC_ERR_INVALID_ARG;
+    a.nv = n_views;
+    a.nr = 0;
+    for (int v = 0; v < n_views; v++) {
+        const double al = views[v].alpha_deg;
+        const float r = views[v].ratio;
+        if (!std::isfinite(al) || !is_finite_f(r) || !(r > 0.0f)) return OCC_ERR_INVALID_ARG;
+        occ_direction(al, &a.view[v].c, &a.view[v].s);
+        a.view[v].r = r;
+        int u = 0;
+        while (u < a.nr && a.ratio[u] != r) u++;
+        if (u == a.nr) a.ratio[a.nr++] = r;
+        a.view[v].ridx = u;
+    }
+    a.gamma = p.gamma;
+    a.zeta = p.zeta;
+    a.beta = p.beta;
+    a.Lover = p.L > 0 ? p.L : 0;
+    a.N = p.N;
+    return OCC_OK;
+}
+
+cudaError_t scratch_grids(Scratch& sc)
+{
+    int dev = 0, sms = 0, bps_lines = 0, bps_scan[kNumClasses] = {0, 0, 0};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = configure_kernels(&bps_lines, bps_scan);
+    if (e != cudaSuccess) return e;
+    sc.grid_lines = sms * (bps_lines > 0 ? bps_lines : 1);
+    for (int c = 0; c < kNumClasses; c++) sc.grid_scan[c] = sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
+    return cudaSuccess;
+}
+
+int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev)
+{
+    const int nv = a.nv;
+    const bool lines = (a.N / 2) <= kLineMaxHalf;
+    a.nf = nf;
+    a.use_fb = lines ? 1 : 0;
+    a.frames = sc.frames;
+    a.plan = sc.plan;
+    a.pref_all = sc.pref;
+    a.pref_cls = sc.pref + (nf * nv + 1);
+    a.ptab = sc.ptab;
+    a.status = sc.status;
+    a.max_quads = 0;
+    a.max_px = 0;
+
+    // Frame records: lists and flags laid out frame after frame in the pools.
+    FrameChunk chunk;
+    std::memset(&chunk, 0, sizeof(chunk));
+    chunk.dst = sc.frames;
+    int64_t cand_off = 0, fb_off = 0;
+    bool wide = false;
+    for (int f = 0; f < nf; f++) {
+        FrameArg& F = chunk.f[f % kFramesPerChunk];
+        std::memset(&F, 0, sizeof(F));
+        F.D = fr[f].D;
+        F.pitch = fr[f].pitch;
+        F.H = fr[f].H;
+        F.W = fr[f].W;
+        F.wide = (int64_t)(F.H - 1) * F.pitch + F.W > (int64_t)INT32_MAX;
+        wide = wide || F.wide;
+        F.O = fr[f].O;
+        F.M = fr[f].M;
+        F.E = fr[f].E;
+        F.A = fr[f].A;
+        F.cap = fr[f].cap;
+        F.cand = sc.cand + cand_off;
+        cand_off += F.cap * nv;
+        F.fb_words = (F.cap + 31) / 32;
+        F.fb = sc.fb + fb_off;
+        fb_off += F.fb_words * nv;
+        F.hdr = sc.hdr + (size_t)f * HDR_WORDS;
+        F.stats = sc.stats + (size_t)f * sc.max_views * 2;
+        const int quads = F.H * ((F.W + 3) / 4);
+        if (quads > a.max_quads) a.max_quads = quads;
+        const int64_t px = (int64_t)nv * F.H * F.W;
+        if (px > a.max_px) a.max_px = px;
+        if (f % kFramesPerChunk == kFramesPerChunk - 1 || f == nf - 1) {
+            chunk.first = f - f % kFramesPerChunk;
+            chunk.count = f % kFramesPerChunk + 1;
+            if (launch_frames(chunk, st) != cudaSuccess) return OCC_ERR_CUDA;
+        }
+    }
+    if (cand_off > sc.cand_entries || (lines && fb_off > sc.fb_entries)) return OCC_ERR_INVALID_ARG;
+
+    auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], st) == cudaSuccess; };
+    if (cudaMemsetAsync(sc.hdr, 0, sizeof(uint32_t) * HDR_WORDS * nf, st) != cudaSuccess ||
+        cudaMemsetAsync(sc.stats, 0, sizeof(unsigned long long) * 2 * sc.max_views * nf, st) != cudaSuccess ||
+        cudaMemsetAsync(sc.status, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        (lines && cudaMemsetAsync(sc.fb, 0, sizeof(uint32_t) * fb_off, st) != cudaSuccess))
+        return OCC_ERR_CUDA;
+    // Size classes of the warp kernels that can receive work: with a fixed L only one.
+    bool run_cls[kNumClasses] = {true, true, true};
+    if (a.Lover > 0) {
+        const int nk = 2 * ((a.Lover + 1) / 2) + 1;
+        const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
+        for (int k = 0; k < kNumClasses; k++) run_cls[k] = (k == c);
+    }
+    if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
+        launch_plan(a, st) != cudaSuccess || !mark(1))
+        return OCC_ERR_CUDA;
+    if (lines && launch_scan_lines(a, sc.grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
+    if (!mark(2)) return OCC_ERR_CUDA;
+    for (int c = 0; c < kNumClasses; c++) {
+        if (run_cls[c] && launch_scan(a, c, sc.grid_scan[c], st) != cudaSuccess) return OCC_ERR_CUDA;
+        if (!mark(3 + c)) return OCC_ERR_CUDA;
+    }
+    if (launch_mask(a, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
+    return OCC_OK;
+}
+
+}  // namespace occ
 
 extern "C" {
 
@@ -118,14 +239,13 @@ void occ_destroy(occ_ctx* ctx)
     if (!ctx) return;
     {
         DeviceGuard g(ctx->device);
-        cudaFree(ctx->d_hdr);
+        cudaFree(ctx->d_block);
         cudaFree(ctx->d_cand);
+        cudaFree(ctx->d_fb);
         cudaFree(ctx->d_O_scratch);
         cudaFree(ctx->d_D_stage);
         cudaFree(ctx->d_M_stage);
         cudaFree(ctx->d_O_stage);
-        cudaFree(ctx->d_fb);
-        cudaFree(ctx->d_ptab);
         for (int i = 0; i <= OCC_NUM_STAGES; i++)
             if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     }
@@ -151,62 +271,78 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
 
     DeviceGuard g(device);
     if (!g.ok) { delete ctx; return OCC_ERR_CUDA; }
-    int bps_edges = 0, bps_lines = 0, bps_mask = 0, bps_scan[kNumClasses] = {0, 0, 0};
-    ctx->fb_words = (ctx->cand_cap + 31) / 32;
-    ctx->hdr_bytes = sizeof(uint32_t) * HDR_WORDS + sizeof(unsigned long long) * 2 * (size_t)max_views;
-    bool ok = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess &&
-              configure_kernels(&bps_edges, &bps_lines, bps_scan, &bps_mask) == cudaSuccess &&
-              cudaMalloc(&ctx->d_hdr, ctx->hdr_bytes) == cudaSuccess &&
-              cudaMalloc(&ctx->d_cand, sizeof(uint32_t) * (size_t)ctx->cand_cap * (size_t)max_views) == cudaSuccess &&
-              cudaMalloc(&ctx->d_fb, sizeof(uint32_t) * (size_t)ctx->fb_words * (size_t)max_views) == cudaSuccess &&
-              cudaMalloc(&ctx->d_ptab, sizeof(int32_t) * (size_t)kTabLen * (size_t)max_views) == cudaSuccess &&
-              cudaMemset(ctx->d_hdr, 0, ctx->hdr_bytes) == cudaSuccess;
+    Scratch& sc = ctx->sc;
+    sc.max_frames = kMaxFrames;
+    sc.max_views = max_views;
+    const size_t nfv = (size_t)kMaxFrames * max_views;
+    const size_t sz_hdr = align256(sizeof(uint32_t) * HDR_WORDS * kMaxFrames);
+    const size_t sz_stats = align256(sizeof(unsigned long long) * 2 * nfv);
+    const size_t sz_status = 256;
+    const size_t sz_frames = align256(sizeof(FrameArg) * kMaxFrames);
+    const size_t sz_plan = align256(sizeof(PlanEntry) * nfv);
+    const size_t sz_pref = align256(sizeof(uint32_t) * (1 + kNumClasses) * (nfv + 1));
+    const size_t sz_tab = align256(sizeof(int32_t) * kTabLen * max_views);
+    const size_t total = sz_hdr + sz_stats + sz_status + sz_frames + sz_plan + sz_pref + sz_tab;
+    sc.cand_entries = ctx->cand_cap * max_views;
+    sc.fb_entries = (ctx->cand_cap / 32 + kMaxFrames + 1) * (int64_t)max_views;
+    bool ok = scratch_grids(sc) == cudaSuccess && cudaMalloc(&ctx->d_block, total) == cudaSuccess &&
+              cudaMalloc(&ctx->d_cand, sizeof(uint32_t) * (size_t)sc.cand_entries) == cudaSuccess &&
+              cudaMalloc(&ctx->d_fb, sizeof(uint32_t) * (size_t)sc.fb_entries) == cudaSuccess &&
+              cudaMemset(ctx->d_block, 0, total) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         occ_destroy(ctx);
         return OCC_ERR_CUDA;
     }
-    ctx->d_stats = reinterpret_cast<unsigned long long*>(ctx->d_hdr + HDR_WORDS);
-    ctx->grid_edges = ctx->num_sms * (bps_edges > 0 ? bps_edges : 1);
-    ctx->grid_mask = ctx->num_sms * (bps_mask > 0 ? bps_mask : 1);
-    ctx->grid_lines = ctx->num_sms * (bps_lines > 0 ? bps_lines : 1);
-    for (int c = 0; c < kNumClasses; c++) ctx->grid_scan[c] = ctx->num_sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
+    char* p = static_cast<char*>(ctx->d_block);
+    sc.hdr = reinterpret_cast<uint32_t*>(p); p += sz_hdr;
+    sc.stats = reinterpret_cast<unsigned long long*>(p); p += sz_stats;
+    sc.status = reinterpret_cast<uint32_t*>(p); p += sz_status;
+    sc.frames = reinterpret_cast<FrameArg*>(p); p += sz_frames;
+    sc.plan = reinterpret_cast<PlanEntry*>(p); p += sz_plan;
+    sc.pref = reinterpret_cast<uint32_t*>(p); p += sz_pref;
+    sc.ptab = reinterpret_cast<int32_t*>(p);
+    sc.cand = ctx->d_cand;
+    sc.fb = ctx->d_fb;
     *out = ctx;
     return OCC_OK;
 }
 
-int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views,
-               int32_t n_views, const occ_params* p_in, uint8_t* M, int32_t* O, float* E, float* A, void* stream)
-{
-    if (!ctx || !D || !views || !M) return OCC_ERR_INVALID_ARG;
-    occ_params p;
-    if (p_in) p = *p_in; else occ_default_params(&p);
-    if (pitch == 0) pitch = W;
-    if (H < 1 || W < 1 || H > OCC_MAX_SIDE || W > OCC_MAX_SIDE || (int64_t)H * W > ctx->max_pixels || pitch < W)
-        return OCC_ERR_INVALID_ARG;
-    if (n_views < 1 || n_views > ctx->max_views) return OCC_ERR_INVALID_ARG;
-    if (p.N < 2 || p.N > OCC_MAX_N || (p.N & 1) || !is_finite_f(p.gamma) || !is_finite_f(p.beta) || !is_finite_f(p.zeta) ||
-        !(p.zeta > 0.0f) || p.L > OCC_MAX_SCAN)
-        return OCC_ERR_INVALID_ARG;
-    if ((reinterpret_cast<uintptr_t>(D) & 3) || (O && (reinterpret_cast<uintptr_t>(O) & 3)) ||
-        (E && (reinterpret_cast<uintptr_t>(E) & 3)) || (A && (reinterpret_cast<uintptr_t>(A) & 3)))
-        return OCC_ERR_INVALID_ARG;
+namespace {
 
+// Queues nf validated frames on the context and records the call for status, statistics and timings.
+int ctx_run(occ_ctx* ctx, const FrameIn* fr, int nf, Args& a, void* stream)
+{
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ctx->last_nf = nf;
+    ctx->last_nv = a.nv;
+    ctx->last_stream = st;
+    const int rc = run_frames(ctx->sc, fr, nf, a, st, ctx->profiling ? ctx->ev : nullptr);
+    ctx->profiled_call = ctx->profiling && rc == OCC_OK;
+    return rc;
+}
+
+bool frame_ok(const occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch)
+{
+    return D && H >= 1 && W >= 1 && H <= OCC_MAX_SIDE && W <= OCC_MAX_SIDE && pitch >= W &&
+           (int64_t)H * W <= ctx->max_pixels && !(reinterpret_cast<uintptr_t>(D) & 3);
+}
+
+}  // namespace
+
+int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views,
+               int32_t n_views, const occ_params* p, uint8_t* M, int32_t* O, float* E, float* A, void* stream)
+{
+    if (!ctx || !M) return OCC_ERR_INVALID_ARG;
+    if (pitch == 0) pitch = W;
+    if (!frame_ok(ctx, D, H, W, pitch) || n_views > ctx->max_views) return OCC_ERR_INVALID_ARG;
+    if ((O && (reinterpret_cast<uintptr_t>(O) & 3)) || (E && (reinterpret_cast<uintptr_t>(E) & 3)) ||
+        (A && (reinterpret_cast<uintptr_t>(A) & 3)))
+        return OCC_ERR_INVALID_ARG;
     Args a;
     std::memset(&a, 0, sizeof(a));
-    a.nv = n_views;
-    a.nr = 0;
-    for (int v = 0; v < n_views; v++) {
-        const double al = views[v].alpha_deg;
-        const float r = views[v].ratio;
-        if (!std::isfinite(al) || !is_finite_f(r) || !(r > 0.0f)) return OCC_ERR_INVALID_ARG;
-        occ_direction(al, &a.view[v].c, &a.view[v].s);
-        a.view[v].r = r;
-        int u = 0;
-        while (u < a.nr && a.ratio[u] != r) u++;
-        if (u == a.nr) a.ratio[a.nr++] = r;
-        a.view[v].ridx = u;
-    }
+    const int rc = prepare_views(views, n_views, p, a);
+    if (rc != OCC_OK) return rc;
 
     DeviceGuard g(ctx->device);
     if (!g.ok) return OCC_ERR_CUDA;
@@ -219,66 +355,42 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
         }
         O = ctx->d_O_scratch;
     }
+    FrameIn fr{D, pitch, H, W, O, M, E, A, ctx->cand_cap};
+    return ctx_run(ctx, &fr, 1, a, stream);
+}
 
-    a.D = D;
-    a.pitch = pitch;
-    a.H = H;
-    a.W = W;
-    a.gamma = p.gamma;
-    a.zeta = p.zeta;
-    a.beta = p.beta;
-    a.Lover = p.L > 0 ? p.L : 0;
-    a.N = p.N;
-    a.cand = ctx->d_cand;
-    a.cand_cap = ctx->cand_cap;
-    a.hdr = ctx->d_hdr;
-    a.stats = ctx->d_stats;
-    a.O = O;
-    a.M = M;
-    a.E = E;
-    a.A = A;
-
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    ctx->last_nv = n_views;
-    ctx->last_stream = st;
-
-    // Classes of scan kernels that can receive work: with a fixed L only one; with Eq. 3 the device decides, and
-    // the kernels of the other classes return at once.
-    bool run_cls[kNumClasses] = {true, true, true};
-    if (a.Lover > 0) {
-        const int nk = 2 * ((a.Lover + 1) / 2) + 1;
-        const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
-        for (int k = 0; k < kNumClasses; k++) run_cls[k] = (k == c);
+int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H, const int32_t* W,
+                       const occ_view* views, int32_t n_views, const occ_params* p, uint8_t* const* M,
+                       int32_t* const* O, void* stream)
+{
+    if (!ctx || !D || !H || !W || !M || !O || n_frames < 1 || n_frames > OCC_MAX_FRAMES ||
+        n_views > ctx->max_views)
+        return OCC_ERR_INVALID_ARG;
+    Args a;
+    std::memset(&a, 0, sizeof(a));
+    int rc = prepare_views(views, n_views, p, a);
+    if (rc != OCC_OK) return rc;
+    FrameIn* fr = static_cast<FrameIn*>(std::malloc(sizeof(FrameIn) * (size_t)n_frames));
+    if (!fr) return OCC_ERR_CUDA;
+    int64_t pixels = 0;
+    for (int f = 0; f < n_frames && rc == OCC_OK; f++) {
+        if (!frame_ok(ctx, D[f], H[f], W[f], W[f]) || !M[f] || !O[f] || (reinterpret_cast<uintptr_t>(O[f]) & 3)) {
+            rc = OCC_ERR_INVALID_ARG;
+            break;
+        }
+        pixels += (int64_t)H[f] * W[f];
+        // List capacity in proportion to the frame: the context's per-pixel share, at least one entry.
+        int64_t cap = (int64_t)((double)H[f] * W[f] * (double)ctx->cand_cap / (double)ctx->max_pixels);
+        if (cap < 1) cap = 1;
+        fr[f] = FrameIn{D[f], W[f], H[f], W[f], O[f], M[f], nullptr, nullptr, cap};
     }
-    const int64_t quads = (int64_t)H * ((W + 3) / 4);
-    const int64_t edge_blocks = (quads + 255) / 256;
-    const int grid_edges = (int)(edge_blocks < ctx->grid_edges ? edge_blocks : ctx->grid_edges);
-
-    // Lines go to the line-per-thread kernel first (N/2 <= kLineMaxHalf); the warp kernels then take the lines it
-    // flagged.  Larger N: the warp kernels take every line.
-    const bool lines = (p.N / 2) <= kLineMaxHalf;
-    a.fb = lines ? ctx->d_fb : nullptr;
-    a.ptab = ctx->d_ptab;
-    a.fb_words = ctx->fb_words;
-    const bool wide = (int64_t)(H - 1) * pitch + W > (int64_t)INT32_MAX;
-
-    const bool prof = ctx->profiling;
-    auto mark = [&](int i) { return !prof || cudaEventRecord(ctx->ev[i], st) == cudaSuccess; };
-    if (cudaMemsetAsync(ctx->d_hdr, 0, ctx->hdr_bytes, st) != cudaSuccess) return OCC_ERR_CUDA;
-    if (lines && cudaMemsetAsync(ctx->d_fb, 0, sizeof(uint32_t) * (size_t)ctx->fb_words * n_views, st) != cudaSuccess)
-        return OCC_ERR_CUDA;
-    if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, grid_edges, st) != cudaSuccess ||
-        !mark(1))
-        return OCC_ERR_CUDA;
-    if (lines && launch_scan_lines(a, ctx->grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
-    if (!mark(2)) return OCC_ERR_CUDA;
-    for (int c = 0; c < kNumClasses; c++) {
-        if (run_cls[c] && launch_scan(a, c, ctx->grid_scan[c], st) != cudaSuccess) return OCC_ERR_CUDA;
-        if (!mark(3 + c)) return OCC_ERR_CUDA;
+    if (rc == OCC_OK && pixels > ctx->max_pixels) rc = OCC_ERR_INVALID_ARG;
+    if (rc == OCC_OK) {
+        DeviceGuard g(ctx->device);
+        rc = g.ok ? ctx_run(ctx, fr, n_frames, a, stream) : OCC_ERR_CUDA;
     }
-    if (launch_mask(a, ctx->grid_mask, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
-    ctx->profiled_call = prof;
-    return OCC_OK;
+    std::free(fr);
+    return rc;
 }
 
 int occ_set_profiling(occ_ctx* ctx, int enable)
@@ -324,7 +436,7 @@ int occ_get_status(occ_ctx* ctx, void* stream)
     if (!g.ok) return OCC_ERR_CUDA;
     uint32_t word = 0;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(&word, ctx->d_hdr + HDR_STATUS, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(&word, ctx->sc.status, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return OCC_ERR_CUDA;
@@ -341,23 +453,36 @@ int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views)
     if (!ctx || !out || n_views < 0 || n_views > ctx->last_nv) return OCC_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     if (!g.ok) return OCC_ERR_CUDA;
-    uint32_t hdr[HDR_WORDS];
-    unsigned long long st[2 * OCC_MAX_VIEWS];
-    if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess ||
-        cudaMemcpy(hdr, ctx->d_hdr, sizeof(hdr), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(st, ctx->d_stats, sizeof(unsigned long long) * 2 * ctx->last_nv, cudaMemcpyDeviceToHost) !=
-            cudaSuccess) {
+    const int nf = ctx->last_nf;
+    uint32_t* hdr = static_cast<uint32_t*>(std::malloc(sizeof(uint32_t) * HDR_WORDS * (size_t)nf));
+    unsigned long long* st =
+        static_cast<unsigned long long*>(std::malloc(sizeof(unsigned long long) * 2 * ctx->max_views * (size_t)nf));
+    int rc = (hdr && st) ? OCC_OK : OCC_ERR_CUDA;
+    if (rc == OCC_OK &&
+        (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess ||
+         cudaMemcpy(hdr, ctx->sc.hdr, sizeof(uint32_t) * HDR_WORDS * nf, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(st, ctx->sc.stats, sizeof(unsigned long long) * 2 * ctx->max_views * nf,
+                    cudaMemcpyDeviceToHost) != cudaSuccess)) {
         cudaGetLastError();
-        return OCC_ERR_CUDA;
+        rc = OCC_ERR_CUDA;
     }
-    for (int v = 0; v < n_views; v++) {
-        out[v].candidates = hdr[HDR_COUNT + v];
-        out[v].samples = (int64_t)st[2 * v];
-        out[v].pair_tests = (int64_t)st[2 * v + 1];
-        out[v].L = (int32_t)hdr[HDR_L + v];
-        out[v].reserved = 0;
+    if (rc == OCC_OK) {
+        for (int v = 0; v < n_views; v++) {
+            occ_view_stats s{0, 0, 0, 0, 0};
+            for (int f = 0; f < nf; f++) {
+                const uint32_t* h = hdr + (size_t)f * HDR_WORDS;
+                const unsigned long long* x = st + (size_t)f * ctx->max_views * 2;
+                s.candidates += h[HDR_COUNT + v];
+                s.samples += (int64_t)x[2 * v];
+                s.pair_tests += (int64_t)x[2 * v + 1];
+                if ((int32_t)h[HDR_L + v] > s.L) s.L = (int32_t)h[HDR_L + v];
+            }
+            out[v] = s;
+        }
     }
-    return OCC_OK;
+    std::free(hdr);
+    std::free(st);
+    return rc;
 }
 
 int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,

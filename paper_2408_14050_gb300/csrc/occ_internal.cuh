@@ -1,5 +1,9 @@
-// occ_internal.cuh -- layout of the context scratch and the launch arguments shared by the kernels
-// (occ_kernels.cu) and the host side of the C ABI (occ_api.cu, occ_noalloc.cu).  Not part of the public interface.
+// occ_internal.cuh -- launch arguments and per-frame records shared by the kernels (occ_kernels.cu) and the host side
+// of the C ABI (occ_api.cu, occ_noalloc.cu).  Not part of the public interface.
+//
+// Every call runs a batch of frames (one for occ_detect): the host writes one FrameArg per frame into a device
+// table, k_plan derives per (frame, view) the scan length, the size class of the scan lines and the prefix sums that
+// number the scan work items, and every kernel finds its frame and view from those tables.
 #pragma once
 
 #include <cstdint>
@@ -10,11 +14,12 @@
 namespace occ {
 
 constexpr int kMaxViews = OCC_MAX_VIEWS;
+constexpr int kMaxFrames = OCC_MAX_FRAMES;
 
-// Words of the per-call device header (uint32).  The host clears the header (and the statistics after it) with one
-// memset at the start of every detect call; the kernels then fill it in stream order.
+// Words of the per-frame device header (uint32); the host clears the headers and statistics of a call with one
+// memset, the kernels fill them in stream order.
 enum : int {
-    HDR_STATUS = 0,                  // status bits (ST_*)
+    HDR_STATUS = 0,                  // status bits of the frame (ST_*)
     HDR_MAX = 1,                     // max D, order-preserving encoding (atomicMax)
     HDR_NEGMIN = 2,                  // min D, complemented encoding (atomicMax)
     HDR_COUNT = 8,                   // [kMaxViews] candidates found per view (may exceed the list capacity)
@@ -45,38 +50,114 @@ struct ViewArg {
     int32_t ridx;    // index of r in Args::ratio
 };
 
-struct Args {
-    const float* D;
-    int64_t pitch;   // elements between rows of D
+// One frame of a call.
+struct FrameArg {
+    const float* D;               // [H][pitch]
+    int64_t pitch;
     int32_t H, W;
-    int32_t nv, nr;  // views, distinct ratios
-    float gamma, zeta, beta;
-    int32_t Lover;   // > 0: fixed scan length; else Eq. 3 per view
-    int32_t N;
-    ViewArg view[kMaxViews];
-    float ratio[kMaxViews];
-    uint32_t* cand;               // [nv][cand_cap] packed (y << 16) | x
-    int64_t cand_cap;
-    int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact; null: no tables
-    uint32_t* fb;                 // [nv][fb_words] bit per candidate: left to the warp kernel (null: all are)
-    int64_t fb_words;
-    uint32_t* hdr;                // HDR_WORDS
-    unsigned long long* stats;    // [nv][2]: samples, pair tests
+    int32_t wide;                 // (H - 1) * pitch + W does not fit in int32
+    int32_t pad;
     int32_t* O;                   // [nv][H][W]
     uint8_t* M;                   // [nv][H][W]
     float* E;                     // [H][W] or null
     float* A;                     // [H][W] or null
+    uint32_t* cand;               // [nv][cap] packed (y << 16) | x
+    int64_t cap;
+    uint32_t* fb;                 // [nv][fb_words] bit per candidate: line left to the warp kernel
+    int64_t fb_words;
+    uint32_t* hdr;                // HDR_WORDS
+    unsigned long long* stats;    // [nv][2]: samples, pair tests
+};
+
+// Per (frame, view), written by k_plan.
+struct PlanEntry {
+    int32_t h;       // half scan length h = ceil(L / 2); -1: view skipped (non-finite input or L too long)
+    int32_t cls;     // size class of its scan lines
+    uint32_t count;  // candidates, clamped to the list capacity
+    uint32_t pad;
+};
+
+struct Args {
+    int32_t nf, nv, nr;           // frames, views, distinct ratios
+    float gamma, zeta, beta;
+    int32_t Lover;                // > 0: fixed scan length; else Eq. 3 per frame and view
+    int32_t N;
+    int32_t use_fb;               // the line kernel runs first: the warp kernels take only the lines it flagged
+    int32_t max_quads;            // max over frames of H * ceil(W / 4)
+    int64_t max_px;               // max over frames of n_views * H * W
+    ViewArg view[kMaxViews];
+    float ratio[kMaxViews];
+    const FrameArg* frames;       // [nf]
+    PlanEntry* plan;              // [nf * nv]
+    uint32_t* pref_all;           // [nf * nv + 1] prefix of the candidate counts of every (frame, view)
+    uint32_t* pref_cls;           // [kNumClasses][nf * nv + 1] the same restricted to each size class
+    int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact
+    uint32_t* status;             // OR of every frame's status bits
+};
+
+// At most kFramesPerChunk frame records travel in the parameters of one k_frames launch.
+constexpr int kFramesPerChunk = 32;
+struct FrameChunk {
+    FrameArg* dst;
+    int32_t first, count;
+    FrameArg f[kFramesPerChunk];
 };
 
 // Launchers (occ_kernels.cu).  Each returns the cudaGetLastError() of its launch.
-cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st);
+cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st);
 cudaError_t launch_tables(const Args& a, cudaStream_t st);
-// The line-per-thread scan over every view; wide = true when H * pitch does not fit in int32.
+cudaError_t launch_edges(const Args& a, cudaStream_t st);
+cudaError_t launch_plan(const Args& a, cudaStream_t st);
+// The line-per-thread scan over every view; wide = true when some frame's offsets need 64 bits.
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
-cudaError_t launch_mask(const Args& a, int grid, cudaStream_t st);
-// Per-SM resident blocks of each kernel (for persistent grids); also sets the shared-memory opt-ins.
-cudaError_t configure_kernels(int* edges_blocks_per_sm, int* lines_blocks_per_sm,
-                              int scan_blocks_per_sm[kNumClasses], int* mask_blocks_per_sm);
+cudaError_t launch_mask(const Args& a, cudaStream_t st);
+// Per-SM resident blocks of the persistent scan kernels; also sets the shared-memory opt-ins.
+cudaError_t configure_kernels(int* lines_blocks_per_sm, int scan_blocks_per_sm[kNumClasses]);
+
+}  // namespace occ
+
+namespace occ {
+
+// Device buffers one call works in: a context's scratch, or the fixed array of occ_detect_noalloc.
+struct Scratch {
+    uint32_t* hdr;                 // [max_frames][HDR_WORDS]
+    unsigned long long* stats;     // [max_frames][max_views][2]
+    uint32_t* status;              // one word
+    FrameArg* frames;              // [max_frames]
+    PlanEntry* plan;               // [max_frames * max_views]
+    uint32_t* pref;                // [(1 + kNumClasses) * (max_frames * max_views + 1)]
+    int32_t* ptab;                 // [max_views][kTabLen]
+    uint32_t* cand;                // candidate list pool
+    int64_t cand_entries;
+    uint32_t* fb;                  // line-flag pool (words)
+    int64_t fb_entries;
+    int32_t max_frames, max_views;
+    int32_t grid_lines;
+    int32_t grid_scan[kNumClasses];
+};
+
+// One frame of a call as the caller gives it.
+struct FrameIn {
+    const float* D;
+    int64_t pitch;
+    int32_t H, W;
+    int32_t* O;
+    uint8_t* M;
+    float* E;
+    float* A;
+    int64_t cap;   // candidate list entries per view
+};
+
+// Checks the parameters and views and fills the view part of `a` (directions, ratios).  OCC_OK or
+// OCC_ERR_INVALID_ARG.
+int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p, Args& a);
+
+// Queues the method (Eq. 1-6) for nf validated frames.  ev (profiling) is null or OCC_NUM_STAGES + 1 events.
+// Returns OCC_OK once queued, or OCC_ERR_CUDA.
+int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev);
+
+// Grid sizes of the persistent scan kernels on the current device (also sets their shared-memory opt-ins).
+cudaError_t scratch_grids(Scratch& sc);
 
 }  // namespace occ

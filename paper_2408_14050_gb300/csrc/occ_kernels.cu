@@ -64,13 +64,14 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
     __shared__ float s_lo[kEdgeWarps], s_hi[kEdgeWarps];
     __shared__ int s_bad;
 
+    const FrameArg F = a.frames[blockIdx.y];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int W = a.W, H = a.H;
+    const int W = F.W, H = F.H;
     const int QW = (W + 3) >> 2;
     const int64_t nq = (int64_t)H * QW;
     const int64_t plane = (int64_t)H * W;
-    const bool vecD = ((a.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.D) & 15) == 0);
-    const bool vecO = ((W & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.O) & 15) == 0);
+    const bool vecD = ((F.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.D) & 15) == 0);
+    const bool vecO = ((W & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.O) & 15) == 0);
     const unsigned lt = (1u << lane) - 1u;
 
     if (threadIdx.x == 0) s_bad = 0;
@@ -87,9 +88,9 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
         if (active) {
             y = (int)(q / QW);
             x0 = (int)(q - (int64_t)y * QW) * 4;
-            load_quad(a.D + (int64_t)y * a.pitch, x0, W, vecD, d);
+            load_quad(F.D + (int64_t)y * F.pitch, x0, W, vecD, d);
             hasd = (y + 1 < H);
-            if (hasd) load_quad(a.D + (int64_t)(y + 1) * a.pitch, x0, W, vecD, dn);
+            if (hasd) load_quad(F.D + (int64_t)(y + 1) * F.pitch, x0, W, vecD, dn);
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 valid[j] = (x0 + j < W);
@@ -102,15 +103,15 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
         }
 
         // E and A of D itself (r = 1).
-        if (active && (a.E || a.A)) {
+        if (active && (F.E || F.A)) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 if (!valid[j]) continue;
                 const float ex = (x0 + j + 1 < W) ? __fsub_rn(d[j + 1], d[j]) : 0.0f;
                 const float ey = hasd ? __fsub_rn(dn[j], d[j]) : 0.0f;
                 const int64_t o = (int64_t)y * W + x0 + j;
-                if (a.E) a.E[o] = __fsqrt_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)));
-                if (a.A) a.A[o] = atan2f(ey, ex);
+                if (F.E) F.E[o] = __fsqrt_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)));
+                if (F.A) F.A[o] = atan2f(ey, ex);
             }
         }
 
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
             uint32_t sum = 0;
 #pragma unroll
             for (int w = 0; w < kEdgeWarps; w++) sum += s_tot[w][v];
-            uint32_t base = sum ? atomicAdd(&a.hdr[HDR_COUNT + v], sum) : 0u;
+            uint32_t base = sum ? atomicAdd(&F.hdr[HDR_COUNT + v], sum) : 0u;
 #pragma unroll
             for (int w = 0; w < kEdgeWarps; w++) {
                 s_base[w][v] = base;
@@ -177,10 +178,10 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 if ((bits[j] >> v) & 1ull) {
-                    if ((int64_t)pos < a.cand_cap)
-                        a.cand[(int64_t)v * a.cand_cap + pos] = ((uint32_t)y << 16) | (uint32_t)(x0 + j);
+                    if ((int64_t)pos < F.cap)
+                        F.cand[(int64_t)v * F.cap + pos] = ((uint32_t)y << 16) | (uint32_t)(x0 + j);
                     else
-                        atomicOr(&a.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
+                        atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
                     pos++;
                 }
             }
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
         if (active) {
             const int64_t o = (int64_t)y * W + x0;
             for (int v = 0; v < a.nv; v++) {
-                int32_t* Ov = a.O + (int64_t)v * plane + o;
+                int32_t* Ov = F.O + (int64_t)v * plane + o;
                 if (vecO && x0 + 4 <= W) {
                     *reinterpret_cast<int4*>(Ov) = make_int4(0, 0, 0, 0);
                 } else {
@@ -221,15 +222,130 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
             bhi = fmaxf(bhi, s_hi[w]);
         }
         if (blo <= bhi) {
-            atomicMax(&a.hdr[HDR_MAX], f2ord(bhi));
-            atomicMax(&a.hdr[HDR_NEGMIN], ~f2ord(blo));
+            atomicMax(&F.hdr[HDR_MAX], f2ord(bhi));
+            atomicMax(&F.hdr[HDR_NEGMIN], ~f2ord(blo));
         }
-        if (s_bad) atomicOr(&a.hdr[HDR_STATUS], ST_NONFINITE);
+        if (s_bad) atomicOr(&F.hdr[HDR_STATUS], ST_NONFINITE);
     }
 }
 
 // ------------------------------------------------------------------------------------------------------------------
-// Shared by the scan kernels.
+// k_frames: copies a chunk of frame records from the launch parameters into the device frame table.
+
+__global__ void k_frames(const __grid_constant__ FrameChunk c)
+{
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) c.dst[c.first + i] = c.f[i];
+}
+
+// ------------------------------------------------------------------------------------------------------------------
+// k_plan: per (frame, view) the scan length (Eq. 3 on D_r unless L is fixed), the size class of the scan lines and
+// the candidate count; then the prefix sums that number the scan work items of all (frame, view)s and of each size
+// class.  One block.
+
+constexpr int kPlanThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan(const __grid_constant__ Args a)
+{
+    __shared__ uint32_t s_carry[1 + kNumClasses];
+    __shared__ uint32_t s_warp[kPlanThreads / 32][1 + kNumClasses];
+    const int n = a.nf * a.nv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 1 + kNumClasses) s_carry[threadIdx.x] = 0;
+    uint32_t st_all = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += kPlanThreads) {
+        const int i = base + threadIdx.x;
+        uint32_t cnt[1 + kNumClasses] = {0, 0, 0, 0};
+        if (i < n) {
+            const int f = i / a.nv, v = i - f * a.nv;
+            const FrameArg& F = a.frames[f];
+            const uint32_t st = F.hdr[HDR_STATUS];
+            PlanEntry pe{-1, 0, 0u, 0u};
+            if (!(st & ST_NONFINITE)) {
+                int L;
+                if (a.Lover > 0) {
+                    L = a.Lover;
+                } else {
+                    // Eq. 3 on D_r: max D_r = fl(r max D) and min D_r = fl(r min D) (rounding is monotone).
+                    const float mx = ord2f(F.hdr[HDR_MAX]);
+                    const float mn = ord2f(~F.hdr[HDR_NEGMIN]);
+                    const float r = a.view[v].r;
+                    const float dmx = (r == 1.0f) ? mx : __fmul_rn(r, mx);
+                    const float dmn = (r == 1.0f) ? mn : __fmul_rn(r, mn);
+                    const float t = __fmul_rn(__fsub_rn(dmx, dmn), 2.0f);
+                    L = (t <= (float)OCC_MAX_SCAN) ? (int)ceilf(t) : -1;
+                }
+                if (L < 0) {
+                    atomicOr(&F.hdr[HDR_STATUS], ST_SCAN_TOO_LONG);
+                    st_all |= ST_SCAN_TOO_LONG;
+                } else {
+                    F.hdr[HDR_L + v] = (uint32_t)L;
+                    pe.h = (L + 1) / 2;
+                    const int nk = 2 * pe.h + 1;
+                    pe.cls = nk <= 256 ? 0 : (nk <= 1024 ? 1 : 2);   // kClassCap
+                    uint32_t c = F.hdr[HDR_COUNT + v];
+                    if ((int64_t)c > F.cap) c = (uint32_t)F.cap;
+                    pe.count = c;
+                    cnt[0] = c;
+                    cnt[1 + pe.cls] = c;
+                }
+            }
+            st_all |= st;
+            a.plan[i] = pe;
+        }
+        // Block-wide exclusive scans of the four count vectors.
+        uint32_t incl[1 + kNumClasses];
+#pragma unroll
+        for (int c = 0; c <= kNumClasses; c++) {
+            uint32_t x = cnt[c];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, x, off);
+                if (lane >= off) x += y;
+            }
+            incl[c] = x;
+            if (lane == 31) s_warp[warp][c] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 1 + kNumClasses) {
+            const int c = threadIdx.x;
+            uint32_t run = s_carry[c];
+            for (int w = 0; w < kPlanThreads / 32; w++) {
+                const uint32_t t = s_warp[w][c];
+                s_warp[w][c] = run;
+                run += t;
+            }
+            s_carry[c] = run;
+        }
+        __syncthreads();
+        if (i < n) {
+            const int stride = n + 1;
+            a.pref_all[i] = s_warp[warp][0] + incl[0] - cnt[0];
+#pragma unroll
+            for (int c = 0; c < kNumClasses; c++) a.pref_cls[c * stride + i] = s_warp[warp][1 + c] + incl[1 + c] - cnt[1 + c];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int stride = n + 1;
+        a.pref_all[n] = s_carry[0];
+        for (int c = 0; c < kNumClasses; c++) a.pref_cls[c * stride + n] = s_carry[1 + c];
+    }
+    st_all = __reduce_or_sync(kFull, st_all);
+    if (lane == 0 && st_all) atomicOr(a.status, st_all);
+}
+
+// The (frame, view) index of a scan work item: the last i with pref[i] <= item (pref non-decreasing, pref[0] = 0,
+// item < pref[n]).
+__device__ __forceinline__ int item_owner(const uint32_t* pref, int n, uint32_t item)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (__ldg(pref + m) <= item) lo = m; else hi = m - 1;
+    }
+    return lo;
+}
 
 // Number of (p, d) pairs with d in {-K..K}\{0} and 0 <= p+d < n, summed over p (Eq. 5's neighbour set).
 __device__ __forceinline__ unsigned long long pair_count(int n, int K)
@@ -237,50 +353,6 @@ __device__ __forceinline__ unsigned long long pair_count(int n, int K)
     const long long nn = n, kk = K;
     const long long one_side = (nn <= kk) ? nn * (nn - 1) / 2 : kk * (kk - 1) / 2 + (nn - kk) * kk;
     return (unsigned long long)(2 * one_side);
-}
-
-// Thread 0 of a scan block: the scan length of every view (Eq. 3 on D_r unless L is fixed), and the list and
-// candidate-count prefix of the views whose scan lines (2h+1 samples) fall into size class `cls` (every view when
-// cls < 0).  Returns the number of such views.  A view whose automatic L exceeds OCC_MAX_SCAN sets ST_SCAN_TOO_LONG
-// and is skipped.
-__device__ int scan_views_of_class(const Args& a, int cls, int32_t* s_h, int32_t* s_vid, uint32_t* s_pref)
-{
-    const uint32_t st = a.hdr[HDR_STATUS];
-    int ncls = 0;
-    uint32_t pref = 0;
-    s_pref[0] = 0;
-    if (st & ST_NONFINITE) return 0;
-    const float mx = ord2f(a.hdr[HDR_MAX]);
-    const float mn = ord2f(~a.hdr[HDR_NEGMIN]);
-    for (int v = 0; v < a.nv; v++) {
-        int L;
-        if (a.Lover > 0) {
-            L = a.Lover;
-        } else {
-            // Eq. 3 on D_r: max D_r = fl(r max D) and min D_r = fl(r min D) (rounding is monotone).
-            const float r = a.view[v].r;
-            const float dmx = (r == 1.0f) ? mx : __fmul_rn(r, mx);
-            const float dmn = (r == 1.0f) ? mn : __fmul_rn(r, mn);
-            const float t = __fmul_rn(__fsub_rn(dmx, dmn), 2.0f);
-            L = (t <= (float)OCC_MAX_SCAN) ? (int)ceilf(t) : -1;
-        }
-        if (L < 0) {
-            atomicOr(&a.hdr[HDR_STATUS], ST_SCAN_TOO_LONG);
-            continue;
-        }
-        const int h = (L + 1) / 2;
-        s_h[v] = h;
-        if (blockIdx.x == 0) a.hdr[HDR_L + v] = (uint32_t)L;
-        const int nk = 2 * h + 1;
-        const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
-        if (cls >= 0 && c != cls) continue;
-        uint32_t cnt = a.hdr[HDR_COUNT + v];
-        if ((int64_t)cnt > a.cand_cap) cnt = (uint32_t)a.cand_cap;
-        s_vid[ncls] = v;
-        pref += cnt;
-        s_pref[++ncls] = pref;
-    }
-    return ncls;
 }
 
 // ------------------------------------------------------------------------------------------------------------------
@@ -332,14 +404,15 @@ struct LineSample {
 
 struct LineJob {
     int x, y;       // candidate
-    int v;          // view
+    int f, v;       // frame, view
+    int h;          // half scan length
     int k0, k1;     // first / last k inside the image
     int ks;         // start of the second macro-run
 };
 
 // Sample k of a line; `bounded` = false when k is known to lie inside the image.
 template <bool kWide>
-__device__ __forceinline__ bool line_sample(const Args& a, const ViewArg& va, const int32_t* tab, int cx, int cy,
+__device__ __forceinline__ bool line_sample(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int cx, int cy,
                                             int h, int k, bool bounded, LineSample& out)
 {
     const int t = tab[k - h + kTabHalf];
@@ -351,15 +424,15 @@ __device__ __forceinline__ bool line_sample(const Args& a, const ViewArg& va, co
     } else {
         const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
         const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
-        if (bounded && !((rx >= 0.0f) && (rx < (float)a.W) && (ry >= 0.0f) && (ry < (float)a.H))) return false;
+        if (bounded && !((rx >= 0.0f) && (rx < (float)F.W) && (ry >= 0.0f) && (ry < (float)F.H))) return false;
         px = (int)rx;
         py = (int)ry;
     }
-    if (bounded && !((unsigned)px < (unsigned)a.W && (unsigned)py < (unsigned)a.H)) return false;
-    const float dv = kWide ? __ldg(a.D + (int64_t)py * a.pitch + px) : __ldg(a.D + (py * (int)a.pitch + px));
+    if (bounded && !((unsigned)px < (unsigned)F.W && (unsigned)py < (unsigned)F.H)) return false;
+    const float dv = kWide ? __ldg(F.D + (int64_t)py * F.pitch + px) : __ldg(F.D + (py * (int)F.pitch + px));
     out.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
     out.w = __fsub_rn(g, out.v);
-    out.p = py * a.W + px;
+    out.p = py * F.W + px;
     out.k = k;
     return true;
 }
@@ -367,46 +440,6 @@ __device__ __forceinline__ bool line_sample(const Args& a, const ViewArg& va, co
 __device__ __forceinline__ bool before(const LineSample& x, const LineSample& y)
 {
     return x.w < y.w || (x.w == y.w && x.k < y.k);
-}
-
-// Pass 1.  Returns the number of macro-runs (1 or 2; 3 means "more than two" or a gap in the valid range), the
-// first and last valid k, the start of the second macro-run and the number of valid samples.
-template <bool kWide>
-__device__ __forceinline__ int line_runs(const Args& a, const ViewArg& va, const int32_t* tab, int cx, int cy, int h,
-                                         int& k0, int& k1, int& ks, int& n)
-{
-    const int nk = 2 * h + 1;
-    int runs = 0;
-    LineSample buf{0.f, 0.f, 0, 0}, last{-INFINITY, 0.f, 0, -1}, s;
-    k0 = -1; k1 = -1; ks = -1; n = 0;
-    for (int k = 0; k < nk; k++) {
-        if (!line_sample<kWide>(a, va, tab, cx, cy, h, k, true, s)) continue;
-        if (k0 < 0) k0 = k;
-        k1 = k;
-        n++;
-        if (runs == 0) {
-            buf = s;
-            runs = 1;
-            continue;
-        }
-        if (before(s, buf)) {
-            if (before(s, last)) {          // s would be emitted out of order: it starts a new macro-run
-                if (++runs > 2) return 3;
-                ks = k;
-                buf = s;
-                last.w = -INFINITY;
-                last.k = -1;
-                continue;
-            }
-            last = s;
-        } else {
-            last = buf;
-            buf = s;
-        }
-    }
-    // The valid samples form one interval of k (positions are monotone in g); if not, the warp kernel reports it.
-    if (n > 0 && k1 - k0 + 1 != n) return 3;
-    return runs;
 }
 
 // Eq. 5 / Eq. 6 over the emitted (sorted) stream: a window of the last N/2 samples, slot 0 the most recent.
@@ -461,30 +494,10 @@ __device__ __forceinline__ void window_flush(const LineWindow& W, int32_t* Ov)
     if (W.wn > 3 && W.o3) atomicAdd(Ov + W.p3, W.o3);
 }
 
-// Pass 2 for a single macro-run [k0, k1].
-template <bool kWide>
-__device__ __forceinline__ void line_counts1(const Args& a, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
-                                             int cy, int h, int half, int k0, int k1)
-{
-    LineWindow Wn;
-    window_init(Wn);
-    LineSample buf, s;
-    line_sample<kWide>(a, va, tab, cx, cy, h, k0, false, buf);
-    for (int k = k0 + 1; k <= k1; k++) {
-        line_sample<kWide>(a, va, tab, cx, cy, h, k, false, s);
-        const bool sb = before(s, buf);
-        const LineSample e = sb ? s : buf;
-        if (!sb) buf = s;
-        window_push(Wn, e, half, a.zeta, a.beta, Ov);
-    }
-    window_push(Wn, buf, half, a.zeta, a.beta, Ov);
-    window_flush(Wn, Ov);
-}
-
 // Pass 2 for two macro-runs [k0, ks - 1] and [ks, k1], each read through its own one-slot buffer; the merge emits
 // the smaller head, and the chosen run reads at most one sample per step.
 template <bool kWide>
-__device__ __forceinline__ void line_counts2(const Args& a, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
+__device__ __forceinline__ void line_counts2(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
                                              int cy, int h, int half, int k0, int k1, int ks)
 {
     LineWindow Wn;
@@ -494,19 +507,19 @@ __device__ __forceinline__ void line_counts2(const Args& a, const ViewArg& va, c
     const int ea = ks - 1, eb = k1;
     LineSample bufa, bufb, ha, hb, s;
     bool hba = true, hbb = true;
-    line_sample<kWide>(a, va, tab, cx, cy, h, k0, false, bufa);
-    line_sample<kWide>(a, va, tab, cx, cy, h, ks, false, bufb);
+    line_sample<kWide>(a, F, va, tab, cx, cy, h, k0, false, bufa);
+    line_sample<kWide>(a, F, va, tab, cx, cy, h, ks, false, bufb);
     bool has_a = true, has_b = true;
     // First heads.
     if (kna <= ea) {
-        line_sample<kWide>(a, va, tab, cx, cy, h, kna++, false, s);
+        line_sample<kWide>(a, F, va, tab, cx, cy, h, kna++, false, s);
         if (before(s, bufa)) ha = s; else { ha = bufa; bufa = s; }
     } else {
         ha = bufa;
         hba = false;
     }
     if (knb <= eb) {
-        line_sample<kWide>(a, va, tab, cx, cy, h, knb++, false, s);
+        line_sample<kWide>(a, F, va, tab, cx, cy, h, knb++, false, s);
         if (before(s, bufb)) hb = s; else { hb = bufb; bufb = s; }
     } else {
         hb = bufb;
@@ -522,7 +535,7 @@ __device__ __forceinline__ void line_counts2(const Args& a, const ViewArg& va, c
         LineSample head = buf;
         bool has = false;
         if (kn <= ke) {
-            line_sample<kWide>(a, va, tab, cx, cy, h, kn, false, s);
+            line_sample<kWide>(a, F, va, tab, cx, cy, h, kn, false, s);
             kn++;
             const bool sb = before(s, buf);
             head = sb ? s : buf;
@@ -541,7 +554,7 @@ __device__ __forceinline__ void line_counts2(const Args& a, const ViewArg& va, c
 
 // Pass 1 with the next sample's load issued before the current one is used.
 template <bool kWide>
-__device__ __forceinline__ int line_runs_p(const Args& a, const ViewArg& va, const int32_t* tab, int cx, int cy, int h,
+__device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int cx, int cy, int h,
                                            int& k0, int& k1, int& ks, int& n)
 {
     const int nk = 2 * h + 1;
@@ -561,24 +574,24 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const ViewArg& va, con
             const float g = (float)(k - h);
             const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
             const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
-            if (!((rx >= 0.0f) && (rx < (float)a.W) && (ry >= 0.0f) && (ry < (float)a.H))) return;
+            if (!((rx >= 0.0f) && (rx < (float)F.W) && (ry >= 0.0f) && (ry < (float)F.H))) return;
             px = (int)rx;
             py = (int)ry;
         }
-        if (!((unsigned)px < (unsigned)a.W && (unsigned)py < (unsigned)a.H)) return;
-        pix = py * a.W + px;
-        off = kWide ? (int64_t)py * a.pitch + px : (int64_t)(py * (int)a.pitch + px);
+        if (!((unsigned)px < (unsigned)F.W && (unsigned)py < (unsigned)F.H)) return;
+        pix = py * F.W + px;
+        off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
     };
     int pn;
     int64_t on;
     pos(0, pn, on);
-    float dn = (pn >= 0) ? __ldg(a.D + on) : 0.0f;
+    float dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
     for (int k = 0; k < nk; k++) {
         const int p = pn;
         const float dv = dn;
         if (k + 1 < nk) {
             pos(k + 1, pn, on);
-            dn = (pn >= 0) ? __ldg(a.D + on) : 0.0f;
+            dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
         }
         if (p < 0) continue;
         LineSample s;
@@ -616,7 +629,7 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const ViewArg& va, con
 
 // Pass 2 for a single macro-run [k0, k1], loads one sample ahead.
 template <bool kWide>
-__device__ __forceinline__ void line_counts1_p(const Args& a, const ViewArg& va, const int32_t* tab, int32_t* Ov,
+__device__ __forceinline__ void line_counts1_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov,
                                                int cx, int cy, int h, int half, int k0, int k1)
 {
     LineWindow Wn;
@@ -632,8 +645,8 @@ __device__ __forceinline__ void line_counts1_p(const Args& a, const ViewArg& va,
             px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
             py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
         }
-        pix = py * a.W + px;
-        off = kWide ? (int64_t)py * a.pitch + px : (int64_t)(py * (int)a.pitch + px);
+        pix = py * F.W + px;
+        off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
     };
     auto make = [&](int k, int p, float dv) -> LineSample {
         LineSample s;
@@ -646,18 +659,18 @@ __device__ __forceinline__ void line_counts1_p(const Args& a, const ViewArg& va,
     int pn;
     int64_t on;
     pos(k0, pn, on);
-    float dn = __ldg(a.D + on);
+    float dn = __ldg(F.D + on);
     LineSample buf = make(k0, pn, dn);
     if (k0 + 1 <= k1) {
         pos(k0 + 1, pn, on);
-        dn = __ldg(a.D + on);
+        dn = __ldg(F.D + on);
     }
     for (int k = k0 + 1; k <= k1; k++) {
         const int p = pn;
         const float dv = dn;
         if (k + 1 <= k1) {
             pos(k + 1, pn, on);
-            dn = __ldg(a.D + on);
+            dn = __ldg(F.D + on);
         }
         const LineSample s = make(k, p, dv);
         const bool sb = before(s, buf);
@@ -669,24 +682,19 @@ __device__ __forceinline__ void line_counts1_p(const Args& a, const ViewArg& va,
     window_flush(Wn, Ov);
 }
 
+constexpr int kStatsSmem = 512;   // (frame, view) statistics accumulated in shared memory before going global
+
 template <bool kWide>
-__global__ void __launch_bounds__(kLineThreads) k_scan_lines(const __grid_constant__ Args a)
+__global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_constant__ Args a)
 {
     constexpr int kWarps = kLineThreads / 32;
     constexpr int kQ = 64;                  // per-warp queue of jobs of each kind
-    __shared__ int32_t s_h[kMaxViews];
-    __shared__ int32_t s_vid[kMaxViews];
-    __shared__ uint32_t s_pref[kMaxViews + 1];
-    __shared__ unsigned long long s_st[2 * kMaxViews];
+    __shared__ unsigned long long s_st[2 * kStatsSmem];
     __shared__ LineJob s_q[kWarps][2][kQ];
-    __shared__ int s_ncls;
-    if (threadIdx.x == 0) s_ncls = scan_views_of_class(a, -1, s_h, s_vid, s_pref);
-    for (int i = threadIdx.x; i < 2 * kMaxViews; i += blockDim.x) s_st[i] = 0;
+    const int nfv = a.nf * a.nv;
+    for (int i = threadIdx.x; i < 2 * kStatsSmem; i += blockDim.x) s_st[i] = 0;
     __syncthreads();
-    const int ncls = s_ncls;
-    if (ncls == 0) return;
-    const uint32_t total = s_pref[ncls];
-    const int64_t plane = (int64_t)a.H * a.W;
+    const uint32_t total = a.pref_all[nfv];
     const int half = a.N >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -695,43 +703,55 @@ __global__ void __launch_bounds__(kLineThreads) k_scan_lines(const __grid_consta
     int n1 = 0, n2 = 0;   // queue lengths (warp-uniform)
 
     auto run1 = [&](const LineJob& jb) {
-        line_counts1_p<kWide>(a, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen, a.O + (int64_t)jb.v * plane, jb.x,
-                              jb.y, s_h[jb.v], half, jb.k0, jb.k1);
+        const FrameArg& F = a.frames[jb.f];
+        line_counts1_p<kWide>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                              F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half, jb.k0, jb.k1);
     };
     auto run2 = [&](const LineJob& jb) {
-        line_counts2<kWide>(a, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen, a.O + (int64_t)jb.v * plane, jb.x,
-                            jb.y, s_h[jb.v], half, jb.k0, jb.k1, jb.ks);
+        const FrameArg& F = a.frames[jb.f];
+        line_counts2<kWide>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                            F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half, jb.k0, jb.k1, jb.ks);
+    };
+    int cur = -1;   // (frame, view) of the statistics being accumulated
+    unsigned long long acc_n = 0, acc_p = 0;
+    auto flush = [&]() {
+        if (cur < 0) return;
+        if (cur < kStatsSmem) {
+            atomicAdd(&s_st[2 * cur], acc_n);
+            atomicAdd(&s_st[2 * cur + 1], acc_p);
+        } else {
+            const int f = cur / a.nv, v = cur - f * a.nv;
+            atomicAdd(&a.frames[f].stats[2 * v], acc_n);
+            atomicAdd(&a.frames[f].stats[2 * v + 1], acc_p);
+        }
     };
 
-    int cur_v = -1;
-    unsigned long long acc_n = 0, acc_p = 0;
     const uint64_t stride = (uint64_t)gridDim.x * kLineThreads;
     for (uint64_t b0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; b0 < total; b0 += stride) {
         // Pass 1 for 32 lines, one per lane.
         const uint64_t item = b0 + lane;
         int runs = 0;
-        LineJob jb{0, 0, 0, 0, 0, 0};
+        LineJob jb{0, 0, 0, 0, 0, 0, 0, 0};
         if (item < total) {
-            int j = 0;
-            while (item >= s_pref[j + 1]) j++;
-            const int v = s_vid[j];
-            const int64_t idx = (int64_t)(item - s_pref[j]);
-            const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + idx];
+            const int i = item_owner(a.pref_all, nfv, (uint32_t)item);
+            const int f = i / a.nv, v = i - f * a.nv;
+            const FrameArg& F = a.frames[f];
+            const int64_t idx = (int64_t)(item - a.pref_all[i]);
+            const uint32_t cw = F.cand[(int64_t)v * F.cap + idx];
             jb.x = (int)(cw & 0xFFFFu);
             jb.y = (int)(cw >> 16);
+            jb.f = f;
             jb.v = v;
+            jb.h = a.plan[i].h;
             int n;
-            runs = line_runs_p<kWide>(a, a.view[v], a.ptab + (int64_t)v * kTabLen, jb.x, jb.y, s_h[v], jb.k0, jb.k1,
-                                      jb.ks, n);
+            runs = line_runs_p<kWide>(a, F, a.view[v], a.ptab + (int64_t)v * kTabLen, jb.x, jb.y, jb.h, jb.k0,
+                                      jb.k1, jb.ks, n);
             if (runs > 2) {
-                atomicOr(&a.fb[(int64_t)v * a.fb_words + (idx >> 5)], 1u << (idx & 31));
+                atomicOr(&F.fb[(int64_t)v * F.fb_words + (idx >> 5)], 1u << (idx & 31));
             } else if (runs > 0) {
-                if (v != cur_v) {
-                    if (cur_v >= 0) {
-                        atomicAdd(&s_st[2 * cur_v], acc_n);
-                        atomicAdd(&s_st[2 * cur_v + 1], acc_p);
-                    }
-                    cur_v = v;
+                if (i != cur) {
+                    flush();
+                    cur = i;
                     acc_n = acc_p = 0;
                 }
                 acc_n += (unsigned long long)n;
@@ -759,13 +779,14 @@ __global__ void __launch_bounds__(kLineThreads) k_scan_lines(const __grid_consta
     // Drain the queues.
     if (lane < n1) run1(q1[lane]);
     if (lane < n2) run2(q2[lane]);
-    if (cur_v >= 0) {
-        atomicAdd(&s_st[2 * cur_v], acc_n);
-        atomicAdd(&s_st[2 * cur_v + 1], acc_p);
-    }
+    flush();
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * a.nv; i += blockDim.x)
-        if (s_st[i]) atomicAdd(&a.stats[i], s_st[i]);
+    const int ns = nfv < kStatsSmem ? nfv : kStatsSmem;
+    for (int i = threadIdx.x; i < 2 * ns; i += blockDim.x)
+        if (s_st[i]) {
+            const int fv = i >> 1, f = fv / a.nv, v = fv - f * a.nv;
+            atomicAdd(&a.frames[f].stats[2 * v + (i & 1)], s_st[i]);
+        }
 }
 
 // ------------------------------------------------------------------------------------------------------------------
@@ -822,23 +843,14 @@ template <int CAP, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args a, int cls)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int32_t s_h[kMaxViews];
-    __shared__ int32_t s_vid[kMaxViews];
-    __shared__ uint32_t s_pref[kMaxViews + 1];
-    __shared__ int s_ncls;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ScanSmem<CAP>& S = reinterpret_cast<ScanSmem<CAP>*>(smem_raw)[warp];
-    if (threadIdx.x == 0) s_ncls = scan_views_of_class(a, cls, s_h, s_vid, s_pref);
-    __syncthreads();
-    const int ncls = s_ncls;
-    if (ncls == 0) return;
-    const uint32_t total = s_pref[ncls];
-
-    const int W = a.W, H = a.H;
-    const int64_t plane = (int64_t)H * W;
+    const int nfv = a.nf * a.nv;
+    const uint32_t* pref = a.pref_cls + (int64_t)cls * (nfv + 1);
+    const uint32_t total = pref[nfv];
+    if (total == 0) return;
     const int half = a.N >> 1;
-    const float fW = (float)W, fH = (float)H;
     const float beta = a.beta, zeta = a.zeta;
     const unsigned lt = (1u << lane) - 1u;
 
@@ -846,17 +858,19 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
     unsigned long long acc_n = 0, acc_p = 0;
 
     for (uint64_t item = (uint64_t)blockIdx.x * WPB + warp; item < total; item += (uint64_t)gridDim.x * WPB) {
-        int j = 0;
-        while (item >= s_pref[j + 1]) j++;
-        const int v = s_vid[j];
-        const int64_t idx = (int64_t)(item - s_pref[j]);
-        if (a.fb && !((a.fb[(int64_t)v * a.fb_words + (idx >> 5)] >> (idx & 31)) & 1u)) continue;
-        const uint32_t cw = a.cand[(int64_t)v * a.cand_cap + idx];
+        const int i = item_owner(pref, nfv, (uint32_t)item);
+        const int f = i / a.nv, v = i - f * a.nv;
+        const FrameArg& F = a.frames[f];
+        const int64_t idx = (int64_t)(item - pref[i]);
+        if (a.use_fb && !((F.fb[(int64_t)v * F.fb_words + (idx >> 5)] >> (idx & 31)) & 1u)) continue;
+        const uint32_t cw = F.cand[(int64_t)v * F.cap + idx];
         const ViewArg va = a.view[v];
         const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
         const bool one = (va.r == 1.0f);
-        const int h = s_h[v];
+        const int h = a.plan[i].h;
         const int nk = 2 * h + 1;
+        const int W = F.W;
+        const float fW = (float)F.W, fH = (float)F.H;
 
         // Eq. 4: positions, bounds, V = D_r at the nearest pixel, W = g - V.
         int k0 = -1, kl = -1, n = 0;
@@ -870,7 +884,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                 ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
                 if (ok) {
                     const int px = (int)rx, py = (int)ry;
-                    const float dv = __ldg(a.D + (int64_t)py * a.pitch + px);
+                    const float dv = __ldg(F.D + (int64_t)py * F.pitch + px);
                     const float V = one ? dv : __fmul_rn(va.r, dv);
                     S.uw[k] = __fsub_rn(g, V);
                     S.uv[k] = V;
@@ -886,7 +900,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         }
         // The samples inside the image form one interval of k (positions are monotone in g).
         if (n == 0 || kl - k0 + 1 != n) {
-            if (lane == 0 && n != 0) atomicOr(&a.hdr[HDR_STATUS], ST_INTERNAL);
+            if (lane == 0 && n != 0) atomicOr(a.status, ST_INTERNAL);
             __syncwarp();
             continue;
         }
@@ -1035,19 +1049,20 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         }
         __syncwarp();
         // Eq. 6: add every sample's count to the occlusion sum of its pixel.
-        int32_t* Ov = a.O + (int64_t)v * plane;
+        int32_t* Ov = F.O + (int64_t)v * F.H * F.W;
         for (int q = lane; q < n; q += 32) {
             const int o = cnt_own[q] + cnt_up[q];
             if (o) atomicAdd(Ov + spix[q], o);
         }
 
         if (lane == 0) {
-            if (v != cur_v) {
+            if (i != cur_v) {
                 if (cur_v >= 0) {
-                    atomicAdd(&a.stats[2 * cur_v], acc_n);
-                    atomicAdd(&a.stats[2 * cur_v + 1], acc_p);
+                    const int cf = cur_v / a.nv, cv = cur_v - cf * a.nv;
+                    atomicAdd(&a.frames[cf].stats[2 * cv], acc_n);
+                    atomicAdd(&a.frames[cf].stats[2 * cv + 1], acc_p);
                 }
-                cur_v = v;
+                cur_v = i;
                 acc_n = acc_p = 0;
             }
             acc_n += (unsigned long long)n;
@@ -1056,8 +1071,9 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         __syncwarp();
     }
     if (lane == 0 && cur_v >= 0) {
-        atomicAdd(&a.stats[2 * cur_v], acc_n);
-        atomicAdd(&a.stats[2 * cur_v + 1], acc_p);
+        const int cf = cur_v / a.nv, cv = cur_v - cf * a.nv;
+        atomicAdd(&a.frames[cf].stats[2 * cv], acc_n);
+        atomicAdd(&a.frames[cf].stats[2 * cv + 1], acc_p);
     }
 }
 
@@ -1068,15 +1084,16 @@ constexpr int kMaskThreads = 256;
 
 __global__ void __launch_bounds__(kMaskThreads) k_mask(const __grid_constant__ Args a)
 {
-    const int64_t n = (int64_t)a.nv * a.H * a.W;
+    const FrameArg& F = a.frames[blockIdx.y];
+    const int64_t n = (int64_t)a.nv * F.H * F.W;
     const int64_t stride = (int64_t)gridDim.x * kMaskThreads;
     const int64_t t0 = (int64_t)blockIdx.x * kMaskThreads + threadIdx.x;
-    const bool vec = ((reinterpret_cast<uintptr_t>(a.O) & 15) == 0) && ((reinterpret_cast<uintptr_t>(a.M) & 15) == 0);
+    const bool vec = ((reinterpret_cast<uintptr_t>(F.O) & 15) == 0) && ((reinterpret_cast<uintptr_t>(F.M) & 15) == 0);
     int64_t done = 0;
     if (vec) {
         const int64_t n16 = n >> 4;
-        const int4* O4 = reinterpret_cast<const int4*>(a.O);
-        uint4* M16 = reinterpret_cast<uint4*>(a.M);
+        const int4* O4 = reinterpret_cast<const int4*>(F.O);
+        uint4* M16 = reinterpret_cast<uint4*>(F.M);
         for (int64_t i = t0; i < n16; i += stride) {
             uint32_t w[4];
 #pragma unroll
@@ -1089,7 +1106,7 @@ __global__ void __launch_bounds__(kMaskThreads) k_mask(const __grid_constant__ A
         }
         done = n16 << 4;
     }
-    for (int64_t i = done + t0; i < n; i += stride) a.M[i] = (uint8_t)(a.O[i] > 0);
+    for (int64_t i = done + t0; i < n; i += stride) F.M[i] = (uint8_t)(F.O[i] > 0);
 }
 
 template <int CAP, int WPB>
@@ -1102,7 +1119,7 @@ constexpr int kWpb0 = 8, kWpb1 = 4, kWpb2 = 2;
 
 }  // namespace
 
-cudaError_t configure_kernels(int* edges_bps, int* lines_bps, int scan_bps[kNumClasses], int* mask_bps)
+cudaError_t configure_kernels(int* lines_bps, int scan_bps[kNumClasses])
 {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_scan<256, kWpb0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1111,8 +1128,6 @@ cudaError_t configure_kernels(int* edges_bps, int* lines_bps, int scan_bps[kNumC
                                   (int)scan_smem<1024, kWpb1>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<4096, kWpb2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<4096, kWpb2>())) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(edges_bps, k_edges, kEdgeThreads, 0)) != cudaSuccess)
-        return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false>, kLineThreads, 0)) !=
         cudaSuccess)
         return e;
@@ -1120,14 +1135,13 @@ cudaError_t configure_kernels(int* edges_bps, int* lines_bps, int scan_bps[kNumC
                                                            scan_smem<256, kWpb0>())) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[1], k_scan<1024, kWpb1>, kWpb1 * 32,
                                                            scan_smem<1024, kWpb1>())) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[2], k_scan<4096, kWpb2>, kWpb2 * 32,
-                                                           scan_smem<4096, kWpb2>())) != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(mask_bps, k_mask, kMaskThreads, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[2], k_scan<4096, kWpb2>, kWpb2 * 32,
+                                                         scan_smem<4096, kWpb2>());
 }
 
-cudaError_t launch_edges(const Args& a, int grid, cudaStream_t st)
+cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st)
 {
-    k_edges<<<grid, kEdgeThreads, 0, st>>>(a);
+    k_frames<<<1, kFramesPerChunk, 0, st>>>(c);
     return cudaGetLastError();
 }
 
@@ -1135,6 +1149,21 @@ cudaError_t launch_tables(const Args& a, cudaStream_t st)
 {
     const int64_t total = (int64_t)a.nv * kTabLen;
     k_tables<<<(int)((total + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edges(const Args& a, cudaStream_t st)
+{
+    int bx = (a.max_quads + kEdgeThreads - 1) / kEdgeThreads;
+    if (bx > 2048) bx = 2048;
+    if (bx < 1) bx = 1;
+    k_edges<<<dim3(bx, a.nf), kEdgeThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const Args& a, cudaStream_t st)
+{
+    k_plan<<<1, kPlanThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1155,9 +1184,12 @@ cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_mask(const Args& a, int grid, cudaStream_t st)
+cudaError_t launch_mask(const Args& a, cudaStream_t st)
 {
-    k_mask<<<grid, kMaskThreads, 0, st>>>(a);
+    int64_t bx = a.max_px / (4096 * 4);
+    if (bx > 1024) bx = 1024;
+    if (bx < 1) bx = 1;
+    k_mask<<<dim3((unsigned)bx, a.nf), kMaskThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

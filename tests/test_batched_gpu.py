@@ -1,0 +1,104 @@
+"""occ_detect_batched: many frames of uneven size and the same views in one batch of launches.
+
+Every frame's M and O must equal, bit for bit, both the oracle's and occ_detect's on that frame alone; the batch must
+be capturable into a CUDA graph and give the same results on replay with new inputs; statuses and statistics must
+aggregate over the frames.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2408_14050_gb300 as occ
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = occ.occ_create(0, max_pixels=24 * 1024 * 1024, max_views=8)
+    yield c
+    c.close()
+
+
+def uneven_frames(seed=0):
+    sizes = [(48, 64), (100, 77), (270, 480), (31, 200), (1, 9), (129, 130)]
+    out = []
+    for i, (H, W) in enumerate(sizes):
+        spec = scenes.SceneSpec(H=H, W=W, bg_base=(2.0, 6.0), bg_slope=(2.0, 8.0), n_objects=4, obj_disp=(8.0, 24.0),
+                                obj_size=(0.1, 0.5), d_max=64.0, sigma=0.3)
+        out.append(scenes.make_scene(spec, scenes.seed_of(30 + seed, i)))
+    return out
+
+
+def test_batch_matches_oracle_frame_by_frame(ctx):
+    frames = uneven_frames()
+    views = scenes.views_3x3()
+    Ds = [torch.from_numpy(f).cuda() for f in frames]
+    Ms, Os = occ.occ_detect_batched(ctx, Ds, views)
+    assert occ.occ_get_status(ctx) == occ.OCC_OK
+    stats = occ.occ_get_stats(ctx, len(views))
+    exp_samples = [0] * len(views)
+    for D, M, O in zip(frames, Ms, Os):
+        for v, (a, r) in enumerate(views):
+            Oo, Mo, st = oracle.detect_view(D, a, r)
+            np.testing.assert_array_equal(O[v].cpu().numpy(), Oo)
+            np.testing.assert_array_equal(M[v].cpu().numpy(), Mo)
+            exp_samples[v] += st["samples"]
+    assert [s["samples"] for s in stats] == exp_samples
+
+
+def test_batch_of_mixed_sizes_matches_single_frame_calls(ctx):
+    wl = scenes.mixed_batch(n_frames=6, sizes=[(480, 640), (720, 1280), (1080, 1920)])
+    views = wl.views
+    Ds = [torch.from_numpy(f).cuda() for f in wl.frames]
+    Ms, Os = occ.occ_detect_batched(ctx, Ds, views)
+    assert occ.occ_get_status(ctx) == occ.OCC_OK
+    for D, M, O in zip(Ds, Ms, Os):
+        M1, O1 = occ.occ_detect(ctx, D, views)
+        assert occ.occ_get_status(ctx) == occ.OCC_OK
+        assert torch.equal(O, O1) and torch.equal(M, M1)
+
+
+def test_batch_captured_in_a_cuda_graph(ctx):
+    views = scenes.views_3x3()
+    first = uneven_frames(seed=1)
+    second = uneven_frames(seed=2)
+    Ds = [torch.from_numpy(f).cuda() for f in first]
+    Ms = [torch.empty((len(views), *D.shape), dtype=torch.uint8, device="cuda") for D in Ds]
+    Os = [torch.empty((len(views), *D.shape), dtype=torch.int32, device="cuda") for D in Ds]
+    occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)          # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)
+    for f_np, D in zip(second, Ds):
+        D.copy_(torch.from_numpy(f_np).cuda())
+    g.replay()
+    torch.cuda.synchronize()
+    for f_np, M, O in zip(second, Ms, Os):
+        for v, (a, r) in enumerate(views):
+            Oo, Mo, _ = oracle.detect_view(f_np, a, r)
+            np.testing.assert_array_equal(O[v].cpu().numpy(), Oo)
+            np.testing.assert_array_equal(M[v].cpu().numpy(), Mo)
+
+
+def test_batch_status_is_the_or_of_the_frames(ctx):
+    frames = uneven_frames()
+    frames[2] = frames[2].copy()
+    frames[2][5, 7] = np.nan
+    Ds = [torch.from_numpy(f).cuda() for f in frames]
+    occ.occ_detect_batched(ctx, Ds, [(0.0, 1.0)])
+    assert occ.occ_get_status(ctx) == occ.OCC_ERR_NONFINITE_INPUT
+
+
+def test_batch_argument_checks(ctx):
+    D = torch.zeros((8, 8), dtype=torch.float32, device="cuda")
+    with pytest.raises(occ.OccError):
+        occ.occ_detect_batched(ctx, [D] * 2, [])
+    big = torch.zeros((4096, 4096), dtype=torch.float32, device="cuda")
+    with pytest.raises(occ.OccError):                 # 2 x 16.8 M pixels > max_pixels
+        occ.occ_detect_batched(ctx, [big, big], [(0.0, 1.0)])
