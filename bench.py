@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
+    ap.add_argument("--batched-frames", type=int, default=16,
+                    help="frames of the mixed-size batch measured through a CUDA graph (0: skip)")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -116,6 +119,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------------------------
 # Our arm
 
+# Kernels one occ_detect queues: frame table, position tables, candidates, plan, line-per-thread scan, the three
+# warp scan classes, mask.
+LAUNCHES_PER_DETECT = 9
+
 # DRAM bytes (read + write) per launch of the dominant kernel from the ncu capture summarised in profiles/, valid
 # only for the kernel source it was taken on (sha256 prefix of csrc/occ_kernels.cu); reported as null otherwise.
 MEASURED_TRAFFIC = {"k_scan (scan_256)": {"bytes": 110033920, "kernels_sha": "17c8fbeda97b22c1"}}
@@ -159,6 +166,10 @@ def run_ours(args):
 
     ctx = occ.occ_create(local, max_pixels=H * W, max_views=V)
     D = [torch.from_numpy(f).to(dev) for f in frames]
+    tuning = occ.occ_get_tuning(ctx)[0]
+    if not args.no_autotune:
+        from paper_2408_14050_gb300 import autotune
+        tuning, _ = autotune.autotune(ctx, [D[0]], views, cache_path=None)
     M = [torch.empty((V, H, W), dtype=torch.uint8, device=dev) for _ in frames]
     O = [torch.empty((V, H, W), dtype=torch.int32, device=dev) for _ in frames]
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -255,6 +266,10 @@ def run_ours(args):
                "h2d_bytes_per_step": 4 * H * W, "d2h_bytes_per_step": V * H * W,
                "api": "occ_detect_host (pinned D in, M out, O kept on the device)"}
 
+    batched = None
+    if args.batched_frames > 0:
+        batched = run_batched(args, dev, views, rank, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(frames[0], views, args.cpu_budget)
@@ -268,13 +283,15 @@ def run_ours(args):
                        "views": "alpha 0..315 step 45; ratio 1 axial, sqrt(2) diagonal",
                        "params": "gamma 1.0, zeta 2.0, beta 0.5, L auto (Eq. 3), N 8",
                        "l2": "flushed between timed steps (write of a 322 MB buffer, untimed)",
-                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "tuning": tuning},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * 6,
+            "gpu_launches": args.steps * LAUNCHES_PER_DETECT,
             "clocks": clk,
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
+            "batched": batched,
             "work": {"samples_per_step": samples, "pair_tests_per_step": pairs,
                      "samples_per_s": round(samples / (ms_per_step / 1e3)),
                      "candidates_per_step": sum(s["candidates"] for s in stats)},
@@ -288,6 +305,50 @@ def run_ours(args):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args, dev, views, rank, world):
+    """Mixed-size batch (equal numbers of 640x480, 1280x720, 1920x1080, 4096x2160 maps, eight views) through one
+    occ_detect_batched call captured in a CUDA graph; inputs and outputs exceed L2."""
+    import torch
+
+    import paper_2408_14050_gb300 as occ
+    from paper_2408_14050_gb300 import autotune, shard
+
+    wl = scenes.mixed_batch(n_frames=args.batched_frames)
+    Ds = [torch.from_numpy(f).to(dev) for f in wl.frames]
+    px = sum(int(f.size) for f in wl.frames)
+    V = len(views)
+    ctx = occ.occ_create(dev.index, max_pixels=px, max_views=V)
+    Ms = [torch.empty((V, *D.shape), dtype=torch.uint8, device=dev) for D in Ds]
+    Os = [torch.empty((V, *D.shape), dtype=torch.int32, device=dev) for D in Ds]
+    p = occ.occ_default_params()
+    tuning = occ.occ_get_tuning(ctx)[0]
+    if not args.no_autotune:
+        tuning, _ = autotune.autotune(ctx, Ds, views, reps=2, cache_path=None)
+    occ.occ_detect_batched(ctx, Ds, views, p, Ms=Ms, Os=Os)
+    if occ.occ_get_status(ctx) != occ.OCC_OK:
+        raise RuntimeError("batched detect failed")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        occ.occ_detect_batched(ctx, Ds, views, p, Ms=Ms, Os=Os)
+    for _ in range(3):
+        g.replay()
+    steps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+    if occ.occ_get_status(ctx) != occ.OCC_OK:
+        raise RuntimeError("batched detect failed")
+    ctx.close()
+    return {"value": round(steps * world * px * V / t / 1e6, 1), "unit": UNIT, "ms_per_step": round(t / steps * 1e3, 3),
+            "frames": len(Ds), "pixels_per_frame_set": px, "views": V, "steps": steps, "cuda_graph": True,
+            "tuning": tuning, "l2": "inputs and outputs larger than L2"}
 
 
 # ---------------------------------------------------------------------------------------------------------------

@@ -163,6 +163,27 @@ int occ_get_status(occ_ctx* ctx, void* stream);
  * n_views exceeds the views of that call. */
 int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
 
+/* How the scan work (Eq. 4-6) is mapped onto the GPU; every choice gives bit-identical results, only the speed
+ * differs (paper_2408_14050_gb300/autotune.py picks one per device and workload).
+ *   line_max_runs        scan lines handled one per thread: 0 none (one warp per line for all), 1 lines whose
+ *                        sort needs only adjacent swaps, 2 also lines made of two such stretches (default 2).
+ *                        Ignored (0) when N > 8.
+ *   line_blocks_per_sm   resident 256-thread blocks per multiprocessor of the line-per-thread kernel, 1 .. the
+ *                        occupancy limit (default: the limit).
+ *   warp_lines_per_block lines in flight per block of the one-warp-per-line kernel for lines of <= 256 samples:
+ *                        4 or 8 (default 8). */
+typedef struct {
+    int32_t line_max_runs;
+    int32_t line_blocks_per_sm;
+    int32_t warp_lines_per_block;
+} occ_tuning;
+
+/* Sets the tuning of later calls (NULL: the defaults).  OCC_ERR_INVALID_ARG for out-of-range fields. */
+int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
+
+/* The tuning in effect, with the occupancy limit of line_blocks_per_sm in *max_line_blocks_per_sm (may be NULL). */
+int occ_get_tuning(occ_ctx* ctx, occ_tuning* t, int32_t* max_line_blocks_per_sm);
+
 /* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the
  * line-per-thread scan (Eq. 4-6 for the scan lines whose sort is a set of adjacent swaps; N <= 8), the warp scan
  * kernels of the three scan-line size classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6 for the remaining

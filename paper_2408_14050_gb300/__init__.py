@@ -35,8 +35,8 @@ OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
 OCC_MAX_FRAMES = 1024
 
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
-            "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc",
-            "occ_status_string"]
+            "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning",
+            "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc", "occ_status_string"]
 
 
 class occ_view(ctypes.Structure):
@@ -57,6 +57,15 @@ class occ_view_stats(ctypes.Structure):
     def as_dict(self):
         return {"candidates": int(self.candidates), "samples": int(self.samples),
                 "pair_tests": int(self.pair_tests), "L": int(self.L)}
+
+
+class occ_tuning(ctypes.Structure):
+    """Mapping of the scan work: line_max_runs (0, 1, 2), line_blocks_per_sm, warp_lines_per_block (4, 8)."""
+    _fields_ = [("line_max_runs", ctypes.c_int32), ("line_blocks_per_sm", ctypes.c_int32),
+                ("warp_lines_per_block", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class OccError(RuntimeError):
@@ -104,6 +113,10 @@ def load(build_if_missing: bool = True):
         L.occ_get_status.restype = ctypes.c_int
         L.occ_get_stats.argtypes = [vp, ctypes.POINTER(occ_view_stats), i32]
         L.occ_get_stats.restype = ctypes.c_int
+        L.occ_set_tuning.argtypes = [vp, ctypes.POINTER(occ_tuning)]
+        L.occ_set_tuning.restype = ctypes.c_int
+        L.occ_get_tuning.argtypes = [vp, ctypes.POINTER(occ_tuning), ctypes.POINTER(i32)]
+        L.occ_get_tuning.restype = ctypes.c_int
         L.occ_set_profiling.argtypes = [vp, ctypes.c_int]
         L.occ_set_profiling.restype = ctypes.c_int
         L.occ_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
@@ -320,3 +333,24 @@ def occ_detect_noalloc(D, views, params: occ_params | None = None, M=None, O=Non
     return int(load().occ_detect_noalloc(_ptr(D), H, W, D.stride(0), _views(views), len(views),
                                          ctypes.byref(params) if params is not None else None, _ptr(M), _ptr(O),
                                          _ptr(status), _stream_handle(stream)))
+
+
+def occ_set_tuning(ctx: Context, tuning: dict | None = None):
+    """Apply a tuning (dict with the occ_tuning fields; None: defaults)."""
+    t = None
+    if tuning is not None:
+        t = occ_tuning(int(tuning["line_max_runs"]), int(tuning["line_blocks_per_sm"]),
+                       int(tuning["warp_lines_per_block"]))
+    rc = load().occ_set_tuning(ctx.handle, ctypes.byref(t) if t is not None else None)
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_set_tuning")
+
+
+def occ_get_tuning(ctx: Context):
+    """(tuning dict, occupancy limit of line_blocks_per_sm)."""
+    t = occ_tuning()
+    m = ctypes.c_int32()
+    rc = load().occ_get_tuning(ctx.handle, ctypes.byref(t), ctypes.byref(m))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_get_tuning")
+    return t.as_dict(), int(m.value)

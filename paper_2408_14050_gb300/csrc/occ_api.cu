@@ -87,22 +87,27 @@ int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p_in
 
 cudaError_t scratch_grids(Scratch& sc)
 {
-    int dev = 0, sms = 0, bps_lines = 0, bps_scan[kNumClasses] = {0, 0, 0};
+    int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = configure_kernels(&bps_lines, bps_scan);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sc.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = configure_kernels(&sc.lines_bps_max, sc.scan_bps);
     if (e != cudaSuccess) return e;
-    sc.grid_lines = sms * (bps_lines > 0 ? bps_lines : 1);
-    for (int c = 0; c < kNumClasses; c++) sc.grid_scan[c] = sms * (bps_scan[c] > 0 ? bps_scan[c] : 1);
+    if (sc.lines_bps_max < 1) sc.lines_bps_max = 1;
+    for (int c = 0; c <= kNumClasses; c++)
+        if (sc.scan_bps[c] < 1) sc.scan_bps[c] = 1;
+    sc.tuning.line_max_runs = 2;
+    sc.tuning.line_blocks_per_sm = sc.lines_bps_max;
+    sc.tuning.warp_lines_per_block = 8;
     return cudaSuccess;
 }
 
 int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev)
 {
     const int nv = a.nv;
-    const bool lines = (a.N / 2) <= kLineMaxHalf;
+    const bool lines = (a.N / 2) <= kLineMaxHalf && sc.tuning.line_max_runs > 0;
     a.nf = nf;
     a.use_fb = lines ? 1 : 0;
+    a.line_max_runs = sc.tuning.line_max_runs;
     a.frames = sc.frames;
     a.plan = sc.plan;
     a.pref_all = sc.pref;
@@ -167,10 +172,12 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
         launch_plan(a, st) != cudaSuccess || !mark(1))
         return OCC_ERR_CUDA;
-    if (lines && launch_scan_lines(a, sc.grid_lines, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
+    if (lines && launch_scan_lines(a, sc.sms * sc.tuning.line_blocks_per_sm, wide, st) != cudaSuccess)
+        return OCC_ERR_CUDA;
     if (!mark(2)) return OCC_ERR_CUDA;
     for (int c = 0; c < kNumClasses; c++) {
-        if (run_cls[c] && launch_scan(a, c, sc.grid_scan[c], st) != cudaSuccess) return OCC_ERR_CUDA;
+        const int id = (c == 0 && sc.tuning.warp_lines_per_block == 4) ? kNumClasses : c;
+        if (run_cls[c] && launch_scan(a, id, sc.sms * sc.scan_bps[id], st) != cudaSuccess) return OCC_ERR_CUDA;
         if (!mark(3 + c)) return OCC_ERR_CUDA;
     }
     if (launch_mask(a, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
@@ -391,6 +398,26 @@ int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, co
     }
     std::free(fr);
     return rc;
+}
+
+int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t)
+{
+    if (!ctx) return OCC_ERR_INVALID_ARG;
+    occ_tuning d{2, ctx->sc.lines_bps_max, 8};
+    if (!t) t = &d;
+    if (t->line_max_runs < 0 || t->line_max_runs > 2 || t->line_blocks_per_sm < 1 ||
+        t->line_blocks_per_sm > ctx->sc.lines_bps_max || (t->warp_lines_per_block != 4 && t->warp_lines_per_block != 8))
+        return OCC_ERR_INVALID_ARG;
+    ctx->sc.tuning = *t;
+    return OCC_OK;
+}
+
+int occ_get_tuning(occ_ctx* ctx, occ_tuning* t, int32_t* max_line_blocks_per_sm)
+{
+    if (!ctx || !t) return OCC_ERR_INVALID_ARG;
+    *t = ctx->sc.tuning;
+    if (max_line_blocks_per_sm) *max_line_blocks_per_sm = ctx->sc.lines_bps_max;
+    return OCC_OK;
 }
 
 int occ_set_profiling(occ_ctx* ctx, int enable)

@@ -83,6 +83,7 @@ struct Args {
     int32_t Lover;                // > 0: fixed scan length; else Eq. 3 per frame and view
     int32_t N;
     int32_t use_fb;               // the line kernel runs first: the warp kernels take only the lines it flagged
+    int32_t line_max_runs;        // the line kernel keeps lines of at most this many macro-runs (1 or 2)
     int32_t max_quads;            // max over frames of H * ceil(W / 4)
     int64_t max_px;               // max over frames of n_views * H * W
     ViewArg view[kMaxViews];
@@ -110,10 +111,12 @@ cudaError_t launch_edges(const Args& a, cudaStream_t st);
 cudaError_t launch_plan(const Args& a, cudaStream_t st);
 // The line-per-thread scan over every view; wide = true when some frame's offsets need 64 bits.
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);
+// cls = kNumClasses launches the class-0 kernel with 4-warp blocks.
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, cudaStream_t st);
-// Per-SM resident blocks of the persistent scan kernels; also sets the shared-memory opt-ins.
-cudaError_t configure_kernels(int* lines_blocks_per_sm, int scan_blocks_per_sm[kNumClasses]);
+// Per-SM resident blocks of the persistent scan kernels (kNumClasses + 1 warp variants); also sets the shared-memory
+// opt-ins.
+cudaError_t configure_kernels(int* lines_blocks_per_sm, int scan_blocks_per_sm[kNumClasses + 1]);
 
 }  // namespace occ
 
@@ -133,8 +136,10 @@ struct Scratch {
     uint32_t* fb;                  // line-flag pool (words)
     int64_t fb_entries;
     int32_t max_frames, max_views;
-    int32_t grid_lines;
-    int32_t grid_scan[kNumClasses];
+    int32_t sms;                   // multiprocessors of the device
+    int32_t lines_bps_max;         // resident blocks per SM of the line kernel
+    int32_t scan_bps[kNumClasses + 1];  // of the warp kernels (classes 0, 1, 2, then class 0 with 4-warp blocks)
+    occ_tuning tuning;             // mapping and grid choices (occ_set_tuning)
 };
 
 // One frame of a call as the caller gives it.
@@ -157,7 +162,8 @@ int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p, A
 // Returns OCC_OK once queued, or OCC_ERR_CUDA.
 int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev);
 
-// Grid sizes of the persistent scan kernels on the current device (also sets their shared-memory opt-ins).
+// Occupancy of the persistent scan kernels on the current device (also sets their shared-memory opt-ins) and the
+// default tuning.
 cudaError_t scratch_grids(Scratch& sc);
 
 }  // namespace occ

@@ -746,7 +746,7 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
             int n;
             runs = line_runs_p<kWide>(a, F, a.view[v], a.ptab + (int64_t)v * kTabLen, jb.x, jb.y, jb.h, jb.k0,
                                       jb.k1, jb.ks, n);
-            if (runs > 2) {
+            if (runs > a.line_max_runs) {
                 atomicOr(&F.fb[(int64_t)v * F.fb_words + (idx >> 5)], 1u << (idx & 31));
             } else if (runs > 0) {
                 if (i != cur) {
@@ -758,6 +758,7 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
                 acc_p += pair_count(n, half);
             }
         }
+        if (runs > a.line_max_runs) runs = 0;
         // Queue the lines by kind (warp-level compaction).
         const unsigned m1 = __ballot_sync(kFull, runs == 1), m2 = __ballot_sync(kFull, runs == 2);
         if (runs == 1) q1[n1 + __popc(m1 & lt)] = jb;
@@ -1115,13 +1116,17 @@ constexpr size_t scan_smem()
     return sizeof(ScanSmem<CAP>) * WPB;
 }
 
-constexpr int kWpb0 = 8, kWpb1 = 4, kWpb2 = 2;
+constexpr int kWpb0 = 8, kWpb0s = 4, kWpb1 = 4, kWpb2 = 2;
 
 }  // namespace
 
-cudaError_t configure_kernels(int* lines_bps, int scan_bps[kNumClasses])
+cudaError_t configure_kernels(int* lines_bps, int scan_bps[kNumClasses + 1])
 {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_scan<256, kWpb0s>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)scan_smem<256, kWpb0s>())) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[kNumClasses], k_scan<256, kWpb0s>, kWpb0s * 32,
+                                                           scan_smem<256, kWpb0s>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<256, kWpb0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<256, kWpb0>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<1024, kWpb1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1179,7 +1184,8 @@ cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st)
     switch (cls) {
     case 0: k_scan<256, kWpb0><<<grid, kWpb0 * 32, scan_smem<256, kWpb0>(), st>>>(a, 0); break;
     case 1: k_scan<1024, kWpb1><<<grid, kWpb1 * 32, scan_smem<1024, kWpb1>(), st>>>(a, 1); break;
-    default: k_scan<4096, kWpb2><<<grid, kWpb2 * 32, scan_smem<4096, kWpb2>(), st>>>(a, 2); break;
+    case 2: k_scan<4096, kWpb2><<<grid, kWpb2 * 32, scan_smem<4096, kWpb2>(), st>>>(a, 2); break;
+    default: k_scan<256, kWpb0s><<<grid, kWpb0s * 32, scan_smem<256, kWpb0s>(), st>>>(a, 0); break;
     }
     return cudaGetLastError();
 }
