@@ -88,6 +88,11 @@ def lib():
                                               ctypes.c_float, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               f32p, f32p, i32p, i64p, ctypes.c_int32]
             L.ora_scanline_sorted.restype = ctypes.c_int32
+            L.ora_median.argtypes = [ctypes.POINTER(f32p), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, f32p]
+            L.ora_median.restype = ctypes.c_int
+            L.ora_warp_view.argtypes = [f32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_float, f32p,
+                                        u8p, f32p]
+            L.ora_warp_view.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -199,3 +204,32 @@ def scanline_sorted(D, alpha_deg: float, ratio: float, L: int, cx: int, cy: int)
     if n < 0:
         raise ValueError("scan line longer than expected")
     return w[:n], v[:n], k[:n], pix[:n]
+
+
+def median(maps):
+    """Pixel-wise median of n maps [H][W] (Section 4.2); even n: fl(a + b) * 0.5 of the two middle values."""
+    maps = [_map(m) for m in maps]
+    H, W = maps[0].shape
+    arr = (ctypes.POINTER(ctypes.c_float) * len(maps))(*[_ptr(m, ctypes.c_float) for m in maps])
+    out = np.empty((H, W), np.float32)
+    rc = lib().ora_median(arr, len(maps), H, W, _ptr(out, ctypes.c_float))
+    if rc != OK:
+        raise ValueError(f"oracle median failed: {rc}")
+    return out
+
+
+def warp_view(D, alpha_deg: float, ratio: float, img, M=None):
+    """Backward warp of a peripheral image into the center view, bilinear, occluded / outside pixels 0 (Section 1)."""
+    D = _map(D)
+    img = _map(img)
+    H, W = D.shape
+    out = np.empty((H, W), np.float32)
+    Mp = None
+    if M is not None:
+        M = np.ascontiguousarray(M, dtype=np.uint8)
+        Mp = _ptr(M, ctypes.c_uint8)
+    rc = lib().ora_warp_view(_ptr(D, ctypes.c_float), H, W, float(alpha_deg), float(ratio), _ptr(img, ctypes.c_float),
+                             Mp, _ptr(out, ctypes.c_float))
+    if rc != OK:
+        raise ValueError(f"oracle warp failed: {rc}")
+    return out

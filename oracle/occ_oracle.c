@@ -316,3 +316,76 @@ int32_t ora_scanline_sorted(const float* D, int32_t H, int32_t W, double alpha_d
     free(buf);
     return n <= cap ? n : -1;
 }
+
+/*
+ * Pixel-wise median of n disparity maps (Section 4.2: the stereo disparities of the peripheral cameras fused into
+ * one center map).  maps: n pointers to [H][W].  For even n the median is the mean of the two middle order
+ * statistics, fl(a + b) * 0.5 (reading: the paper names a median and gives no rule for an even count).
+ */
+static int cmp_float(const void* pa, const void* pb)
+{
+    float a = *(const float*)pa, b = *(const float*)pb;
+    return (a > b) - (a < b);
+}
+
+int ora_median(const float* const* maps, int32_t n, int32_t H, int32_t W, float* out)
+{
+    if (n < 1 || n > 64 || H < 1 || W < 1) return ORA_ERR_ARG;
+    float v[64];
+    for (int64_t i = 0; i < (int64_t)H * W; i++) {
+        for (int32_t m = 0; m < n; m++) {
+            v[m] = maps[m][i];
+            if (!isfinite(v[m])) return ORA_ERR_NONFINITE;
+        }
+        qsort(v, (size_t)n, sizeof(float), cmp_float);
+        if (n & 1) {
+            out[i] = v[n / 2];
+        } else {
+            float s = v[n / 2 - 1] + v[n / 2];
+            out[i] = s * 0.5f;
+        }
+    }
+    return ORA_OK;
+}
+
+/*
+ * Backward warp of one peripheral view into the center view (Section 1: the registration step whose occluded pixels
+ * the mask marks).  The center pixel (x, y) of disparity d = fl(r D[y][x]) was seen by the peripheral camera at
+ * (x - cos(alpha) d, y - sin(alpha) d) (reading R1: content moves by -r D along alpha); its value is the bilinear
+ * interpolation of the peripheral image there, evaluated as
+ *   top = I00 + fx (I01 - I00), bottom = I10 + fx (I11 - I10), value = top + fy (bottom - top)
+ * with one binary32 rounding per operation.  Pixels marked in M (occluded) and positions outside
+ * [0, W-1] x [0, H-1] get 0.  img: [H][W] binary32.  M: [H][W] uint8 or NULL.  out: [H][W].
+ */
+int ora_warp_view(const float* D, int32_t H, int32_t W, double alpha_deg, float r, const float* img,
+                  const uint8_t* M, float* out)
+{
+    if (H < 1 || W < 1 || !(r > 0.0f)) return ORA_ERR_ARG;
+    float c, s;
+    ora_direction(alpha_deg, &c, &s);
+    for (int64_t y = 0; y < H; y++) {
+        for (int64_t x = 0; x < W; x++) {
+            int64_t i = y * W + x;
+            out[i] = 0.0f;
+            if (M && M[i]) continue;
+            float d = r * D[i];
+            float dx = c * d;
+            float dy = s * d;
+            float sx = (float)x - dx;
+            float sy = (float)y - dy;
+            if (!(sx >= 0.0f && sx <= (float)(W - 1) && sy >= 0.0f && sy <= (float)(H - 1))) continue;
+            float fx0 = floorf(sx), fy0 = floorf(sy);
+            int64_t x0 = (int64_t)fx0, y0 = (int64_t)fy0;
+            int64_t x1 = x0 + 1 < W ? x0 + 1 : x0;
+            int64_t y1 = y0 + 1 < H ? y0 + 1 : y0;
+            float fx = sx - fx0;
+            float fy = sy - fy0;
+            float i00 = img[y0 * W + x0], i01 = img[y0 * W + x1];
+            float i10 = img[y1 * W + x0], i11 = img[y1 * W + x1];
+            float top = i00 + fx * (i01 - i00);
+            float bot = i10 + fx * (i11 - i10);
+            out[i] = top + fy * (bot - top);
+        }
+    }
+    return ORA_OK;
+}

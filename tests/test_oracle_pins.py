@@ -399,3 +399,56 @@ def test_nonfinite_input_is_rejected():
     D[3, 4] = np.inf
     with pytest.raises(ValueError):
         oracle.detect_view(D, 0.0, 1.0, params())
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Disparity fusion (Section 4.2) and the backward warp of the registration (Section 1)
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 9])
+def test_median_matches_numpy(n):
+    rng = np.random.default_rng(n)
+    maps = [rng.normal(20, 5, (13, 17)).astype(np.float32) for _ in range(n)]
+    got = oracle.median(maps)
+    st = np.sort(np.stack(maps), axis=0)
+    if n % 2:
+        exp = st[n // 2]
+    else:
+        exp = ((st[n // 2 - 1] + st[n // 2]).astype(np.float32) * np.float32(0.5)).astype(np.float32)
+    np.testing.assert_array_equal(got, exp)
+    np.testing.assert_allclose(got, np.median(np.stack(maps), axis=0), rtol=1e-6)
+
+
+def test_median_of_equal_maps_is_the_map():
+    D = small_scene(20, 30, frame=9)
+    np.testing.assert_array_equal(oracle.median([D] * 8), D)
+
+
+def test_warp_constant_integer_disparity_is_a_shift():
+    # d = 3 everywhere, alpha = 0: the center pixel x shows the peripheral pixel x - 3 exactly (fx = fy = 0).
+    H, W = 10, 16
+    img = np.arange(H * W, dtype=np.float32).reshape(H, W)
+    D = np.full((H, W), 3.0, np.float32)
+    out = oracle.warp_view(D, 0.0, 1.0, img)
+    exp = np.zeros_like(img)
+    exp[:, 3:] = img[:, :-3]
+    np.testing.assert_array_equal(out, exp)
+    out = oracle.warp_view(D, 90.0, 1.0, img)            # alpha = 90: rows shift
+    exp = np.zeros_like(img)
+    exp[3:, :] = img[:-3, :]
+    np.testing.assert_array_equal(out, exp)
+    np.testing.assert_array_equal(oracle.warp_view(np.zeros((H, W), np.float32), 33.0, 1.7, img), img)
+
+
+def test_warp_half_pixel_is_the_mean_and_mask_zeroes():
+    H, W = 6, 9
+    rng = np.random.default_rng(4)
+    img = rng.integers(0, 100, (H, W)).astype(np.float32)
+    D = np.full((H, W), 0.5, np.float32)
+    out = oracle.warp_view(D, 180.0, 1.0, img)           # alpha = 180: sample at x + 0.5
+    exp = np.zeros_like(img)
+    exp[:, :-1] = img[:, :-1] + np.float32(0.5) * (img[:, 1:] - img[:, :-1])
+    np.testing.assert_array_equal(out, exp)
+    M = np.zeros((H, W), np.uint8)
+    M[2, 3] = 1
+    out = oracle.warp_view(D, 180.0, 1.0, img, M)
+    assert out[2, 3] == 0 and out[2, 2] == exp[2, 2]
