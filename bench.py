@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--batched-frames", type=int, default=16,
                     help="frames of the mixed-size batch measured through a CUDA graph (0: skip)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fusion", action="store_true", help="skip the median-fusion / backward-warp measurement")
     return ap.parse_args()
 
 
@@ -186,7 +187,14 @@ def run_ours(args):
     status = occ.occ_get_status(ctx, stream)
     if status != occ.OCC_OK:
         raise RuntimeError(f"detect failed: {occ.occ_status_string(status)}")
-    stats = occ.occ_get_stats(ctx, V)
+    # Work counts of each frame in the rotation (the timed steps cycle through them evenly when steps is a multiple
+    # of the frame count; the mean is used either way).
+    per_frame = []
+    for j in range(len(frames)):
+        step(j)
+        per_frame.append(occ.occ_get_stats(ctx, V))
+    stats = [{k: sum(pf[v][k] for pf in per_frame) / len(per_frame) for k in ("samples", "pair_tests", "candidates")}
+             for v in range(V)]
 
     occ.occ_set_profiling(ctx, True)
     start = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -227,8 +235,8 @@ def run_ours(args):
     groups = {"scan": scan_ms, **{k: v for k, v in mean_stage.items() if not k.startswith("scan")}}
     dom = max(groups, key=groups.get)
     hbm_peak, peak_src = peaks()
-    samples = sum(s["samples"] for s in stats)
-    pairs = sum(s["pair_tests"] for s in stats)
+    samples = round(sum(s["samples"] for s in stats))
+    pairs = round(sum(s["pair_tests"] for s in stats))
     step_bytes = algorithmic_bytes(H, W, V)
     alu_peak = 152 * 128 * 2.07e9   # FP32/INT32 lane operations per second at the maximum SM clock
     if dom == "scan":
@@ -275,6 +283,7 @@ def run_ours(args):
     batched = None
     if args.batched_frames > 0:
         batched = run_batched(args, dev, views, rank, world)
+    fusion = None if args.no_fusion else run_fusion(args, dev, frames[0], views)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,9 +307,11 @@ def run_ours(args):
             "clocks": clk,
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
             "batched": batched,
+            "fusion_and_warp": fusion,
             "work": {"samples_per_step": samples, "pair_tests_per_step": pairs,
                      "samples_per_s": round(samples / (ms_per_step / 1e3)),
-                     "candidates_per_step": sum(s["candidates"] for s in stats)},
+                     "candidates_per_step": round(sum(s["candidates"] for s in stats)),
+                     "frames_averaged": len(frames)},
             "hbm_step": {"algorithmic_bytes": step_bytes,
                          "achieved_gbs": round(step_bytes / (ms_per_step / 1e3) / 1e9, 1),
                          "peak_gbs": hbm_peak, "frac": round(step_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak, 4),
@@ -355,6 +366,50 @@ def run_batched(args, dev, views, rank, world):
     return {"value": round(steps * world * px * V / t / 1e6, 1), "unit": UNIT, "ms_per_step": round(t / steps * 1e3, 3),
             "frames": len(Ds), "pixels_per_frame_set": px, "views": V, "steps": steps, "cuda_graph": True,
             "tuning": tuning, "l2": "inputs and outputs larger than L2"}
+
+
+def run_fusion(args, dev, frame, views):
+    """The steps around the detection on the bench frame: the median fusion of eight stereo maps into D (Section 4.2)
+    and the masked backward warp of eight peripheral images (Section 1).  Each is timed alone with CUDA events, L2
+    flushed before every launch, and reported against the measured HBM bandwidth by its algorithmic bytes."""
+    import torch
+
+    import paper_2408_14050_gb300 as occ
+
+    H, W = frame.shape
+    V = len(views)
+    maps = [torch.from_numpy(m).to(dev) for m in scenes.stereo_maps(frame, V, seed=scenes.seed_of(60, 0))]
+    imgs = [torch.from_numpy(i).to(dev) for i in scenes.peripheral_images(H, W, V, seed=scenes.seed_of(61, 0))]
+    D = torch.empty((H, W), dtype=torch.float32, device=dev)
+    st = torch.zeros((1,), dtype=torch.int32, device=dev)
+    ctx = occ.occ_create(dev.index, max_pixels=H * W, max_views=V)
+    M, _ = occ.occ_detect(ctx, torch.from_numpy(frame).to(dev), views)
+    out = torch.empty((V, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    hbm_peak, _ = peaks()
+    steps = max(3, min(args.steps, 50))
+    res = {}
+    for name, fn, nbytes in (
+            ("median", lambda: occ.occ_fuse_median(maps, D=D, status=st), (4 * V + 4) * H * W),
+            ("warp", lambda: occ.occ_warp_views(D, views, imgs, M=M, out=out), (4 + 9 * V) * H * W)):
+        for _ in range(3):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+        torch.cuda.synchronize()
+        ms = statistics.fmean(a.elapsed_time(b) for a, b in ev)
+        gbs = nbytes / (ms / 1e3) / 1e9
+        res[name] = {"ms": round(ms, 4), "algorithmic_bytes": nbytes, "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / hbm_peak, 4), "launches": 1}
+    if int(st.item()) != occ.OCC_OK:
+        raise RuntimeError("median fusion reported non-finite input")
+    ctx.close()
+    res["config"] = f"{W}x{H}, {V} stereo maps -> D; {V} views warped with their masks; L2 flushed before each launch"
+    return res
 
 
 # ---------------------------------------------------------------------------------------------------------------

@@ -230,6 +230,60 @@ int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
 int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views, int32_t n_views,
                        const occ_params* p, uint8_t* M, int32_t* O, int32_t* status, void* stream);
 
+/*
+ * The fused center map D as the pixel-wise median of the n_maps stereo disparity maps that the peripheral cameras
+ * give for the center view (Section 4.2: the maps are fused by a pixel-wise median before the detection runs).
+ * maps: n_maps (1..64) device pointers, each a binary32 [H][pitch] map (pitch in elements, 0 = W), read only.
+ * D: device binary32 [H][d_pitch] output (0 = W); it may be one of the maps only if d_pitch equals pitch.  For odd
+ * n_maps the result is the middle value; for even n_maps fl(fl(a + b) * 0.5) of the two middle values; a zero of
+ * either sign counts as +0.  Runs on the current CUDA device, asynchronously on `stream`; allocates nothing.
+ * status (device int32, or NULL) receives, in stream order, 0, or OCC_ERR_NONFINITE_INPUT when some map holds a NaN
+ * or an infinity (D is then unspecified).  Returns OCC_OK once queued, OCC_ERR_INVALID_ARG for bad arguments (NULL
+ * or misaligned pointers, sizes out of range), OCC_ERR_CUDA if the launch fails.
+ */
+int occ_fuse_median(const float* const* maps, int32_t n_maps, int32_t H, int32_t W, int64_t pitch, float* D,
+                    int64_t d_pitch, int32_t* status, void* stream);
+
+/*
+ * Backward warp of the peripheral images to the center view (Section 1: every view is warped to the center view;
+ * Section 4.2: the pixels the detection marks are the ones left for reconstruction).  For view v (alpha, ratio r as
+ * in occ_detect) the center pixel (x, y) takes the bilinear interpolation of images[v] at
+ * (x - cos(alpha) fl(r D), y - sin(alpha) fl(r D)), evaluated as top = I00 + fx (I01 - I00), bottom = I10 + fx
+ * (I11 - I10), top + fy (bottom - top) with one binary32 rounding per operation and the upper neighbours clamped to
+ * the last row / column; pixels with M[v] != 0, positions outside [0, W-1] x [0, H-1] and non-finite D give 0.
+ * D: device binary32 [H][pitch] (0 = W).  images: n_views (1..64) device pointers to binary32 [H][img_pitch]
+ * (0 = W).  M: device uint8 [n_views][H][W] (the mask of occ_detect), or NULL for no mask.  out: device binary32
+ * [n_views][H][W]; it must not overlap the inputs.  Runs on the current CUDA device, asynchronously on `stream`;
+ * allocates nothing.  Returns OCC_OK once queued, OCC_ERR_INVALID_ARG for bad arguments (NULL or misaligned
+ * pointers, a ratio that is not finite and positive, sizes out of range), OCC_ERR_CUDA if the launch fails.
+ */
+int occ_warp_views(const float* D, int32_t H, int32_t W, int64_t pitch, const occ_view* views, int32_t n_views,
+                   const float* const* images, int64_t img_pitch, const uint8_t* M, float* out, void* stream);
+
+/* Side of the square pixel tiles of occ_detect_batched_tiles (proposals and hit flags). */
+#define OCC_TILE 32
+
+/*
+ * occ_detect_batched with per-tile control of the candidates, for the learned tile proposer (a concrete form of the
+ * paper's closing remark that thinning the candidate list would cut the runtime further) and for its training labels.
+ * The frame is cut into tiles of OCC_TILE x OCC_TILE pixels, tiles_x = ceil(W / OCC_TILE) by tiles_y =
+ * ceil(H / OCC_TILE) (the last row and column of tiles may be partial); a candidate belongs to the tile of its own
+ * pixel.
+ *   proposal   n_frames pointers (or NULL for "every tile" in all frames; an individual NULL likewise), each to a
+ *              device uint8 [n_views][tiles_y][tiles_x]: 0 = the scan lines of the candidates of that tile and view
+ *              are not walked (Eq. 4-6 skip them), non-zero = they are.  With every entry non-zero the results equal
+ *              occ_detect_batched's.  Otherwise M and O equal the method run on the candidate list restricted to the
+ *              proposed tiles.
+ *   tile_hits  n_frames pointers (or NULL), each to a device uint8 [n_views][tiles_y][tiles_x] that receives 1 where
+ *              at least one scan line walked from a candidate of the tile added a non-zero count to O (Eq. 5-6), else
+ *              0: the per-tile label "the tile's candidates find an occlusion" of the plain method.
+ * Everything else is as for occ_detect_batched.
+ */
+int occ_detect_batched_tiles(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H,
+                             const int32_t* W, const occ_view* views, int32_t n_views, const occ_params* p,
+                             const uint8_t* const* proposal, uint8_t* const* M, int32_t* const* O,
+                             uint8_t* const* tile_hits, void* stream);
+
 /* A static, human-readable name of a status code. */
 const char* occ_status_string(int status);
 

@@ -233,3 +233,33 @@ def warp_view(D, alpha_deg: float, ratio: float, img, M=None):
     if rc != OK:
         raise ValueError(f"oracle warp failed: {rc}")
     return out
+
+
+def tile_mask(H: int, W: int, table, T: int = 32) -> np.ndarray:
+    """uint8 [H][W] pixel mask that is 1 on the tiles where table [ceil(H/T)][ceil(W/T)] is non-zero."""
+    table = np.asarray(table)
+    return np.kron(table != 0, np.ones((T, T), dtype=bool))[:H, :W].astype(np.uint8)
+
+
+def detect_view_proposed(D, alpha_deg: float, ratio: float, params: Params | None, proposal, T: int = 32):
+    """The method with the candidate list of Eq. 2 restricted to the tiles where proposal [tiles_y][tiles_x] is
+    non-zero (a candidate belongs to the tile of its pixel).  Returns (O, M)."""
+    D = _map(D)
+    O, _ = detect_view_masked(D, alpha_deg, ratio, params, tile_mask(*D.shape, proposal, T))
+    return O, (O > 0).astype(np.uint8)
+
+
+def tile_labels(D, alpha_deg: float, ratio: float, params: Params | None = None, T: int = 32) -> np.ndarray:
+    """uint8 [tiles_y][tiles_x]: 1 where the scan lines of the tile's candidates (Eq. 2, Eq. 4) add a non-zero count
+    to O (Eq. 5-6), each tile run on its own."""
+    D = _map(D)
+    H, W = D.shape
+    ty, tx = (H + T - 1) // T, (W + T - 1) // T
+    out = np.zeros((ty, tx), np.uint8)
+    for i in range(ty):
+        for j in range(tx):
+            one = np.zeros((ty, tx), np.uint8)
+            one[i, j] = 1
+            O, _ = detect_view_masked(D, alpha_deg, ratio, params, tile_mask(H, W, one, T))
+            out[i, j] = 1 if O.any() else 0
+    return out

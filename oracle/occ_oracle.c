@@ -319,8 +319,10 @@ int32_t ora_scanline_sorted(const float* D, int32_t H, int32_t W, double alpha_d
 
 /*
  * Pixel-wise median of n disparity maps (Section 4.2: the stereo disparities of the peripheral cameras fused into
- * one center map).  maps: n pointers to [H][W].  For even n the median is the mean of the two middle order
- * statistics, fl(a + b) * 0.5 (reading: the paper names a median and gives no rule for an even count).
+ * one center map).  maps: n pointers to [H][W].  Readings: for even n the median is the mean of the two middle
+ * order statistics, fl(a + b) * 0.5 (the paper names a median and gives no rule for an even count); a zero of
+ * either sign enters as +0 (fl(v + 0) maps -0 to +0), so the result does not depend on how equal keys are ordered;
+ * non-finite input is rejected, as for the detection.
  */
 static int cmp_float(const void* pa, const void* pb)
 {
@@ -334,7 +336,7 @@ int ora_median(const float* const* maps, int32_t n, int32_t H, int32_t W, float*
     float v[64];
     for (int64_t i = 0; i < (int64_t)H * W; i++) {
         for (int32_t m = 0; m < n; m++) {
-            v[m] = maps[m][i];
+            v[m] = maps[m][i] + 0.0f;
             if (!isfinite(v[m])) return ORA_ERR_NONFINITE;
         }
         qsort(v, (size_t)n, sizeof(float), cmp_float);

@@ -36,7 +36,10 @@ OCC_MAX_FRAMES = 1024
 
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
             "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning",
-            "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc", "occ_status_string"]
+            "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc", "occ_fuse_median", "occ_warp_views",
+            "occ_detect_batched_tiles", "occ_status_string"]
+
+TILE = 32   # OCC_TILE
 
 
 class occ_view(ctypes.Structure):
@@ -109,6 +112,11 @@ def load(build_if_missing: bool = True):
                                          ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
                                          ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.occ_detect_batched.restype = ctypes.c_int
+        L.occ_detect_batched_tiles.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                               ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
+                                               ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                               ctypes.POINTER(vp), vp]
+        L.occ_detect_batched_tiles.restype = ctypes.c_int
         L.occ_get_status.argtypes = [vp, vp]
         L.occ_get_status.restype = ctypes.c_int
         L.occ_get_stats.argtypes = [vp, ctypes.POINTER(occ_view_stats), i32]
@@ -124,6 +132,11 @@ def load(build_if_missing: bool = True):
         L.occ_detect_noalloc.argtypes = [vp, i32, i32, i64, ctypes.POINTER(occ_view), i32,
                                          ctypes.POINTER(occ_params), vp, vp, vp, vp]
         L.occ_detect_noalloc.restype = ctypes.c_int
+        L.occ_fuse_median.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i64, vp, i64, vp, vp]
+        L.occ_fuse_median.restype = ctypes.c_int
+        L.occ_warp_views.argtypes = [vp, i32, i32, i64, ctypes.POINTER(occ_view), i32, ctypes.POINTER(vp), i64, vp,
+                                     vp, vp]
+        L.occ_warp_views.restype = ctypes.c_int
         L.occ_status_string.argtypes = [ctypes.c_int]
         L.occ_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -244,9 +257,19 @@ def occ_detect(ctx: Context, D, views, params: occ_params | None = None, M=None,
     return M, O
 
 
-def occ_detect_batched(ctx: Context, Ds, views, params: occ_params | None = None, Ms=None, Os=None, stream=None):
+def tiles_of(H: int, W: int):
+    """(tiles_y, tiles_x) of a frame for occ_detect_batched_tiles."""
+    return (H + TILE - 1) // TILE, (W + TILE - 1) // TILE
+
+
+def occ_detect_batched(ctx: Context, Ds, views, params: occ_params | None = None, Ms=None, Os=None, stream=None,
+                       proposals=None, hits=None):
     """Queue the method for a list of float32 CUDA maps [H][W] (contiguous) with the same views, as one batch.
-    Returns (Ms, Os): lists of uint8 / int32 [V][H][W] tensors (allocated when not given)."""
+    Returns (Ms, Os): lists of uint8 / int32 [V][H][W] tensors (allocated when not given).
+
+    proposals: optional list of uint8 CUDA tensors [V][tiles_y][tiles_x] (0 = skip the tile's candidates);
+    hits: optional list of uint8 CUDA tensors of the same shape that receive the per-tile hit flags.  With either,
+    the call goes through occ_detect_batched_tiles."""
     import torch
     nf = len(Ds)
     nv = len(views)
@@ -263,9 +286,21 @@ def occ_detect_batched(ctx: Context, Ds, views, params: occ_params | None = None
     o_arr = (vp * nf)(*[O.data_ptr() for O in Os])
     h_arr = (ctypes.c_int32 * nf)(*[D.shape[0] for D in Ds])
     w_arr = (ctypes.c_int32 * nf)(*[D.shape[1] for D in Ds])
-    rc = load().occ_detect_batched(ctx.handle, nf, d_arr, h_arr, w_arr, _views(views), nv,
-                                   ctypes.byref(params) if params is not None else None, m_arr, o_arr,
-                                   _stream_handle(stream))
+    pv = ctypes.byref(params) if params is not None else None
+    if proposals is None and hits is None:
+        rc = load().occ_detect_batched(ctx.handle, nf, d_arr, h_arr, w_arr, _views(views), nv, pv, m_arr, o_arr,
+                                       _stream_handle(stream))
+    else:
+        def table(ts):
+            if ts is None:
+                return None
+            for D, t in zip(Ds, ts):
+                if t is not None and (t.shape != (nv, *tiles_of(*D.shape)) or t.dtype != torch.uint8
+                                      or not t.is_contiguous()):
+                    raise ValueError("tile tables must be contiguous uint8 [V][tiles_y][tiles_x]")
+            return (vp * nf)(*[None if t is None else t.data_ptr() for t in ts])
+        rc = load().occ_detect_batched_tiles(ctx.handle, nf, d_arr, h_arr, w_arr, _views(views), nv, pv,
+                                             table(proposals), m_arr, o_arr, table(hits), _stream_handle(stream))
     if rc != OCC_OK:
         raise OccError(rc, "occ_detect_batched")
     ctx.last_views = nv
@@ -333,6 +368,53 @@ def occ_detect_noalloc(D, views, params: occ_params | None = None, M=None, O=Non
     return int(load().occ_detect_noalloc(_ptr(D), H, W, D.stride(0), _views(views), len(views),
                                          ctypes.byref(params) if params is not None else None, _ptr(M), _ptr(O),
                                          _ptr(status), _stream_handle(stream)))
+
+
+def occ_fuse_median(maps, D=None, status=None, stream=None):
+    """Pixel-wise median of the disparity maps (list of CUDA float32 [H][W] tensors, same shape and row stride) into
+    D (a new tensor if None), on the maps' device.  status: optional CUDA int32 tensor of one element that receives
+    0 or OCC_ERR_NONFINITE_INPUT in stream order.  Returns D."""
+    import torch
+    if not maps:
+        raise ValueError("no maps")
+    H, W = maps[0].shape
+    for m in maps:
+        if m.shape != (H, W) or m.dtype != torch.float32 or m.stride() != maps[0].stride() or m.stride(1) != 1:
+            raise ValueError("maps must be float32 [H][W] with equal shape and row stride")
+    if D is None:
+        D = torch.empty((H, W), dtype=torch.float32, device=maps[0].device)
+    arr = (ctypes.c_void_p * len(maps))(*[m.data_ptr() for m in maps])
+    rc = load().occ_fuse_median(arr, len(maps), H, W, maps[0].stride(0), _ptr(D), D.stride(0), _ptr(status),
+                                _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_fuse_median")
+    return D
+
+
+def occ_warp_views(D, views, images, M=None, out=None, stream=None):
+    """Backward warp of the peripheral images (list of CUDA float32 [H][W], one per view, equal row stride) to the
+    center view along each view's baseline, bilinear, with M [V][H][W] (uint8, or None) zeroing the occluded
+    pixels.  Returns out [V][H][W] float32."""
+    import torch
+    H, W = D.shape
+    V = len(views)
+    if len(images) != V:
+        raise ValueError("one image per view")
+    for im in images:
+        if im.shape != (H, W) or im.dtype != torch.float32 or im.stride() != images[0].stride() or im.stride(1) != 1:
+            raise ValueError("images must be float32 [H][W] with equal row stride")
+    if M is not None and (M.shape != (V, H, W) or M.dtype != torch.uint8 or not M.is_contiguous()):
+        raise ValueError("M must be a contiguous uint8 [V][H][W] tensor")
+    if out is None:
+        out = torch.empty((V, H, W), dtype=torch.float32, device=D.device)
+    elif out.shape != (V, H, W) or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 [V][H][W] tensor")
+    arr = (ctypes.c_void_p * V)(*[im.data_ptr() for im in images])
+    rc = load().occ_warp_views(_ptr(D), H, W, D.stride(0), _views(views), V, arr, images[0].stride(0), _ptr(M),
+                               _ptr(out), _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_warp_views")
+    return out
 
 
 def occ_set_tuning(ctx: Context, tuning: dict | None = None):

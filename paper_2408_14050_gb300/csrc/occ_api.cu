@@ -116,6 +116,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.status = sc.status;
     a.max_quads = 0;
     a.max_px = 0;
+    a.hits = 0;
 
     // Frame records: lists and flags laid out frame after frame in the pools.
     FrameChunk chunk;
@@ -144,6 +145,11 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         fb_off += F.fb_words * nv;
         F.hdr = sc.hdr + (size_t)f * HDR_WORDS;
         F.stats = sc.stats + (size_t)f * sc.max_views * 2;
+        F.prop = fr[f].prop;
+        F.hits = fr[f].hits;
+        if (F.hits) a.hits = 1;
+        F.tiles_x = (F.W + kTile - 1) / kTile;
+        F.tiles_y = (F.H + kTile - 1) / kTile;
         const int quads = F.H * ((F.W + 3) / 4);
         if (quads > a.max_quads) a.max_quads = quads;
         const int64_t px = (int64_t)nv * F.H * F.W;
@@ -366,9 +372,10 @@ int occ_detect(occ_ctx* ctx, const float* D, int32_t H, int32_t W, int64_t pitch
     return ctx_run(ctx, &fr, 1, a, stream);
 }
 
-int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H, const int32_t* W,
-                       const occ_view* views, int32_t n_views, const occ_params* p, uint8_t* const* M,
-                       int32_t* const* O, void* stream)
+int occ_detect_batched_tiles(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H,
+                             const int32_t* W, const occ_view* views, int32_t n_views, const occ_params* p,
+                             const uint8_t* const* proposal, uint8_t* const* M, int32_t* const* O,
+                             uint8_t* const* tile_hits, void* stream)
 {
     if (!ctx || !D || !H || !W || !M || !O || n_frames < 1 || n_frames > OCC_MAX_FRAMES ||
         n_views > ctx->max_views)
@@ -390,6 +397,8 @@ int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, co
         int64_t cap = (int64_t)((double)H[f] * W[f] * (double)ctx->cand_cap / (double)ctx->max_pixels);
         if (cap < 1) cap = 1;
         fr[f] = FrameIn{D[f], W[f], H[f], W[f], O[f], M[f], nullptr, nullptr, cap};
+        fr[f].prop = proposal ? proposal[f] : nullptr;
+        fr[f].hits = tile_hits ? tile_hits[f] : nullptr;
     }
     if (rc == OCC_OK && pixels > ctx->max_pixels) rc = OCC_ERR_INVALID_ARG;
     if (rc == OCC_OK) {
@@ -398,6 +407,13 @@ int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, co
     }
     std::free(fr);
     return rc;
+}
+
+int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H, const int32_t* W,
+                       const occ_view* views, int32_t n_views, const occ_params* p, uint8_t* const* M,
+                       int32_t* const* O, void* stream)
+{
+    return occ_detect_batched_tiles(ctx, n_frames, D, H, W, views, n_views, p, nullptr, M, O, nullptr, stream);
 }
 
 int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t)

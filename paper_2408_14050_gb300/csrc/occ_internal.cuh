@@ -38,6 +38,7 @@ enum : uint32_t {
 
 // Scan-length classes of the warp scan kernel, sized by the samples of one scan line (2h+1).
 constexpr int kNumClasses = 3;
+constexpr int kTile = OCC_TILE;     // side of the square tiles of proposals and hit flags
 constexpr int kClassCap[kNumClasses] = {256, 1024, 4096};
 // The line-per-thread scan kernel keeps N/2 sorted neighbours in registers; larger N use the warp kernel only.
 constexpr int kLineMaxHalf = 4;
@@ -67,6 +68,9 @@ struct FrameArg {
     int64_t fb_words;
     uint32_t* hdr;                // HDR_WORDS
     unsigned long long* stats;    // [nv][2]: samples, pair tests
+    const uint8_t* prop;          // [nv][tiles_y][tiles_x]: 0 = the tile's candidates are skipped; null = none skipped
+    uint8_t* hits;                // [nv][tiles_y][tiles_x]: 1 = a scan line from the tile found an occlusion; or null
+    int32_t tiles_x, tiles_y;     // ceil(W / kTile), ceil(H / kTile)
 };
 
 // Per (frame, view), written by k_plan.
@@ -84,6 +88,7 @@ struct Args {
     int32_t N;
     int32_t use_fb;               // the line kernel runs first: the warp kernels take only the lines it flagged
     int32_t line_max_runs;        // the line kernel keeps lines of at most this many macro-runs (1 or 2)
+    int32_t hits;                 // some frame asks for per-tile hit flags
     int32_t max_quads;            // max over frames of H * ceil(W / 4)
     int64_t max_px;               // max over frames of n_views * H * W
     ViewArg view[kMaxViews];
@@ -96,8 +101,8 @@ struct Args {
     uint32_t* status;             // OR of every frame's status bits
 };
 
-// At most kFramesPerChunk frame records travel in the parameters of one k_frames launch.
-constexpr int kFramesPerChunk = 32;
+// At most kFramesPerChunk frame records travel in the parameters of one k_frames launch (under 4 KB).
+constexpr int kFramesPerChunk = 24;
 struct FrameChunk {
     FrameArg* dst;
     int32_t first, count;
@@ -152,6 +157,8 @@ struct FrameIn {
     float* E;
     float* A;
     int64_t cap;   // candidate list entries per view
+    const uint8_t* prop = nullptr;   // tile proposal (see FrameArg), or null
+    uint8_t* hits = nullptr;         // tile hit flags (see FrameArg), or null
 };
 
 // Checks the parameters and views and fills the view part of `a` (directions, ratios).  OCC_OK or

@@ -145,6 +145,22 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
             }
         }
 
+        // Tile proposals: candidates of tiles proposed empty are dropped from the lists (the 4 pixels of a quad lie in
+        // one tile).  The top-left quad of each tile clears the tile's hit flags.
+        if (active && (F.prop || F.hits)) {
+            const int tpv = F.tiles_x * F.tiles_y;
+            const int t = (y / kTile) * F.tiles_x + x0 / kTile;
+            if (F.prop) {
+                uint64_t keep = 0;
+                for (int v = 0; v < a.nv; v++)
+                    if (F.prop[(int64_t)v * tpv + t]) keep |= 1ull << v;
+#pragma unroll
+                for (int j = 0; j < 4; j++) bits[j] &= keep;
+            }
+            if (F.hits && (y % kTile) == 0 && (x0 % kTile) == 0)
+                for (int v = 0; v < a.nv; v++) F.hits[(int64_t)v * tpv + t] = 0;
+        }
+
         // Compaction: warp totals per view, then one reservation per block and view.
         for (int v = 0; v < a.nv; v++) {
             uint32_t tot = 0;
@@ -447,6 +463,7 @@ struct LineWindow {
     float w0, w1, w2, w3, v0, v1, v2, v3, b0, b1, b2, b3;
     int p0, p1, p2, p3, o0, o1, o2, o3;
     int wn;
+    int hit;   // a non-zero count went to O
 };
 
 __device__ __forceinline__ void window_init(LineWindow& W)
@@ -457,8 +474,10 @@ __device__ __forceinline__ void window_init(LineWindow& W)
     W.p0 = W.p1 = W.p2 = W.p3 = 0;
     W.o0 = W.o1 = W.o2 = W.o3 = 0;
     W.wn = 0;
+    W.hit = 0;
 }
 
+template <bool kHits>
 __device__ __forceinline__ void window_push(LineWindow& W, const LineSample& e, int half, float zeta, float beta,
                                             int32_t* Ov)
 {
@@ -476,7 +495,10 @@ __device__ __forceinline__ void window_push(LineWindow& W, const LineSample& e, 
     if (W.wn == half) {
         const int ol = half == 1 ? W.o0 : (half == 2 ? W.o1 : (half == 3 ? W.o2 : W.o3));
         const int pl = half == 1 ? W.p0 : (half == 2 ? W.p1 : (half == 3 ? W.p2 : W.p3));
-        if (ol) atomicAdd(Ov + pl, ol);
+        if (ol) {
+            atomicAdd(Ov + pl, ol);
+            if (kHits) W.hit = 1;
+        }
     } else {
         W.wn++;
     }
@@ -486,18 +508,21 @@ __device__ __forceinline__ void window_push(LineWindow& W, const LineSample& e, 
     W.w0 = e.w; W.v0 = e.v; W.b0 = eb; W.p0 = e.p; W.o0 = eo;
 }
 
-__device__ __forceinline__ void window_flush(const LineWindow& W, int32_t* Ov)
+// Returns whether the line added any non-zero count to O.
+__device__ __forceinline__ bool window_flush(const LineWindow& W, int32_t* Ov)
 {
-    if (W.wn > 0 && W.o0) atomicAdd(Ov + W.p0, W.o0);
-    if (W.wn > 1 && W.o1) atomicAdd(Ov + W.p1, W.o1);
-    if (W.wn > 2 && W.o2) atomicAdd(Ov + W.p2, W.o2);
-    if (W.wn > 3 && W.o3) atomicAdd(Ov + W.p3, W.o3);
+    const bool h0 = W.wn > 0 && W.o0, h1 = W.wn > 1 && W.o1, h2 = W.wn > 2 && W.o2, h3 = W.wn > 3 && W.o3;
+    if (h0) atomicAdd(Ov + W.p0, W.o0);
+    if (h1) atomicAdd(Ov + W.p1, W.o1);
+    if (h2) atomicAdd(Ov + W.p2, W.o2);
+    if (h3) atomicAdd(Ov + W.p3, W.o3);
+    return (W.hit != 0) || h0 || h1 || h2 || h3;
 }
 
 // Pass 2 for two macro-runs [k0, ks - 1] and [ks, k1], each read through its own one-slot buffer; the merge emits
 // the smaller head, and the chosen run reads at most one sample per step.
-template <bool kWide>
-__device__ __forceinline__ void line_counts2(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
+template <bool kWide, bool kHits>
+__device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
                                              int cy, int h, int half, int k0, int k1, int ks)
 {
     LineWindow Wn;
@@ -547,9 +572,9 @@ __device__ __forceinline__ void line_counts2(const Args& a, const FrameArg& F, c
         }
         if (ta) { kna = kn; hba = hbuf; bufa = buf; ha = head; has_a = has; }
         else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; }
-        window_push(Wn, e, half, a.zeta, a.beta, Ov);
+        window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov);
     }
-    window_flush(Wn, Ov);
+    return window_flush(Wn, Ov);
 }
 
 // Pass 1 with the next sample's load issued before the current one is used.
@@ -628,8 +653,8 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
 }
 
 // Pass 2 for a single macro-run [k0, k1], loads one sample ahead.
-template <bool kWide>
-__device__ __forceinline__ void line_counts1_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov,
+template <bool kWide, bool kHits>
+__device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov,
                                                int cx, int cy, int h, int half, int k0, int k1)
 {
     LineWindow Wn;
@@ -676,15 +701,15 @@ __device__ __forceinline__ void line_counts1_p(const Args& a, const FrameArg& F,
         const bool sb = before(s, buf);
         const LineSample e = sb ? s : buf;
         if (!sb) buf = s;
-        window_push(Wn, e, half, a.zeta, a.beta, Ov);
+        window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov);
     }
-    window_push(Wn, buf, half, a.zeta, a.beta, Ov);
-    window_flush(Wn, Ov);
+    window_push<kHits>(Wn, buf, half, a.zeta, a.beta, Ov);
+    return window_flush(Wn, Ov);
 }
 
 constexpr int kStatsSmem = 512;   // (frame, view) statistics accumulated in shared memory before going global
 
-template <bool kWide>
+template <bool kWide, bool kHits>
 __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_constant__ Args a)
 {
     constexpr int kWarps = kLineThreads / 32;
@@ -702,15 +727,24 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
     LineJob* q2 = s_q[warp][1];
     int n1 = 0, n2 = 0;   // queue lengths (warp-uniform)
 
+    // kHits: some frame of the batch asks for per-tile hit flags.
+    auto mark_hit = [&](const FrameArg& F, const LineJob& jb) {
+        if (F.hits)
+            F.hits[(int64_t)jb.v * F.tiles_x * F.tiles_y + (jb.y / kTile) * F.tiles_x + jb.x / kTile] = 1;
+    };
     auto run1 = [&](const LineJob& jb) {
         const FrameArg& F = a.frames[jb.f];
-        line_counts1_p<kWide>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
-                              F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half, jb.k0, jb.k1);
+        const bool hit = line_counts1_p<kWide, kHits>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                                                       F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
+                                                       jb.k0, jb.k1);
+        if (kHits && hit) mark_hit(F, jb);
     };
     auto run2 = [&](const LineJob& jb) {
         const FrameArg& F = a.frames[jb.f];
-        line_counts2<kWide>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
-                            F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half, jb.k0, jb.k1, jb.ks);
+        const bool hit = line_counts2<kWide, kHits>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                                                     F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
+                                                     jb.k0, jb.k1, jb.ks);
+        if (kHits && hit) mark_hit(F, jb);
     };
     int cur = -1;   // (frame, view) of the statistics being accumulated
     unsigned long long acc_n = 0, acc_p = 0;
@@ -1051,9 +1085,17 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         __syncwarp();
         // Eq. 6: add every sample's count to the occlusion sum of its pixel.
         int32_t* Ov = F.O + (int64_t)v * F.H * F.W;
+        bool hit = false;
         for (int q = lane; q < n; q += 32) {
             const int o = cnt_own[q] + cnt_up[q];
-            if (o) atomicAdd(Ov + spix[q], o);
+            if (o) {
+                atomicAdd(Ov + spix[q], o);
+                hit = true;
+            }
+        }
+        if (__any_sync(kFull, hit) && lane == 0 && F.hits) {
+            const int cx = (int)(cw & 0xFFFFu), cy = (int)(cw >> 16);
+            F.hits[(int64_t)v * F.tiles_x * F.tiles_y + (cy / kTile) * F.tiles_x + cx / kTile] = 1;
         }
 
         if (lane == 0) {
@@ -1133,7 +1175,7 @@ cudaError_t configure_kernels(int* lines_bps, int scan_bps[kNumClasses + 1])
                                   (int)scan_smem<1024, kWpb1>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<4096, kWpb2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<4096, kWpb2>())) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false>, kLineThreads, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false, false>, kLineThreads, 0)) !=
         cudaSuccess)
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[0], k_scan<256, kWpb0>, kWpb0 * 32,
@@ -1174,8 +1216,13 @@ cudaError_t launch_plan(const Args& a, cudaStream_t st)
 
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st)
 {
-    if (wide) k_scan_lines<true><<<grid, kLineThreads, 0, st>>>(a);
-    else k_scan_lines<false><<<grid, kLineThreads, 0, st>>>(a);
+    if (a.hits) {
+        if (wide) k_scan_lines<true, true><<<grid, kLineThreads, 0, st>>>(a);
+        else k_scan_lines<false, true><<<grid, kLineThreads, 0, st>>>(a);
+    } else {
+        if (wide) k_scan_lines<true, false><<<grid, kLineThreads, 0, st>>>(a);
+        else k_scan_lines<false, false><<<grid, kLineThreads, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

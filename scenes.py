@@ -225,3 +225,69 @@ def stress_5x5(frame: int = 0, H: int = 2160, W: int = 4096) -> Workload:
     """4096x2160 map with salt outliers, 24 views on the rings of a 5x5 array."""
     return Workload(f"array5x5_{W}x{H}_24views", [make_scene(spec_stress(H, W), seed_of(4, frame))],
                     views_5x5_ring())
+
+
+def stereo_maps(D: np.ndarray, n: int, seed: int, sigma: float = 0.25, salt: float = 0.01,
+                d_max: float = 64.0) -> list:
+    """n per-camera estimates of the center map D, as the stereo matches of n peripheral cameras would give them
+    before fusion: D plus independent Gaussian noise (sigma px) and, with probability `salt` per pixel, a wrong match
+    drawn from U[0, d_max]."""
+    H, W = D.shape
+    out = []
+    for k in range(n):
+        e = D.astype(np.float64) + sigma * CounterRng(seed, key=16 + 2 * k).normal(H * W).reshape(H, W)
+        if salt > 0:
+            r = CounterRng(seed, key=17 + 2 * k).uniform(2 * H * W).reshape(H, W, 2)
+            e = np.where(r[..., 0] < salt, r[..., 1] * d_max, e)
+        out.append(np.ascontiguousarray(e.astype(np.float32)))
+    return out
+
+
+def peripheral_images(H: int, W: int, n: int, seed: int) -> list:
+    """n smooth-plus-texture float32 images standing in for the peripheral cameras' spectral images (values in
+    [0, 1]): a low-frequency pattern plus uniform texture."""
+    ys = np.arange(H, dtype=np.float64)[:, None]
+    xs = np.arange(W, dtype=np.float64)[None, :]
+    out = []
+    for k in range(n):
+        rng = CounterRng(seed, key=64 + k)
+        fx, fy, ph = rng.scalar(0.005, 0.05), rng.scalar(0.005, 0.05), rng.scalar(0.0, 6.28)
+        base = 0.5 + 0.3 * np.sin(fx * xs + ph) * np.cos(fy * ys)
+        tex = 0.2 * rng.uniform(H * W).reshape(H, W)
+        out.append(np.ascontiguousarray((base + tex).astype(np.float32)))
+    return out
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Initial parameters of the learned tile proposer (seeded; the network's own arithmetic lives elsewhere).
+# Layout of the flat float32 parameter vector: for each 3x3 convolution (c_in -> c_out) the weights
+# [c_out][9][c_in] (tap = (dy + 1) * 3 + (dx + 1)) then the bias [c_out]; then the view encoding's weights [16][3]
+# and bias [16], then the output bias [1].
+
+NET_LAYERS = [(8, 16), (16, 32), (32, 32), (32, 16)]
+NET_FEATURES = 16
+NET_ENC = 3
+
+
+def net_param_count() -> int:
+    n = sum(co * 9 * ci + co for ci, co in NET_LAYERS)
+    return n + NET_FEATURES * NET_ENC + NET_FEATURES + 1
+
+
+def net_init(seed: int) -> np.ndarray:
+    """He-normal convolution weights (fan-in = 9 x the input channels that carry data: 1 for the first layer, whose
+    input has the disparity in channel 0 and zeros elsewhere), zero biases, N(0, 0.5) view-encoding weights."""
+    rng = CounterRng(seed, key=200)
+    out = []
+    off = 0
+    for li, (ci, co) in enumerate(NET_LAYERS):
+        fan = 9 * (1 if li == 0 else ci)
+        w = rng.normal(co * 9 * ci, offset=off) * np.sqrt(2.0 / fan)
+        off += co * 9 * ci
+        if li == 0:
+            w = w.reshape(co, 9, ci)
+            w[:, :, 1:] = 0.0
+            w = w.reshape(-1)
+        out += [w, np.zeros(co)]
+    out += [rng.normal(NET_FEATURES * NET_ENC, offset=off) * 0.5, np.zeros(NET_FEATURES), np.zeros(1)]
+    return np.concatenate(out).astype(np.float32)

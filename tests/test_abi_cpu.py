@@ -82,4 +82,25 @@ def test_invalid_arguments_rejected_before_any_device_work():
     assert lib.occ_detect(None, None, 4, 4, 0, v, 1, None, None, None, None, None, None) == occ.OCC_ERR_INVALID_ARG
     assert lib.occ_get_status(None, None) == occ.OCC_ERR_INVALID_ARG
     assert lib.occ_get_stats(None, None, 1) == occ.OCC_ERR_INVALID_ARG
+    # Median fusion and backward warp: argument checks come before any CUDA call (fake, never dereferenced,
+    # 4-byte-aligned addresses).
+    fake = ctypes.c_void_p(0x1000)
+    maps = (ctypes.c_void_p * 2)(0x1000, 0x2000)
+    assert lib.occ_fuse_median(None, 2, 4, 4, 0, fake, 0, None, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_fuse_median(maps, 0, 4, 4, 0, fake, 0, None, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_fuse_median(maps, 65, 4, 4, 0, fake, 0, None, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_fuse_median(maps, 2, 4, 4, 3, fake, 0, None, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_fuse_median(maps, 2, 4, 4, 0, ctypes.c_void_p(0x1002), 0, None, None) == occ.OCC_ERR_INVALID_ARG
+    bad_maps = (ctypes.c_void_p * 2)(0x1000, None)
+    assert lib.occ_fuse_median(bad_maps, 2, 4, 4, 0, fake, 0, None, None) == occ.OCC_ERR_INVALID_ARG
+    imgs = (ctypes.c_void_p * 1)(0x3000)
+    v[0].alpha_deg, v[0].ratio = 0.0, 1.0
+    assert lib.occ_warp_views(None, 4, 4, 0, v, 1, imgs, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_warp_views(fake, 4, 4, 0, v, 0, imgs, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_warp_views(fake, 4, 4, 0, v, 1, None, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
+    assert lib.occ_warp_views(fake, 0, 4, 0, v, 1, imgs, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
+    v[0].ratio = 0.0
+    assert lib.occ_warp_views(fake, 4, 4, 0, v, 1, imgs, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
+    v[0].ratio = float("nan")
+    assert lib.occ_warp_views(fake, 4, 4, 0, v, 1, imgs, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
     lib.occ_destroy(None)

@@ -452,3 +452,39 @@ def test_warp_half_pixel_is_the_mean_and_mask_zeroes():
     M[2, 3] = 1
     out = oracle.warp_view(D, 180.0, 1.0, img, M)
     assert out[2, 3] == 0 and out[2, 2] == exp[2, 2]
+
+
+def test_median_signed_zero_and_nonfinite():
+    a = np.full((2, 3), -0.0, np.float32)
+    b = np.full((2, 3), 0.0, np.float32)
+    for maps in ([a, b, a], [a, a], [b, a]):
+        got = oracle.median(maps)
+        assert not np.signbit(got).any()
+    c = b.copy()
+    c[1, 2] = np.inf
+    with pytest.raises(ValueError):
+        oracle.median([b, c, b])
+
+
+def test_tile_helpers_partition_the_work():
+    """The proposal helpers: all tiles proposed is the plain method; the tiles' separate runs add up to it (Eq. 6 is
+    a sum over scan lines); labels are 1 exactly on the tiles whose own run finds an occlusion."""
+    D = small_scene(70, 100, frame=11)
+    a, r = 0.0, 1.0
+    O, M, _ = oracle.detect_view(D, a, r)
+    ty, tx = 3, 4
+    O_all, M_all = oracle.detect_view_proposed(D, a, r, None, np.ones((ty, tx), np.uint8))
+    np.testing.assert_array_equal(O_all, O)
+    total = np.zeros_like(O)
+    labels = oracle.tile_labels(D, a, r)
+    for i in range(ty):
+        for j in range(tx):
+            one = np.zeros((ty, tx), np.uint8)
+            one[i, j] = 1
+            Ot, _ = oracle.detect_view_proposed(D, a, r, None, one)
+            total += Ot
+            assert labels[i, j] == (1 if Ot.any() else 0)
+    np.testing.assert_array_equal(total, O)
+    assert oracle.tile_mask(70, 100, np.ones((3, 4))).shape == (70, 100)
+    O_none, M_none = oracle.detect_view_proposed(D, a, r, None, np.zeros((ty, tx), np.uint8))
+    assert not O_none.any() and not M_none.any()
