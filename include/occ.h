@@ -284,6 +284,84 @@ int occ_detect_batched_tiles(occ_ctx* ctx, int32_t n_frames, const float* const*
                              const uint8_t* const* proposal, uint8_t* const* M, int32_t* const* O,
                              uint8_t* const* tile_hits, void* stream);
 
+/*
+ * Learned tile proposer.  A small convolutional network scores, for every OCC_TILE x OCC_TILE tile of a center map D
+ * and every view, whether the scan lines of the tile's candidates find an occlusion, so that occ_detect_batched_tiles
+ * can skip the tiles it rules out (a concrete form of the paper's closing remark, Section 5, that thinning the
+ * candidate list would cut the runtime further).  It is trained on the tile_hits labels of the plain method.
+ *
+ * Network (all tensors NHWC; bf16 = bfloat16 rounded to nearest even):
+ *   x0       = bf16(fl(D / 32) - 1) in channel 0 of 8, channels 1..7 zero
+ *   a_l      = bf16(relu(conv3x3(a_{l-1}, bf16(W_l)) + b_l)), l = 1..4, channels 8 -> 16 -> 16 -> 32 -> 16, zero
+ *              padding ('same'), bf16 products summed in fp32 on the tensor cores
+ *   g(v)     = We (cos alpha, sin alpha, r) + be                 (16 values; cos, sin as occ_direction gives them)
+ *   z_v(p)   = sum_c a_4(p)[c] g_c(v) + b0
+ *   s_v(t)   = log(mean over the tile's pixels of exp(z_v))       (the tile logit; partial tiles use their pixels)
+ *   loss     = mean over frames, views and tiles of -(w y log sigmoid(s) + (1 - y) log(1 - sigmoid(s)))
+ * Back-propagated gradients of the pre-activations are gated by a_l > 0 and stored as bf16, like the activations.
+ *
+ * Parameters: one fp32 vector of OCC_NET_PARAMS values: per layer W_l [c_out][9][c_in] (tap = (dy+1)*3 + (dx+1))
+ * then b_l [c_out]; then We [16][3], be [16], b0.
+ *
+ * Frames: n maps of one size H x W, contiguous ([n][H][W] binary32 device memory).  Per-tile tables (logits,
+ * labels, proposals) are [n][n_views][tiles_y][tiles_x] with tiles_y = ceil(H / OCC_TILE), tiles_x = ceil(W /
+ * OCC_TILE).  All calls run asynchronously on `stream` (NULL: the legacy default stream) on the network's device,
+ * except occ_net_set_params / occ_net_get_params, which wait.  Returns as for the detection: OCC_OK once queued,
+ * OCC_ERR_INVALID_ARG, OCC_ERR_CAPACITY (n * H * W above the network's max_pixels), OCC_ERR_CUDA.
+ */
+#define OCC_NET_PARAMS 12817
+
+typedef struct occ_net occ_net;
+
+/* Network state on `device`: parameters, Adam moments, bf16 operand copies, activations for up to max_pixels pixels
+ * (n * H * W) per call, up to max_views views.  Parameters start at zero: set them before use. */
+int occ_net_create(occ_net** out, int device, int64_t max_pixels, int32_t max_views);
+void occ_net_destroy(occ_net* net);
+
+/* Copy the fp32 parameter vector in from / out to host memory (count must be OCC_NET_PARAMS).  Setting them also
+ * clears the Adam moments.  Both wait for completion. */
+int occ_net_set_params(occ_net* net, const float* params, int64_t count);
+int occ_net_get_params(occ_net* net, float* params, int64_t count);
+
+/* Tile logits s [n][n_views][tiles_y][tiles_x] (device fp32) of the maps D. */
+int occ_net_forward(occ_net* net, const float* D, int32_t n, int32_t H, int32_t W, const occ_view* views,
+                    int32_t n_views, float* logits, void* stream);
+
+/* Forward and backward pass on labelled maps: labels [n][n_views][tiles_y][tiles_x] (device uint8, non-zero = the
+ * tile's candidates find an occlusion), positive weight w > 0.  Writes the loss (device fp32 [1]), the gradient of the
+ * loss with respect to the parameter vector (device fp32 [OCC_NET_PARAMS], overwritten) and, if logits is not NULL,
+ * the tile logits. */
+int occ_net_loss_grad(occ_net* net, const float* D, int32_t n, int32_t H, int32_t W, const occ_view* views,
+                      int32_t n_views, const uint8_t* labels, float pos_weight, float* grads, float* loss,
+                      float* logits, void* stream);
+
+/* One Adam step (step = 1, 2, ... for the bias corrections) on the fp32 parameters with the device gradient `grads`,
+ * then the bf16 operand copies are refreshed. */
+int occ_net_adam(occ_net* net, const float* grads, float lr, float beta1, float beta2, float eps, int32_t step,
+                 void* stream);
+
+/* proposal[i] = logits[i] > threshold (device arrays of `count` entries): the proposal table of
+ * occ_detect_batched_tiles. */
+int occ_net_propose(const float* logits, int64_t count, float threshold, uint8_t* proposal, void* stream);
+
+/* OCC_ERR_TIMEOUT if a bounded wait of a network kernel on the tensor cores expired (on the current device) since
+ * the library was loaded, else OCC_OK.  Waits for `stream`. */
+int occ_net_status(void* stream);
+
+/* One 3x3 'same' convolution layer of the network on the tensor cores, for tests and custom pipelines.  X: device
+ * bf16 [n][H][W][c_in]; Wb: device bf16 [c_out][K] with K = 9 * c_in rounded up to a multiple of 16, k = tap * c_in
+ * + ci, zero beyond 9 * c_in; bias: device fp32 [c_out] or NULL; gate: device bf16 [n][H][W][c_out] or NULL (an output
+ * whose gate value is not > 0 becomes 0); relu != 0 clamps at 0 after the bias; Y: device bf16 [n][H][W][c_out].
+ * (c_in, c_out) is one of (8, 16), (16, 16), (16, 32), (32, 16).  X, Wb, gate, Y 16-byte aligned. */
+int occ_net_conv3x3(const void* X, int32_t n, int32_t H, int32_t W, int32_t c_in, const void* Wb, const float* bias,
+                    int32_t c_out, const void* gate, int32_t relu, void* Y, void* stream);
+
+/* Weight gradient of that layer on the tensor cores: dWt[tap * c_in + ci][co] += sum over pixels p of
+ * X[p + tap][ci] dY[p][co] (zero padding), and dWt[9 * c_in][co] += sum_p dY[p][co] (the bias gradient).  X, dY as
+ * above (16-byte aligned); dWt: device fp32 [9 * c_in + 1][c_out], accumulated. */
+int occ_net_conv3x3_wgrad(const void* X, const void* dY, int32_t n, int32_t H, int32_t W, int32_t c_in,
+                          int32_t c_out, float* dWt, void* stream);
+
 /* A static, human-readable name of a status code. */
 const char* occ_status_string(int status);
 

@@ -7,7 +7,7 @@ occlusion (Eq. 5-6), so that the tiles it rules out need not be scanned.  It is 
 method.  This file computes its forward pass, loss and gradients the slow, obvious way:
 
   input      x0[y][x] = bf16(fl(D * 1/32) - 1) in channel 0 of 8 (channels 1..7 are zero)
-  4 layers   a_l = bf16(relu(conv3x3_same(a_{l-1}, bf16(W_l)) + b_l)), channels 8 -> 16 -> 32 -> 32 -> 16,
+  4 layers   a_l = bf16(relu(conv3x3_same(a_{l-1}, bf16(W_l)) + b_l)), channels 8 -> 16 -> 16 -> 32 -> 16,
              zero padding, products of bf16 values summed in binary32
   view code  g(v) = We (cos alpha, sin alpha, r) + be        (16 values; cos and sin as the detection rounds them)
   pixel      z_v[y][x] = sum_c a_4[y][x][c] g_c(v) + b0
@@ -25,7 +25,7 @@ from __future__ import annotations
 
 import numpy as np
 
-LAYERS = [(8, 16), (16, 32), (32, 32), (32, 16)]
+LAYERS = [(8, 16), (16, 16), (16, 32), (32, 16)]
 FEATURES = 16
 ENC = 3
 TILE = 32

@@ -37,7 +37,11 @@ OCC_MAX_FRAMES = 1024
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
             "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning",
             "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc", "occ_fuse_median", "occ_warp_views",
-            "occ_detect_batched_tiles", "occ_status_string"]
+            "occ_detect_batched_tiles", "occ_net_create", "occ_net_destroy", "occ_net_set_params",
+            "occ_net_get_params", "occ_net_forward", "occ_net_loss_grad", "occ_net_adam", "occ_net_propose",
+            "occ_net_status", "occ_net_conv3x3", "occ_net_conv3x3_wgrad", "occ_status_string"]
+
+NET_PARAMS = 12817   # OCC_NET_PARAMS
 
 TILE = 32   # OCC_TILE
 
@@ -137,6 +141,30 @@ def load(build_if_missing: bool = True):
         L.occ_warp_views.argtypes = [vp, i32, i32, i64, ctypes.POINTER(occ_view), i32, ctypes.POINTER(vp), i64, vp,
                                      vp, vp]
         L.occ_warp_views.restype = ctypes.c_int
+        L.occ_net_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64, i32]
+        L.occ_net_create.restype = ctypes.c_int
+        L.occ_net_destroy.argtypes = [vp]
+        L.occ_net_destroy.restype = None
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.occ_net_set_params.argtypes = [vp, fp, i64]
+        L.occ_net_set_params.restype = ctypes.c_int
+        L.occ_net_get_params.argtypes = [vp, fp, i64]
+        L.occ_net_get_params.restype = ctypes.c_int
+        L.occ_net_forward.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(occ_view), i32, vp, vp]
+        L.occ_net_forward.restype = ctypes.c_int
+        L.occ_net_loss_grad.argtypes = [vp, vp, i32, i32, i32, ctypes.POINTER(occ_view), i32, vp, ctypes.c_float, vp,
+                                        vp, vp, vp]
+        L.occ_net_loss_grad.restype = ctypes.c_int
+        L.occ_net_adam.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, vp]
+        L.occ_net_adam.restype = ctypes.c_int
+        L.occ_net_propose.argtypes = [vp, i64, ctypes.c_float, vp, vp]
+        L.occ_net_propose.restype = ctypes.c_int
+        L.occ_net_status.argtypes = [vp]
+        L.occ_net_status.restype = ctypes.c_int
+        L.occ_net_conv3x3.argtypes = [vp, i32, i32, i32, i32, vp, vp, i32, vp, i32, vp, vp]
+        L.occ_net_conv3x3.restype = ctypes.c_int
+        L.occ_net_conv3x3_wgrad.argtypes = [vp, vp, i32, i32, i32, i32, i32, vp, vp]
+        L.occ_net_conv3x3_wgrad.restype = ctypes.c_int
         L.occ_status_string.argtypes = [ctypes.c_int]
         L.occ_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -436,3 +464,138 @@ def occ_get_tuning(ctx: Context):
     if rc != OCC_OK:
         raise OccError(rc, "occ_get_tuning")
     return t.as_dict(), int(m.value)
+
+
+
+# ---------------------------------------------------------------------------------------------------------------
+# Learned tile proposer
+
+class Net:
+    """The learned tile proposer's network (occ_net): fp32 master parameters, Adam state and activation scratch for up
+    to max_pixels pixels (n x H x W) per call, on one device."""
+
+    def __init__(self, device: int = 0, max_pixels: int = 1 << 22, max_views: int = 8):
+        h = ctypes.c_void_p()
+        rc = load().occ_net_create(ctypes.byref(h), device, max_pixels, max_views)
+        if rc != OCC_OK:
+            raise OccError(rc, "occ_net_create")
+        self.handle = h
+        self.device = device
+        self.max_pixels = max_pixels
+
+    def close(self):
+        if self.handle:
+            load().occ_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != NET_PARAMS:
+            raise ValueError("parameter count")
+        rc = load().occ_net_set_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size)
+        if rc != OCC_OK:
+            raise OccError(rc, "occ_net_set_params")
+
+    def get_params(self):
+        import numpy as np
+        p = np.empty(NET_PARAMS, dtype=np.float32)
+        rc = load().occ_net_get_params(self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), p.size)
+        if rc != OCC_OK:
+            raise OccError(rc, "occ_net_get_params")
+        return p
+
+    @staticmethod
+    def _frames(D):
+        import torch
+        if D.dim() == 2:
+            D = D.unsqueeze(0)
+        if D.dtype != torch.float32 or not D.is_cuda or not D.is_contiguous():
+            raise ValueError("maps must be a contiguous float32 CUDA tensor [n][H][W]")
+        return D
+
+    def forward(self, D, views, logits=None, stream=None):
+        """Tile logits [n][V][tiles_y][tiles_x] of the maps D ([n][H][W] or [H][W])."""
+        import torch
+        D = self._frames(D)
+        n, H, W = D.shape
+        ty, tx = tiles_of(H, W)
+        if logits is None:
+            logits = torch.empty((n, len(views), ty, tx), dtype=torch.float32, device=D.device)
+        rc = load().occ_net_forward(self.handle, _ptr(D), n, H, W, _views(views), len(views), _ptr(logits),
+                                    _stream_handle(stream))
+        if rc != OCC_OK:
+            raise OccError(rc, "occ_net_forward")
+        return logits
+
+    def loss_grad(self, D, views, labels, pos_weight: float = 1.0, grads=None, loss=None, logits=None, stream=None):
+        """(loss [1], grads [NET_PARAMS]) device tensors for labelled maps."""
+        import torch
+        D = self._frames(D)
+        n, H, W = D.shape
+        if labels.dtype != torch.uint8 or not labels.is_contiguous() or \
+                labels.shape != (n, len(views), *tiles_of(H, W)):
+            raise ValueError("labels must be contiguous uint8 [n][V][tiles_y][tiles_x]")
+        if grads is None:
+            grads = torch.empty(NET_PARAMS, dtype=torch.float32, device=D.device)
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=D.device)
+        rc = load().occ_net_loss_grad(self.handle, _ptr(D), n, H, W, _views(views), len(views), _ptr(labels),
+                                      float(pos_weight), _ptr(grads), _ptr(loss), _ptr(logits), _stream_handle(stream))
+        if rc != OCC_OK:
+            raise OccError(rc, "occ_net_loss_grad")
+        return loss, grads
+
+    def adam(self, grads, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             stream=None):
+        rc = load().occ_net_adam(self.handle, _ptr(grads), lr, beta1, beta2, eps, step, _stream_handle(stream))
+        if rc != OCC_OK:
+            raise OccError(rc, "occ_net_adam")
+
+
+def occ_net_propose(logits, threshold: float, proposal=None, stream=None):
+    """uint8 proposal table: logits > threshold."""
+    import torch
+    if proposal is None:
+        proposal = torch.empty(logits.shape, dtype=torch.uint8, device=logits.device)
+    rc = load().occ_net_propose(_ptr(logits), logits.numel(), float(threshold), _ptr(proposal), _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_net_propose")
+    return proposal
+
+
+def occ_net_status(stream=None) -> int:
+    return int(load().occ_net_status(_stream_handle(stream)))
+
+
+def occ_net_conv3x3(X, Wb, bias=None, gate=None, relu: bool = False, Y=None, stream=None):
+    """One network convolution layer on bf16 NHWC tensors X [n][H][W][c_in], Wb [c_out][K] (see include/occ.h)."""
+    import torch
+    n, H, W, ci = X.shape
+    co = Wb.shape[0]
+    if Y is None:
+        Y = torch.empty((n, H, W, co), dtype=torch.bfloat16, device=X.device)
+    rc = load().occ_net_conv3x3(_ptr(X), n, H, W, ci, _ptr(Wb), _ptr(bias), co, _ptr(gate), 1 if relu else 0, _ptr(Y),
+                                _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_net_conv3x3")
+    return Y
+
+
+def occ_net_conv3x3_wgrad(X, dY, dWt=None, stream=None):
+    """dWt [9 c_in + 1][c_out] (fp32, accumulated) of a network convolution layer."""
+    import torch
+    n, H, W, ci = X.shape
+    co = dY.shape[-1]
+    if dWt is None:
+        dWt = torch.zeros((9 * ci + 1, co), dtype=torch.float32, device=X.device)
+    rc = load().occ_net_conv3x3_wgrad(_ptr(X), _ptr(dY), n, H, W, ci, co, _ptr(dWt), _stream_handle(stream))
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_net_conv3x3_wgrad")
+    return dWt

@@ -264,7 +264,7 @@ def peripheral_images(H: int, W: int, n: int, seed: int) -> list:
 # [c_out][9][c_in] (tap = (dy + 1) * 3 + (dx + 1)) then the bias [c_out]; then the view encoding's weights [16][3]
 # and bias [16], then the output bias [1].
 
-NET_LAYERS = [(8, 16), (16, 32), (32, 32), (32, 16)]
+NET_LAYERS = [(8, 16), (16, 16), (16, 32), (32, 16)]
 NET_FEATURES = 16
 NET_ENC = 3
 
@@ -291,3 +291,28 @@ def net_init(seed: int) -> np.ndarray:
         out += [w, np.zeros(co)]
     out += [rng.normal(NET_FEATURES * NET_ENC, offset=off) * 0.5, np.zeros(NET_FEATURES), np.zeros(1)]
     return np.concatenate(out).astype(np.float32)
+
+
+def proposer_spec(frame: int, H: int, W: int, seed: int) -> SceneSpec:
+    """Scene statistics of one training frame of the learned tile proposer: the 3x3-array recipe with the noise
+    level drawn from [0, 0.3] px and 4 to 20 objects, so that both noisy and clean maps are seen."""
+    rng = CounterRng(seed_of(seed, frame), key=300)
+    return SceneSpec(H=H, W=W, bg_base=(0.0, 8.0), bg_slope=(2.0, 8.0), n_objects=int(rng.scalar(4, 21)),
+                     obj_disp=(8.0, 64.0), obj_size=(0.05, 0.35), d_max=64.0, sigma=rng.scalar(0.0, 0.3))
+
+
+def proposer_frame(frame: int, H: int, W: int, seed: int) -> np.ndarray:
+    return make_scene(proposer_spec(frame, H, W, seed), seed_of(seed + 1, frame))
+
+
+def proposer_frames(n: int, H: int, W: int, seed: int, first: int = 0, workers: int = 0) -> np.ndarray:
+    """Frames first .. first + n - 1 of the proposer's training stream as one float32 array [n][H][W].  workers > 1
+    draws them in a pool of spawned processes (safe after CUDA has been initialised)."""
+    idx = list(range(first, first + n))
+    if workers > 1 and n > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            out = pool.starmap(proposer_frame, [(i, H, W, seed) for i in idx], chunksize=max(1, n // (4 * workers)))
+    else:
+        out = [proposer_frame(i, H, W, seed) for i in idx]
+    return np.stack(out)

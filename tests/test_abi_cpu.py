@@ -18,7 +18,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "occ.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(occ_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(occ_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_binding_names():
@@ -31,7 +31,7 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
     nm = subprocess.run(["nm", "-D", "--defined-only", occ.library_path()], capture_output=True, text=True)
     if nm.returncode == 0:
-        exported = set(re.findall(r"\bT (occ_[a-z_]+)$", nm.stdout, flags=re.M))
+        exported = set(re.findall(r"\bT (occ_[a-z0-9_]+)$", nm.stdout, flags=re.M))
         assert set(declared_functions()) <= exported
 
 
