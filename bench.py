@@ -52,6 +52,10 @@ def parse():
                     help="frames of the mixed-size batch measured through a CUDA graph (0: skip)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="skip the median-fusion / backward-warp measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip training and measuring the learned tile proposer")
+    ap.add_argument("--learned-train-frames", type=int, default=20000)
+    ap.add_argument("--learned-eval-frames", type=int, default=16,
+                    help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")
     return ap.parse_args()
 
 
@@ -67,6 +71,15 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def bf16_peak():
+    """Dense bf16 tensor-core peak in TFLOP/s: the measured burst figure, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
 
 
 # ---------------------------------------------------------------------------------------------------------------
@@ -284,6 +297,7 @@ def run_ours(args):
     if args.batched_frames > 0:
         batched = run_batched(args, dev, views, rank, world)
     fusion = None if args.no_fusion else run_fusion(args, dev, frames[0], views)
+    learned_res = None if args.no_learned else run_learned(args, dev, views)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -308,6 +322,7 @@ def run_ours(args):
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
             "batched": batched,
             "fusion_and_warp": fusion,
+            "learned": learned_res,
             "work": {"samples_per_step": samples, "pair_tests_per_step": pairs,
                      "samples_per_s": round(samples / (ms_per_step / 1e3)),
                      "candidates_per_step": round(sum(s["candidates"] for s in stats)),
@@ -410,6 +425,72 @@ def run_fusion(args, dev, frame, views):
     ctx.close()
     res["config"] = f"{W}x{H}, {V} stereo maps -> D; {V} views warped with their masks; L2 flushed before each launch"
     return res
+
+
+# Network FLOPs per pixel of one forward pass (3x3 convolutions 8(1 carrying data) -> 16 -> 16 -> 32 -> 16, counted
+# with the channels that carry data: 2 * 9 * c_in * c_out per layer) and of the head (16 multiply-adds per view).
+NET_FWD_FLOP_PER_PX = 2 * 9 * (1 * 16 + 16 * 16 + 16 * 32 + 32 * 16)
+
+
+def run_learned(args, dev, views):
+    """The learned tile proposer (trained here on the GPU with the library's own kernels on labels of the plain
+    method) against the plain method on the mixed-size batch: pixel recall and precision of the masks, tiles skipped,
+    device times and the net's tensor-core throughput."""
+    import torch
+
+    import paper_2408_14050_gb300 as occ
+    from paper_2408_14050_gb300 import learned
+
+    H, W = 192, 256
+    workers = max(1, min(16, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    Dtr = torch.from_numpy(scenes.proposer_frames(args.learned_train_frames, H, W, seed=500,
+                                                  workers=workers)).to(dev)
+    Dcal = torch.from_numpy(scenes.proposer_frames(256, H, W, seed=500, first=10 ** 7, workers=workers)).to(dev)
+    t_gen = time.perf_counter() - t0
+    lctx = occ.occ_create(dev.index, max_pixels=64 * H * W, max_views=len(views))
+    Ltr = learned.labels_for(lctx, Dtr, views)
+    net = occ.Net(dev.index, max_pixels=max(32 * H * W, 4096 * 2160), max_views=len(views))
+    net.set_params(scenes.net_init(1))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = learned.train(net, Dtr, Ltr, views, epochs=1, batch=32, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    th, rec_cal, sk_cal = learned.calibrate(net, lctx, [Dcal[i] for i in range(Dcal.shape[0])], views)
+    lctx.close()
+    del Dtr, Ltr
+
+    wl = scenes.mixed_batch(n_frames=args.learned_eval_frames)
+    frames = [torch.from_numpy(f).to(dev) for f in wl.frames]
+    px = sum(int(f.numel()) for f in frames)
+    ctx = occ.occ_create(dev.index, max_pixels=px, max_views=len(views))
+    ev = learned.evaluate(net, ctx, frames, views, th)
+    ctx.close()
+    if occ.occ_net_status() != occ.OCC_OK:
+        raise RuntimeError("a tensor-core wait of the network expired")
+    net.close()
+    tflops = NET_FWD_FLOP_PER_PX * px / (ev["ms_net"] / 1e3) / 1e12
+    peak, src = bf16_peak()
+    return {
+        "value": round(px * len(views) / (ev["ms_learned"] / 1e3) / 1e6, 1), "unit": UNIT,
+        "plain_value": round(px * len(views) / (ev["ms_plain"] / 1e3) / 1e6, 1),
+        "speedup_vs_plain": round(ev["speedup"], 4),
+        "pixel_recall": round(ev["recall"], 6), "pixel_precision": round(ev["precision"], 6),
+        "skipped_tiles": round(ev["skipped_tiles"], 4), "tiles": ev["tiles"],
+        "ms_plain": round(ev["ms_plain"], 3), "ms_learned": round(ev["ms_learned"], 3), "ms_net": round(ev["ms_net"], 3),
+        "threshold": round(th, 5), "calibration": {"frames": 256, "pixel_recall": round(rec_cal, 6),
+                                                   "skipped_tiles": round(sk_cal, 4), "target": 0.999},
+        "training": {"frames": args.learned_train_frames, "frame": f"{W}x{H}", "epochs": 1, "batch": 32,
+                     "steps": len(losses), "loss_first": round(losses[0], 4), "loss_last": round(losses[-1], 4),
+                     "seconds": round(t_train, 2), "generation_seconds": round(t_gen, 1),
+                     "mpx_per_s": round(args.learned_train_frames * H * W / t_train / 1e6, 1)},
+        "roofline": {"bound": "tensor", "kernel": "k_conv_tma / k_conv (network forward, all layers)",
+                     "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tflops / peak, 4),
+                     "flop_per_px": NET_FWD_FLOP_PER_PX, "peak_source": src},
+        "eval": f"{len(frames)} mixed frames ({', '.join(sorted({f'{f.shape[1]}x{f.shape[0]}' for f in frames}))}),"
+                " 8 views; masks of the proposed run are a subset of the plain masks by construction",
+    }
 
 
 # ---------------------------------------------------------------------------------------------------------------

@@ -6,13 +6,18 @@
 //
 // Kernels:
 //   k_prep     D -> x0 (NHWC bf16, 8 channels: fl(D / 32) - 1 in channel 0)
-//   k_conv     3x3 'same' convolution as an implicit GEMM on the 5th-generation tensor cores: 128 output pixels per
-//              CTA (M = 128), all output channels (N = 16 or 32), K = 9 x c_in (padded to a multiple of 16).  The
-//              CTA gathers its im2col rows into shared memory in the canonical K-major layout, one thread issues
-//              tcgen05.mma (kind::f16, bf16 x bf16 -> fp32) with the accumulator in tensor memory, and the epilogue
-//              reads it back with tcgen05.ld and applies bias, ReLU or a ReLU gate before rounding to bf16.  The
-//              forward layers and the input-gradient (dgrad) pass both use it: dgrad is the same convolution of the
-//              output gradient with the taps mirrored and the channel roles swapped.
+//   k_conv_tma 3x3 'same' convolution as an implicit GEMM on the 5th-generation tensor cores, for c_in >= 16: a CTA
+//              computes a 16 x 8 block of output pixels (M = 128) for all output channels (N = 16 or 32).  TMA
+//              (cp.async.bulk.tensor) brings the 18 x 10 pixel halo of the block into shared memory, one copy per
+//              8 channels, laid out so that the 8 pixels of an output row form one canonical K-major core matrix:
+//              every tap is then the same halo read at a shifted start address (SBO = one halo row), and one thread
+//              issues 9 x c_in / 16 tcgen05.mma (kind::f16, bf16 x bf16 -> fp32, accumulator in tensor memory)
+//              without any im2col copy.  The epilogue reads the accumulator with tcgen05.ld and applies bias, ReLU
+//              or a ReLU gate before rounding to bf16.  The forward layers and the input-gradient (dgrad) pass both
+//              use it: dgrad is the same convolution of the output gradient with the taps mirrored and the channel
+//              roles swapped.
+//   k_conv     the same convolution for the 8-channel input layer, gathering im2col rows into shared memory (a tap
+//              is a single 8-channel chunk there, so taps cannot be addressed as shifted halo reads).
 //   k_wgrad    weight gradient dW[co][tap][ci] = sum_p dY[p][co] X[p + tap][ci] (and the bias gradient, through a
 //              row of ones) as a GEMM with M = (tap, ci), N = co, K = pixels on the tensor cores; the CTA transposes
 //              8x8 blocks of the NHWC tensors into K-major core matrices, accumulates 128-pixel stages in tensor
@@ -23,6 +28,8 @@
 //
 // Every wait on the tensor cores is bounded (about two seconds of %globaltimer); on expiry the kernel records an
 // error, waits once more (bounded) for the outstanding MMA, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cfloat>
@@ -178,6 +185,21 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// TMA: the 4-D box at (c, x, y, n) of the tensor map into shared memory; completion is counted on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c, int x, int y, int n, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c), "r"(x), "r"(y), "r"(n), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // 16 consecutive fp32 columns of this thread's tensor-memory lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
 {
@@ -330,6 +352,132 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(const __grid_constant__ C
                 }
                 if (a.gate) {
                     // bf16 bit patterns of positive values are positive int16 values other than 0.
+                    if ((int16_t)gv[c] <= 0) v0 = 0.0f;
+                    if ((int16_t)gv[c + 1] <= 0) v1 = 0.0f;
+                }
+                outw[c / 2] = (uint32_t)bf16_bits(v0) | ((uint32_t)bf16_bits(v1) << 16);
+            }
+#pragma unroll
+            for (int c = 0; c < COUT / 2; c += 4)
+                *reinterpret_cast<uint4*>(a.Y + p * COUT + 2 * c) = make_uint4(outw[c], outw[c + 1], outw[c + 2],
+                                                                               outw[c + 3]);
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_free(tmem, 32);
+}
+
+// ------------------------------------------------------------------------------------------------------------------
+// k_conv_tma: the convolution for c_in in {16, 32} on a 16 x 8 output block with a TMA-loaded halo.
+
+constexpr int kBlkH = 16, kBlkW = 8;                              // output block (M = 128 pixels, row-major)
+constexpr int kHaloH = kBlkH + 2, kHaloW = kBlkW + 2;             // 18 x 10 input pixels
+constexpr uint32_t kHaloBytes = kHaloH * kHaloW * 16;             // one 8-channel plane: 2880 bytes
+constexpr uint32_t kPlane = (kHaloBytes + 127) / 128 * 128;       // plane stride (TMA destinations are 128-aligned)
+
+template <int CIN, int COUT>
+constexpr size_t conv_tma_smem()
+{
+    return (size_t)(CIN / 8) * kPlane + (size_t)kpad(CIN) / 8 * COUT * 16 + 1024 + kGuard;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant__ CUtensorMap xmap,
+                                                          const __grid_constant__ ConvArgs a)
+{
+    static_assert(CIN % 16 == 0, "two 8-channel planes per MMA");
+    constexpr int KP = kpad(CIN);
+    constexpr int KC = KP / 8;
+    constexpr int NPL = CIN / 8;
+    constexpr uint32_t kLboB = COUT * 16;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t s_bar[2];   // 0: halo loaded, 1: MMAs done
+    __shared__ uint32_t s_tmem;
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = smem;                    // [NPL][18][10][16 B]
+    uint8_t* sB = smem + NPL * kPlane;     // [KC][COUT][16 B]
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int x0 = blockIdx.x * kBlkW, y0 = blockIdx.y * kBlkH, img = blockIdx.z;
+
+    if (warp == 0) tmem_alloc(&s_tmem, 32);
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&s_bar[0], NPL * kHaloBytes);
+#pragma unroll
+        for (int pl = 0; pl < NPL; pl++) tma_load_4d(sA + pl * kPlane, &xmap, pl * 8, x0 - 1, y0 - 1, img, &s_bar[0]);
+    }
+    // B: the weights, while the halo is in flight.
+    for (int u = tid; u < COUT * KC; u += kConvThreads) {
+        const int nrow = u % COUT, kc = u / COUT;
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.Wb + (int64_t)nrow * KP + kc * 8));
+        *reinterpret_cast<uint4*>(sB + kc * kLboB + (nrow >> 3) * 128 + (nrow & 7) * 16) = v;
+    }
+    fence_async_smem();
+    bool ok = mbar_wait_bounded(&s_bar[0], 0);
+    tc_before_sync();
+    ok = __syncthreads_and(ok);
+    tc_after_sync();
+    const uint32_t tmem = s_tmem;
+
+    if (ok && tid == 0) {
+        constexpr uint32_t idesc = idesc_bf16(128, COUT);
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; tap++) {
+            const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
+#pragma unroll
+            for (int j = 0; j < CIN / 16; j++)
+                mma_bf16(tmem, smem_desc(a0 + 2 * j * kPlane + shift, kPlane, kHaloW * 16),
+                         smem_desc(b0 + (tap * NPL + 2 * j) * kLboB, kLboB, 128), idesc,
+                         (tap > 0 || j > 0) ? 1u : 0u);
+        }
+        mma_commit(&s_bar[1]);
+    }
+    if (ok) {
+        ok = mbar_wait_bounded(&s_bar[1], 0);
+        if (!ok) mbar_wait_bounded(&s_bar[1], 0);
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicExch(&g_net_error, 1);
+    tc_after_sync();
+
+    if (ok) {
+        float acc[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, acc + c);
+        const int y = y0 + (tid >> 3), x = x0 + (tid & 7);
+        if (y < a.H && x < a.W) {
+            const int64_t p = ((int64_t)img * a.H + y) * a.W + x;
+            uint16_t gv[COUT];
+            if (a.gate) {
+#pragma unroll
+                for (int c = 0; c < COUT; c += 8) {
+                    const uint4 g = __ldg(reinterpret_cast<const uint4*>(a.gate + p * COUT + c));
+                    const uint16_t* gh = reinterpret_cast<const uint16_t*>(&g);
+#pragma unroll
+                    for (int i = 0; i < 8; i++) gv[c + i] = gh[i];
+                }
+            }
+            uint32_t outw[COUT / 2];
+#pragma unroll
+            for (int c = 0; c < COUT; c += 2) {
+                float v0 = acc[c], v1 = acc[c + 1];
+                if (a.bias) {
+                    v0 = __fadd_rn(v0, __ldg(a.bias + c));
+                    v1 = __fadd_rn(v1, __ldg(a.bias + c + 1));
+                }
+                if (a.relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                if (a.gate) {
                     if ((int16_t)gv[c] <= 0) v0 = 0.0f;
                     if ((int16_t)gv[c + 1] <= 0) v1 = 0.0f;
                 }
@@ -778,6 +926,13 @@ cudaError_t conv_attr()
 }
 
 template <int CIN, int COUT>
+cudaError_t conv_tma_attr()
+{
+    return cudaFuncSetAttribute(k_conv_tma<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)conv_tma_smem<CIN, COUT>());
+}
+
+template <int CIN, int COUT>
 cudaError_t wgrad_attr()
 {
     return cudaFuncSetAttribute(k_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -794,8 +949,8 @@ cudaError_t setup_device()
     if (e != cudaSuccess || dev < 0 || dev >= 64) return e != cudaSuccess ? e : cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
     if (done[dev]) return cudaSuccess;
-    if ((e = conv_attr<8, 16>()) != cudaSuccess || (e = conv_attr<16, 16>()) != cudaSuccess ||
-        (e = conv_attr<16, 32>()) != cudaSuccess || (e = conv_attr<32, 16>()) != cudaSuccess ||
+    if ((e = conv_attr<8, 16>()) != cudaSuccess || (e = conv_tma_attr<16, 16>()) != cudaSuccess ||
+        (e = conv_tma_attr<16, 32>()) != cudaSuccess || (e = conv_tma_attr<32, 16>()) != cudaSuccess ||
         (e = wgrad_attr<8, 16>()) != cudaSuccess || (e = wgrad_attr<16, 16>()) != cudaSuccess ||
         (e = wgrad_attr<16, 32>()) != cudaSuccess || (e = wgrad_attr<32, 16>()) != cudaSuccess)
         return e;
@@ -803,15 +958,52 @@ cudaError_t setup_device()
     return cudaSuccess;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of an NHWC bf16 tensor [n][H][W][C] with an 8-channel x 10 x 18 box (the halo of one output block);
+// coordinates outside the tensor read as zero.
+bool halo_map(CUtensorMap* map, const uint16_t* X, int n, int H, int W, int C)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(X) & 15)) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, (cuuint32_t)kHaloH, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t*>(X), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_conv(const ConvArgs& a, int cin, int cout, cudaStream_t st)
 {
     const int64_t P = (int64_t)a.n * a.H * a.W;
-    const unsigned grid = (unsigned)((P + 127) / 128);
-    if (grid == 0) return cudaSuccess;
-    if (cin == 8 && cout == 16) k_conv<8, 16><<<grid, kConvThreads, conv_smem<8, 16>(), st>>>(a);
-    else if (cin == 16 && cout == 16) k_conv<16, 16><<<grid, kConvThreads, conv_smem<16, 16>(), st>>>(a);
-    else if (cin == 16 && cout == 32) k_conv<16, 32><<<grid, kConvThreads, conv_smem<16, 32>(), st>>>(a);
-    else if (cin == 32 && cout == 16) k_conv<32, 16><<<grid, kConvThreads, conv_smem<32, 16>(), st>>>(a);
+    if (P == 0) return cudaSuccess;
+    if (cin == 8) {
+        if (cout != 16) return cudaErrorInvalidValue;
+        k_conv<8, 16><<<(unsigned)((P + 127) / 128), kConvThreads, conv_smem<8, 16>(), st>>>(a);
+        return cudaGetLastError();
+    }
+    CUtensorMap map;
+    if (!halo_map(&map, a.X, a.n, a.H, a.W, cin)) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((a.W + kBlkW - 1) / kBlkW), (unsigned)((a.H + kBlkH - 1) / kBlkH), (unsigned)a.n);
+    if (cin == 16 && cout == 16) k_conv_tma<16, 16><<<grid, kConvThreads, conv_tma_smem<16, 16>(), st>>>(map, a);
+    else if (cin == 16 && cout == 32) k_conv_tma<16, 32><<<grid, kConvThreads, conv_tma_smem<16, 32>(), st>>>(map, a);
+    else if (cin == 32 && cout == 16) k_conv_tma<32, 16><<<grid, kConvThreads, conv_tma_smem<32, 16>(), st>>>(map, a);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

@@ -61,17 +61,21 @@ def train(net: Net, D, labels, views, epochs: int = 1, batch: int = 32, lr: floa
 
 
 def logits_for(net: Net, frames, views):
-    """Tile logits of a list of [H][W] CUDA maps (frames of one size are run together)."""
+    """Tile logits of a list of [H][W] CUDA maps (frames of one size are run together, as many per call as the
+    network's activation scratch holds)."""
     import torch
     out = [None] * len(frames)
     by_size = {}
     for i, f in enumerate(frames):
         by_size.setdefault(tuple(f.shape), []).append(i)
-    for shape, idx in by_size.items():
-        D = torch.stack([frames[i] for i in idx]) if len(idx) > 1 else frames[idx[0]].unsqueeze(0)
-        s = net.forward(D.contiguous(), views)
-        for k, i in enumerate(idx):
-            out[i] = s[k]
+    for (H, W), idx in by_size.items():
+        per_call = max(1, net.max_pixels // (H * W))
+        for s0 in range(0, len(idx), per_call):
+            part = idx[s0:s0 + per_call]
+            D = torch.stack([frames[i] for i in part]) if len(part) > 1 else frames[part[0]].unsqueeze(0)
+            s = net.forward(D.contiguous(), views)
+            for k, i in enumerate(part):
+                out[i] = s[k]
     return out
 
 
