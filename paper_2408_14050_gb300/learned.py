@@ -12,7 +12,6 @@ target (0.999 by default).
 """
 from __future__ import annotations
 
-import time
 
 import numpy as np
 
@@ -80,7 +79,19 @@ def logits_for(net: Net, frames, views):
 
 
 def masks(ctx, frames, views, proposals=None):
-    Ms, _ = occ_detect_batched(ctx, frames, views, proposals=proposals)
+    """Masks of the plain (or, with proposals, the proposed) run, in batches that fit the context."""
+    Ms = []
+    s = 0
+    while s < len(frames):
+        e, px = s, 0
+        while e < len(frames) and e - s < 1024 and px + frames[e].numel() <= ctx.max_pixels:
+            px += frames[e].numel()
+            e += 1
+        if e == s:
+            raise ValueError("a frame is larger than the context")
+        part, _ = occ_detect_batched(ctx, frames[s:e], views, proposals=None if proposals is None else proposals[s:e])
+        Ms += part
+        s = e
     return Ms
 
 

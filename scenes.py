@@ -212,12 +212,13 @@ def array_3x3(frame: int = 0, H: int = 1080, W: int = 1920) -> Workload:
     return Workload(f"array3x3_{W}x{H}_8views", [make_scene(spec_array(H, W), seed_of(2, frame))], views_3x3())
 
 
-def mixed_batch(n_frames: int = 64, sizes=None) -> Workload:
-    """n_frames maps of uneven resolution (equal counts of each size, seeded shuffle), eight views each."""
+def mixed_batch(n_frames: int = 64, sizes=None, config: int = 3) -> Workload:
+    """n_frames maps of uneven resolution (equal counts of each size, seeded shuffle), eight views each.  Another
+    `config` draws other frames of the same recipe (e.g. held-out frames for calibration)."""
     sizes = sizes or MIXED_SIZES
     order = [sizes[i % len(sizes)] for i in range(n_frames)]
-    perm = np.argsort(CounterRng(seed_of(3, 1 << 20), key=4).uniform(n_frames), kind="stable")
-    frames = [make_scene(spec_array(*order[i]), seed_of(3, f)) for f, i in enumerate(perm)]
+    perm = np.argsort(CounterRng(seed_of(config, 1 << 20), key=4).uniform(n_frames), kind="stable")
+    frames = [make_scene(spec_array(*order[i]), seed_of(config, f)) for f, i in enumerate(perm)]
     return Workload(f"mixed_{n_frames}frames_8views", frames, views_3x3())
 
 
