@@ -453,9 +453,17 @@ __device__ __forceinline__ bool line_sample(const Args& a, const FrameArg& F, co
     return true;
 }
 
-__device__ __forceinline__ bool before(const LineSample& x, const LineSample& y)
+// The sort key is (W, k).  A sample read later along a line has the larger k, so it precedes an earlier one exactly
+// when its W is smaller; a sample of the first macro-run has a smaller k than every sample of the second, so it
+// precedes one of the second exactly when its W is not larger.
+__device__ __forceinline__ bool later_before(const LineSample& later, const LineSample& earlier)
 {
-    return x.w < y.w || (x.w == y.w && x.k < y.k);
+    return later.w < earlier.w;
+}
+
+__device__ __forceinline__ bool first_run_before(const LineSample& a, const LineSample& b)
+{
+    return a.w <= b.w;
 }
 
 // Eq. 5 / Eq. 6 over the emitted (sorted) stream: a window of the last N/2 samples, slot 0 the most recent.
@@ -519,9 +527,62 @@ __device__ __forceinline__ bool window_flush(const LineWindow& W, int32_t* Ov)
     return (W.hit != 0) || h0 || h1 || h2 || h3;
 }
 
+// The same window for N = 8 without moving samples between slots: the stream's i-th sample goes to slot i mod 4,
+// which held sample i - 4 (the oldest, whose count is final once tested against the new one).  Callers unroll their
+// loops by 4 so that every slot index is a compile-time constant; empty slots hold W = +inf, which no sample is close
+// to, so the first samples need no count of the window's fill.
+struct RotWindow {
+    float w[4], v[4], b[4];
+    int p[4], o[4];
+};
+
+__device__ __forceinline__ void rot_init(RotWindow& R)
+{
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        R.w[i] = __int_as_float(0x7f800000);
+        R.v[i] = R.b[i] = 0.0f;
+        R.p[i] = R.o[i] = 0;
+    }
+}
+
+template <int J, bool kHits>
+__device__ __forceinline__ void rot_push(RotWindow& R, const LineSample& e, float zeta, float beta, int32_t* Ov,
+                                         int& hit)
+{
+    const float eb = __fadd_rn(e.v, beta);
+    int eo = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const bool close = fabsf(__fsub_rn(e.w, R.w[i])) < zeta;
+        eo += (close && eb < R.v[i]) ? 1 : 0;
+        R.o[i] += (close && R.b[i] < e.v) ? 1 : 0;
+    }
+    if (R.o[J]) {
+        atomicAdd(Ov + R.p[J], R.o[J]);
+        if (kHits) hit = 1;
+    }
+    R.w[J] = e.w;
+    R.v[J] = e.v;
+    R.b[J] = eb;
+    R.p[J] = e.p;
+    R.o[J] = eo;
+}
+
+__device__ __forceinline__ bool rot_flush(const RotWindow& R, int32_t* Ov, int hit)
+{
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+        if (R.o[i]) {
+            atomicAdd(Ov + R.p[i], R.o[i]);
+            hit = 1;
+        }
+    return hit != 0;
+}
+
 // Pass 2 for two macro-runs [k0, ks - 1] and [ks, k1], each read through its own one-slot buffer; the merge emits
 // the smaller head, and the chosen run reads at most one sample per step.
-template <bool kWide, bool kHits>
+template <bool kWide, bool kHits, bool kHalf4>
 __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
                                              int cy, int h, int half, int k0, int k1, int ks)
 {
@@ -538,42 +599,62 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
     // First heads.
     if (kna <= ea) {
         line_sample<kWide>(a, F, va, tab, cx, cy, h, kna++, false, s);
-        if (before(s, bufa)) ha = s; else { ha = bufa; bufa = s; }
+        if (later_before(s, bufa)) ha = s; else { ha = bufa; bufa = s; }
     } else {
         ha = bufa;
         hba = false;
     }
     if (knb <= eb) {
         line_sample<kWide>(a, F, va, tab, cx, cy, h, knb++, false, s);
-        if (before(s, bufb)) hb = s; else { hb = bufb; bufb = s; }
+        if (later_before(s, bufb)) hb = s; else { hb = bufb; bufb = s; }
     } else {
         hb = bufb;
         hbb = false;
     }
-    while (has_a || has_b) {
-        const bool ta = has_a && (!has_b || before(ha, hb));
-        const LineSample e = ta ? ha : hb;
-        int kn = ta ? kna : knb;
-        const int ke = ta ? ea : eb;
-        bool hbuf = ta ? hba : hbb;
-        LineSample buf = ta ? bufa : bufb;
-        LineSample head = buf;
-        bool has = false;
-        if (kn <= ke) {
-            line_sample<kWide>(a, F, va, tab, cx, cy, h, kn, false, s);
-            kn++;
-            const bool sb = before(s, buf);
-            head = sb ? s : buf;
-            if (!sb) buf = s;
-            has = true;
-        } else if (hbuf) {
-            hbuf = false;
-            has = true;
-        }
-        if (ta) { kna = kn; hba = hbuf; bufa = buf; ha = head; has_a = has; }
-        else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; }
-        window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov);
+    // One merge step: the smaller head is emitted, its run advances by one sample through its buffer.
+#define OCC_MERGE_STEP(PUSH)                                                                   \
+    {                                                                                          \
+        const bool ta = has_a && (!has_b || first_run_before(ha, hb));                         \
+        const LineSample e = ta ? ha : hb;                                                     \
+        int kn = ta ? kna : knb;                                                               \
+        const int ke = ta ? ea : eb;                                                           \
+        bool hbuf = ta ? hba : hbb;                                                            \
+        LineSample buf = ta ? bufa : bufb;                                                     \
+        LineSample head = buf;                                                                 \
+        bool has = false;                                                                      \
+        if (kn <= ke) {                                                                        \
+            line_sample<kWide>(a, F, va, tab, cx, cy, h, kn, false, s);                        \
+            kn++;                                                                              \
+            const bool sb = later_before(s, buf);                                              \
+            head = sb ? s : buf;                                                               \
+            if (!sb) buf = s;                                                                  \
+            has = true;                                                                        \
+        } else if (hbuf) {                                                                     \
+            hbuf = false;                                                                      \
+            has = true;                                                                        \
+        }                                                                                      \
+        if (ta) { kna = kn; hba = hbuf; bufa = buf; ha = head; has_a = has; }                  \
+        else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; }                     \
+        PUSH;                                                                                  \
     }
+    if (kHalf4) {
+        RotWindow R;
+        rot_init(R);
+        int hit = 0;
+        for (;;) {
+            if (!(has_a || has_b)) break;
+            OCC_MERGE_STEP((rot_push<0, kHits>(R, e, a.zeta, a.beta, Ov, hit)))
+            if (!(has_a || has_b)) break;
+            OCC_MERGE_STEP((rot_push<1, kHits>(R, e, a.zeta, a.beta, Ov, hit)))
+            if (!(has_a || has_b)) break;
+            OCC_MERGE_STEP((rot_push<2, kHits>(R, e, a.zeta, a.beta, Ov, hit)))
+            if (!(has_a || has_b)) break;
+            OCC_MERGE_STEP((rot_push<3, kHits>(R, e, a.zeta, a.beta, Ov, hit)))
+        }
+        return rot_flush(R, Ov, hit);
+    }
+    while (has_a || has_b) OCC_MERGE_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov)))
+#undef OCC_MERGE_STEP
     return window_flush(Wn, Ov);
 }
 
@@ -632,8 +713,8 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
             runs = 1;
             continue;
         }
-        if (before(s, buf)) {
-            if (before(s, last)) {          // s would be emitted out of order: it starts a new macro-run
+        if (later_before(s, buf)) {
+            if (later_before(s, last)) {    // s would be emitted out of order: it starts a new macro-run
                 if (++runs > 2) return 3;
                 ks = k;
                 buf = s;
@@ -653,7 +734,7 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
 }
 
 // Pass 2 for a single macro-run [k0, k1], loads one sample ahead.
-template <bool kWide, bool kHits>
+template <bool kWide, bool kHits, bool kHalf4>
 __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov,
                                                int cx, int cy, int h, int half, int k0, int k1)
 {
@@ -690,6 +771,39 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
         pos(k0 + 1, pn, on);
         dn = __ldg(F.D + on);
     }
+    if (kHalf4) {
+        // The emitted stream is min(sample k, buffer) for k = k0 + 1 .. k1, then the buffer: n samples.
+        RotWindow R;
+        rot_init(R);
+        int hit = 0;
+        int k = k0 + 1;
+#define OCC_ROT_STEP(J)                                                                        \
+        {                                                                                      \
+            if (k > k1 + 1) break;                                                             \
+            LineSample e;                                                                      \
+            if (k <= k1) {                                                                     \
+                const int p = pn;                                                              \
+                const float dv = dn;                                                           \
+                if (k + 1 <= k1) {                                                             \
+                    pos(k + 1, pn, on);                                                        \
+                    dn = __ldg(F.D + on);                                                      \
+                }                                                                              \
+                const LineSample s = make(k, p, dv);                                           \
+                const bool sb = later_before(s, buf);                                          \
+                e = sb ? s : buf;                                                              \
+                if (!sb) buf = s;                                                              \
+            } else {                                                                           \
+                e = buf;                                                                       \
+            }                                                                                  \
+            rot_push<J, kHits>(R, e, a.zeta, a.beta, Ov, hit);                                 \
+            k++;                                                                               \
+        }
+        for (;;) {
+            OCC_ROT_STEP(0) OCC_ROT_STEP(1) OCC_ROT_STEP(2) OCC_ROT_STEP(3)
+        }
+#undef OCC_ROT_STEP
+        return rot_flush(R, Ov, hit);
+    }
     for (int k = k0 + 1; k <= k1; k++) {
         const int p = pn;
         const float dv = dn;
@@ -698,7 +812,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
             dn = __ldg(F.D + on);
         }
         const LineSample s = make(k, p, dv);
-        const bool sb = before(s, buf);
+        const bool sb = later_before(s, buf);
         const LineSample e = sb ? s : buf;
         if (!sb) buf = s;
         window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov);
@@ -709,7 +823,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
 
 constexpr int kStatsSmem = 512;   // (frame, view) statistics accumulated in shared memory before going global
 
-template <bool kWide, bool kHits>
+template <bool kWide, bool kHits, bool kHalf4>
 __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_constant__ Args a)
 {
     constexpr int kWarps = kLineThreads / 32;
@@ -734,14 +848,14 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
     };
     auto run1 = [&](const LineJob& jb) {
         const FrameArg& F = a.frames[jb.f];
-        const bool hit = line_counts1_p<kWide, kHits>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+        const bool hit = line_counts1_p<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
                                                        F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
                                                        jb.k0, jb.k1);
         if (kHits && hit) mark_hit(F, jb);
     };
     auto run2 = [&](const LineJob& jb) {
         const FrameArg& F = a.frames[jb.f];
-        const bool hit = line_counts2<kWide, kHits>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+        const bool hit = line_counts2<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
                                                      F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
                                                      jb.k0, jb.k1, jb.ks);
         if (kHits && hit) mark_hit(F, jb);
@@ -1175,7 +1289,7 @@ cudaError_t configure_kernels(int* lines_bps, int scan_bps[kNumClasses + 1])
                                   (int)scan_smem<1024, kWpb1>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<4096, kWpb2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<4096, kWpb2>())) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false, false>, kLineThreads, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false, false, true>, kLineThreads, 0)) !=
         cudaSuccess)
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[0], k_scan<256, kWpb0>, kWpb0 * 32,
@@ -1216,12 +1330,20 @@ cudaError_t launch_plan(const Args& a, cudaStream_t st)
 
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st)
 {
-    if (a.hits) {
-        if (wide) k_scan_lines<true, true><<<grid, kLineThreads, 0, st>>>(a);
-        else k_scan_lines<false, true><<<grid, kLineThreads, 0, st>>>(a);
+    // N = 8 (the default) takes the rotating window; wide frames and hit flags are the rarer variants.
+    const bool h4 = a.N == 8;
+    if (!wide && !a.hits) {
+        if (h4) k_scan_lines<false, false, true><<<grid, kLineThreads, 0, st>>>(a);
+        else k_scan_lines<false, false, false><<<grid, kLineThreads, 0, st>>>(a);
+    } else if (!wide) {
+        if (h4) k_scan_lines<false, true, true><<<grid, kLineThreads, 0, st>>>(a);
+        else k_scan_lines<false, true, false><<<grid, kLineThreads, 0, st>>>(a);
+    } else if (!a.hits) {
+        if (h4) k_scan_lines<true, false, true><<<grid, kLineThreads, 0, st>>>(a);
+        else k_scan_lines<true, false, false><<<grid, kLineThreads, 0, st>>>(a);
     } else {
-        if (wide) k_scan_lines<true, false><<<grid, kLineThreads, 0, st>>>(a);
-        else k_scan_lines<false, false><<<grid, kLineThreads, 0, st>>>(a);
+        if (h4) k_scan_lines<true, true, true><<<grid, kLineThreads, 0, st>>>(a);
+        else k_scan_lines<true, true, false><<<grid, kLineThreads, 0, st>>>(a);
     }
     return cudaGetLastError();
 }

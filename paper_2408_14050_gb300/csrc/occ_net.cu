@@ -822,6 +822,107 @@ __global__ void __launch_bounds__(kHeadThreads) k_head(const __grid_constant__ H
     }
 }
 
+// Inference only, up to kFwdViews views: the same tile logits as k_head with every view's pixel scores kept in
+// registers and the max / sum reductions of all views done together (two block barriers in all).
+constexpr int kFwdViews = 8;
+
+__global__ void __launch_bounds__(kHeadThreads) k_head_fwd(const __grid_constant__ HeadArgs a)
+{
+    constexpr ParamLayout L = param_layout();
+    constexpr int kWarps = kHeadThreads / 32;
+    __shared__ float s_g[kFwdViews][kFeat];
+    __shared__ float s_red[kWarps][kFwdViews];
+    const int t = blockIdx.x, img = blockIdx.y;
+    const int i = t / a.tx, j = t - i * a.tx;
+    const int y0 = i * kTile, x0 = j * kTile;
+    const int th = min(kTile, a.H - y0), tw = min(kTile, a.W - x0);
+    const int npx = th * tw;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int u = threadIdx.x; u < a.nv * kFeat; u += kHeadThreads) {
+        const int v = u / kFeat, c = u - v * kFeat;
+        float g = a.params[L.be + c];
+        for (int e = 0; e < kEnc; e++) g += a.params[L.we + c * kEnc + e] * a.enc[v][e];
+        s_g[v][c] = g;
+    }
+    __syncthreads();
+    const float b0 = a.params[L.b0];
+
+    float z[4][kFwdViews];
+    float m[kFwdViews];
+#pragma unroll
+    for (int v = 0; v < kFwdViews; v++) m[v] = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int q = threadIdx.x + k * kHeadThreads;
+        float f[kFeat];
+        const bool ok = q < npx;
+        if (ok) {
+            const int yy = y0 + q / tw, xx = x0 + q % tw;
+            const uint4* src = reinterpret_cast<const uint4*>(a.f + (((int64_t)img * a.H + yy) * a.W + xx) * kFeat);
+            const uint4 u0 = __ldg(src), u1 = __ldg(src + 1);
+            const uint16_t* h0 = reinterpret_cast<const uint16_t*>(&u0);
+            const uint16_t* h1 = reinterpret_cast<const uint16_t*>(&u1);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                f[c] = bf16_val(h0[c]);
+                f[8 + c] = bf16_val(h1[c]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kFwdViews; v++) {
+            float sum = 0.0f;
+            if (ok && v < a.nv) {
+#pragma unroll
+                for (int c = 0; c < kFeat; c++) sum += f[c] * s_g[v][c];
+                sum += b0;
+            } else {
+                sum = -INFINITY;
+            }
+            z[k][v] = sum;
+            m[v] = fmaxf(m[v], sum);
+        }
+    }
+    // Block max of every view.
+#pragma unroll
+    for (int v = 0; v < kFwdViews; v++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m[v] = fmaxf(m[v], __shfl_xor_sync(0xffffffffu, m[v], o));
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int v = 0; v < kFwdViews; v++) s_red[warp][v] = m[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < kFwdViews; v++) {
+        float r = s_red[0][v];
+        for (int w = 1; w < kWarps; w++) r = fmaxf(r, s_red[w][v]);
+        m[v] = r;
+    }
+    __syncthreads();
+    // Block sum of exp(z - max) of every view.
+    float se[kFwdViews];
+#pragma unroll
+    for (int v = 0; v < kFwdViews; v++) {
+        float sv = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; k++) sv += (z[k][v] > -INFINITY) ? expf(z[k][v] - m[v]) : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+        se[v] = sv;
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int v = 0; v < kFwdViews; v++) s_red[warp][v] = se[v];
+    __syncthreads();
+    if (threadIdx.x < a.nv) {
+        const int v = threadIdx.x;
+        float r = 0.0f;
+        for (int w = 0; w < kWarps; w++) r += s_red[w][v];
+        a.logits[(((int64_t)img * a.nv + v) * a.ty + i) * a.tx + j] = logf(r) + m[v] - logf((float)npx);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------------------------
 // Parameter kernels.
 
@@ -1233,7 +1334,8 @@ int occ_net_forward(occ_net* net, const float* D, int32_t n, int32_t H, int32_t 
     h.nv = n_views;
     h.params = net->params;
     h.logits = logits;
-    k_head<<<dim3((unsigned)(h.tx * h.ty), (unsigned)n), kHeadThreads, 0, st>>>(h);
+    if (n_views <= kFwdViews) k_head_fwd<<<dim3((unsigned)(h.tx * h.ty), (unsigned)n), kHeadThreads, 0, st>>>(h);
+    else k_head<<<dim3((unsigned)(h.tx * h.ty), (unsigned)n), kHeadThreads, 0, st>>>(h);
     return cudaGetLastError() == cudaSuccess ? OCC_OK : OCC_ERR_CUDA;
 }
 
