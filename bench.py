@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-fusion", action="store_true", help="skip the median-fusion / backward-warp measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and measuring the learned tile proposer")
     ap.add_argument("--learned-train-frames", type=int, default=20000)
+    ap.add_argument("--learned-cal-target", type=float, default=0.9995,
+                    help="pixel recall the skip threshold is calibrated for on held-out frames")
     ap.add_argument("--learned-eval-frames", type=int, default=16,
                     help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")
     return ap.parse_args()
@@ -401,6 +403,7 @@ def run_fusion(args, dev, frame, views):
     M, _ = occ.occ_detect(ctx, torch.from_numpy(frame).to(dev), views)
     out = torch.empty((V, H, W), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    clean = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     hbm_peak, _ = peaks()
     steps = max(3, min(args.steps, 50))
     res = {}
@@ -411,7 +414,8 @@ def run_fusion(args, dev, frame, views):
             fn()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         for a, b in ev:
-            flush.zero_()
+            flush.zero_()      # evict the inputs from L2 (untimed) ...
+            clean.sum()        # ... and leave it holding clean lines, so the timed kernel pays no write-backs
             a.record()
             fn()
             b.record()
@@ -423,7 +427,8 @@ def run_fusion(args, dev, frame, views):
     if int(st.item()) != occ.OCC_OK:
         raise RuntimeError("median fusion reported non-finite input")
     ctx.close()
-    res["config"] = f"{W}x{H}, {V} stereo maps -> D; {V} views warped with their masks; L2 flushed before each launch"
+    res["config"] = (f"{W}x{H}, {V} stereo maps -> D; {V} views warped with their masks; before each launch L2 is "
+                     "flushed by a 322 MB write, then a 322 MB read (clean lines)")
     return res
 
 
@@ -459,10 +464,11 @@ def run_learned(args, dev, views):
     lctx.close()
     del Dtr, Ltr
     # Calibration on held-out frames of the evaluation recipe (other seeds), for the recall target there.
-    cal = scenes.mixed_batch(n_frames=args.learned_eval_frames, config=33)
+    # The calibration target carries a margin over the 0.999 the evaluation must reach on frames it has not seen.
+    cal = scenes.mixed_batch(n_frames=2 * args.learned_eval_frames, config=33)
     cal_frames = [torch.from_numpy(f).to(dev) for f in cal.frames]
     cctx = occ.occ_create(dev.index, max_pixels=sum(int(f.numel()) for f in cal_frames), max_views=len(views))
-    th, rec_cal, sk_cal = learned.calibrate(net, cctx, cal_frames, views)
+    th, rec_cal, sk_cal = learned.calibrate(net, cctx, cal_frames, views, target_recall=args.learned_cal_target)
     cctx.close()
     del cal_frames
 
@@ -485,8 +491,9 @@ def run_learned(args, dev, views):
         "skipped_tiles": round(ev["skipped_tiles"], 4), "tiles": ev["tiles"],
         "ms_plain": round(ev["ms_plain"], 3), "ms_learned": round(ev["ms_learned"], 3), "ms_net": round(ev["ms_net"], 3),
         "threshold": round(th, 5),
-        "calibration": {"frames": f"{args.learned_eval_frames} held-out mixed frames (other seeds)",
-                        "pixel_recall": round(rec_cal, 6), "skipped_tiles": round(sk_cal, 4), "target": 0.999},
+        "calibration": {"frames": f"{2 * args.learned_eval_frames} held-out mixed frames (other seeds)",
+                        "pixel_recall": round(rec_cal, 6), "skipped_tiles": round(sk_cal, 4),
+                        "target": args.learned_cal_target},
         "training": {"frames": args.learned_train_frames, "frame": f"{W}x{H}", "epochs": 1, "batch": 32,
                      "steps": len(losses), "loss_first": round(losses[0], 4), "loss_last": round(losses[-1], 4),
                      "seconds": round(t_train, 2), "generation_seconds": round(t_gen, 1),

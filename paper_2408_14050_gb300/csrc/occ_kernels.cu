@@ -637,7 +637,7 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
         else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; }                     \
         PUSH;                                                                                  \
     }
-    if (kHalf4) {
+    if constexpr (kHalf4) {
         RotWindow R;
         rot_init(R);
         int hit = 0;
@@ -652,10 +652,11 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
             OCC_MERGE_STEP((rot_push<3, kHits>(R, e, a.zeta, a.beta, Ov, hit)))
         }
         return rot_flush(R, Ov, hit);
+    } else {
+        while (has_a || has_b) OCC_MERGE_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov)))
+        return window_flush(Wn, Ov);
     }
-    while (has_a || has_b) OCC_MERGE_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov)))
 #undef OCC_MERGE_STEP
-    return window_flush(Wn, Ov);
 }
 
 // Pass 1 with the next sample's load issued before the current one is used.
@@ -667,9 +668,8 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
     int runs = 0;
     LineSample buf{0.f, 0.f, 0, 0}, last{-INFINITY, 0.f, 0, -1};
     k0 = -1; k1 = -1; ks = -1; n = 0;
-    // Position of sample k: pixel index and element offset in D (pixel -1 outside the image).
-    auto pos = [&](int k, int& pix, int64_t& off) {
-        const int t = tab[k - h + kTabHalf];
+    // Position of sample k from its table word t: pixel index and element offset in D (pixel -1 outside the image).
+    auto pos = [&](int t, int k, int& pix, int64_t& off) {
         int px, py;
         pix = -1;
         off = 0;
@@ -688,15 +688,20 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
         pix = py * F.W + px;
         off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
     };
+    // Loads run ahead: the table word two samples ahead, D one sample ahead.
+    const int* tk = tab + (kTabHalf - h);
     int pn;
     int64_t on;
-    pos(0, pn, on);
+    pos(tk[0], 0, pn, on);
     float dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
+    int tnext = nk > 1 ? tk[1] : 0;
     for (int k = 0; k < nk; k++) {
         const int p = pn;
         const float dv = dn;
         if (k + 1 < nk) {
-            pos(k + 1, pn, on);
+            const int t = tnext;
+            if (k + 2 < nk) tnext = tk[k + 2];
+            pos(t, k + 1, pn, on);
             dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
         }
         if (p < 0) continue;
@@ -740,8 +745,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
 {
     LineWindow Wn;
     window_init(Wn);
-    auto pos = [&](int k, int& pix, int64_t& off) {
-        const int t = tab[k - h + kTabHalf];
+    auto pos = [&](int t, int k, int& pix, int64_t& off) {
         int px, py;
         if (t != kTabExact) {
             px = cx + (int)(int16_t)(t & 0xFFFF);
@@ -754,6 +758,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
         pix = py * F.W + px;
         off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
     };
+    const int* tk = tab + (kTabHalf - h);
     auto make = [&](int k, int p, float dv) -> LineSample {
         LineSample s;
         s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
@@ -764,14 +769,15 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
     };
     int pn;
     int64_t on;
-    pos(k0, pn, on);
+    pos(tk[k0], k0, pn, on);
     float dn = __ldg(F.D + on);
     LineSample buf = make(k0, pn, dn);
     if (k0 + 1 <= k1) {
-        pos(k0 + 1, pn, on);
+        pos(tk[k0 + 1], k0 + 1, pn, on);
         dn = __ldg(F.D + on);
     }
-    if (kHalf4) {
+    int tnext = k0 + 2 <= k1 ? tk[k0 + 2] : 0;   // table word of the sample after the one in flight
+    if constexpr (kHalf4) {
         // The emitted stream is min(sample k, buffer) for k = k0 + 1 .. k1, then the buffer: n samples.
         RotWindow R;
         rot_init(R);
@@ -785,7 +791,9 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
                 const int p = pn;                                                              \
                 const float dv = dn;                                                           \
                 if (k + 1 <= k1) {                                                             \
-                    pos(k + 1, pn, on);                                                        \
+                    const int t = tnext;                                                       \
+                    if (k + 2 <= k1) tnext = tk[k + 2];                                        \
+                    pos(t, k + 1, pn, on);                                                     \
                     dn = __ldg(F.D + on);                                                      \
                 }                                                                              \
                 const LineSample s = make(k, p, dv);                                           \
@@ -803,12 +811,14 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
         }
 #undef OCC_ROT_STEP
         return rot_flush(R, Ov, hit);
-    }
+    } else {
     for (int k = k0 + 1; k <= k1; k++) {
         const int p = pn;
         const float dv = dn;
         if (k + 1 <= k1) {
-            pos(k + 1, pn, on);
+            const int t = tnext;
+            if (k + 2 <= k1) tnext = tk[k + 2];
+            pos(t, k + 1, pn, on);
             dn = __ldg(F.D + on);
         }
         const LineSample s = make(k, p, dv);
@@ -819,6 +829,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
     }
     window_push<kHits>(Wn, buf, half, a.zeta, a.beta, Ov);
     return window_flush(Wn, Ov);
+    }
 }
 
 constexpr int kStatsSmem = 512;   // (frame, view) statistics accumulated in shared memory before going global
@@ -1006,12 +1017,34 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
     int cur_v = -1;
     unsigned long long acc_n = 0, acc_p = 0;
 
-    for (uint64_t item = (uint64_t)blockIdx.x * WPB + warp; item < total; item += (uint64_t)gridDim.x * WPB) {
-        const int i = item_owner(pref, nfv, (uint32_t)item);
+    // Work distribution: warp w owns the lines w, w + nwarps, w + 2 nwarps, ... (so that lines the line kernel
+    // left, which cluster along edges, spread over the warps).  It looks at 32 of them at once, one per lane, finds
+    // with one ballot which are its to do (all, or the flagged ones), and walks those.
+    const uint64_t gwarp = (uint64_t)blockIdx.x * WPB + warp, nwarps = (uint64_t)gridDim.x * WPB;
+    for (uint64_t round = 0;; round++) {
+        const uint64_t first = gwarp + round * 32 * nwarps;
+        if (first >= total) break;
+        const uint64_t mine = first + (uint64_t)lane * nwarps;
+        bool want = mine < total;
+        int my_i = 0;
+        uint32_t my_idx = 0;
+        if (want) {
+            my_i = item_owner(pref, nfv, (uint32_t)mine);
+            my_idx = (uint32_t)(mine - pref[my_i]);
+            if (a.use_fb) {
+                const int mf = my_i / a.nv, mv = my_i - mf * a.nv;
+                const FrameArg& MF = a.frames[mf];
+                want = (MF.fb[(int64_t)mv * MF.fb_words + (my_idx >> 5)] >> (my_idx & 31)) & 1u;
+            }
+        }
+        unsigned todo = __ballot_sync(kFull, want);
+        while (todo) {
+        const int jl = __ffs(todo) - 1;
+        todo &= todo - 1;
+        const int i = __shfl_sync(kFull, my_i, jl);
+        const int64_t idx = (int64_t)__shfl_sync(kFull, my_idx, jl);
         const int f = i / a.nv, v = i - f * a.nv;
         const FrameArg& F = a.frames[f];
-        const int64_t idx = (int64_t)(item - pref[i]);
-        if (a.use_fb && !((F.fb[(int64_t)v * F.fb_words + (idx >> 5)] >> (idx & 31)) & 1u)) continue;
         const uint32_t cw = F.cand[(int64_t)v * F.cap + idx];
         const ViewArg va = a.view[v];
         const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
@@ -1226,6 +1259,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
             acc_p += pair_count(n, half);
         }
         __syncwarp();
+        }
     }
     if (lane == 0 && cur_v >= 0) {
         const int cf = cur_v / a.nv, cv = cur_v - cf * a.nv;

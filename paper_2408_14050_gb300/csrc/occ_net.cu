@@ -54,8 +54,7 @@ constexpr int kHeadThreads = 256;
 constexpr int kConvThreads = 128;
 constexpr int kWgradStagesPerCta = 16;
 constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr int kGuard = 32768;   // shared memory past the operands, so that no descriptor reading can leave the CTA's
-                                // allocation
+constexpr int kGuard = 0;       // shared memory past the operands (the descriptors read only inside them)
 
 __host__ __device__ constexpr int kpad(int cin) { return ((9 * cin + 15) / 16) * 16; }
 

@@ -21,7 +21,7 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-@pytest.mark.parametrize("W", [301, 304])             # 304: four pixels per thread when n <= 8
+@pytest.mark.parametrize("W", [301, 304])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 9, 16, 17, 24, 32, 33, 64])
 def test_median_matches_oracle(n, W):
     H = 37
@@ -31,7 +31,7 @@ def test_median_matches_oracle(n, W):
     np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), oracle.median(maps).view(np.uint32))
 
 
-@pytest.mark.parametrize("offset", [4, 5])          # 4: 16-byte aligned rows (vector path); 5: scalar path
+@pytest.mark.parametrize("offset", [4, 5])          # 16-byte aligned and unaligned rows
 def test_median_full_size_ties_signed_zeros_and_pitch(offset):
     H, W = 1080, 1920
     D = scenes.make_scene(scenes.spec_array(H, W), scenes.seed_of(42, 0))
