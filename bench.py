@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-fusion", action="store_true", help="skip the median-fusion / backward-warp measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and measuring the learned tile proposer")
     ap.add_argument("--learned-train-frames", type=int, default=20000)
-    ap.add_argument("--learned-cal-target", type=float, default=0.9995,
+    ap.add_argument("--learned-cal-target", type=float, default=0.9999,
                     help="pixel recall the skip threshold is calibrated for on held-out frames")
     ap.add_argument("--learned-eval-frames", type=int, default=16,
                     help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")

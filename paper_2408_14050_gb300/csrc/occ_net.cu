@@ -36,6 +36,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -378,9 +379,11 @@ constexpr uint32_t kPlane = (kHaloBytes + 127) / 128 * 128;       // plane strid
 template <int CIN, int COUT>
 constexpr size_t conv_tma_smem()
 {
-    return (size_t)(CIN / 8) * kPlane + (size_t)kpad(CIN) / 8 * COUT * 16 + 1024 + kGuard;
+    return 2 * (size_t)(CIN / 8) * kPlane + (size_t)kpad(CIN) / 8 * COUT * 16 + 1024 + kGuard;
 }
 
+// Persistent: a CTA loads the weights once and walks output blocks b = blockIdx.x, + gridDim.x, ...; the halo of
+// the next block is loaded (TMA, second buffer) while the current block's MMAs and epilogue run.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant__ CUtensorMap xmap,
                                                           const __grid_constant__ ConvArgs a)
@@ -390,67 +393,93 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
     constexpr int KC = KP / 8;
     constexpr int NPL = CIN / 8;
     constexpr uint32_t kLboB = COUT * 16;
+    constexpr uint32_t kHalo = NPL * kPlane;   // one halo buffer
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t s_bar[2];   // 0: halo loaded, 1: MMAs done
+    __shared__ uint64_t s_bar[3];   // 0, 1: halo buffer loaded; 2: MMAs of the current block done
     __shared__ uint32_t s_tmem;
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = smem;                    // [NPL][18][10][16 B]
-    uint8_t* sB = smem + NPL * kPlane;     // [KC][COUT][16 B]
+    uint8_t* sA = smem;                    // 2 x [NPL][18][10][16 B]
+    uint8_t* sB = smem + 2 * kHalo;        // [KC][COUT][16 B]
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int x0 = blockIdx.x * kBlkW, y0 = blockIdx.y * kBlkH, img = blockIdx.z;
+    const int bx_n = (a.W + kBlkW - 1) / kBlkW, by_n = (a.H + kBlkH - 1) / kBlkH;
+    const int nblk = bx_n * by_n * a.n;
+    auto block_xy = [&](int b, int& x0, int& y0, int& img) {
+        img = b / (bx_n * by_n);
+        const int r = b - img * bx_n * by_n;
+        y0 = (r / bx_n) * kBlkH;
+        x0 = (r - (r / bx_n) * bx_n) * kBlkW;
+    };
+    auto load_halo = [&](int b, int buf) {
+        int x0, y0, img;
+        block_xy(b, x0, y0, img);
+        mbar_expect_tx(&s_bar[buf], NPL * kHaloBytes);
+#pragma unroll
+        for (int pl = 0; pl < NPL; pl++)
+            tma_load_4d(sA + buf * kHalo + pl * kPlane, &xmap, pl * 8, x0 - 1, y0 - 1, img, &s_bar[buf]);
+    };
 
     if (warp == 0) tmem_alloc(&s_tmem, 32);
     if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
+        mbar_init(&s_bar[2], 1);
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
     }
     __syncthreads();
     if (tid == 0) {
-        mbar_expect_tx(&s_bar[0], NPL * kHaloBytes);
-#pragma unroll
-        for (int pl = 0; pl < NPL; pl++) tma_load_4d(sA + pl * kPlane, &xmap, pl * 8, x0 - 1, y0 - 1, img, &s_bar[0]);
+        if ((int)blockIdx.x < nblk) load_halo(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < nblk) load_halo(blockIdx.x + gridDim.x, 1);
     }
-    // B: the weights, while the halo is in flight.
     for (int u = tid; u < COUT * KC; u += kConvThreads) {
         const int nrow = u % COUT, kc = u / COUT;
         const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.Wb + (int64_t)nrow * KP + kc * 8));
         *reinterpret_cast<uint4*>(sB + kc * kLboB + (nrow >> 3) * 128 + (nrow & 7) * 16) = v;
     }
     fence_async_smem();
-    bool ok = mbar_wait_bounded(&s_bar[0], 0);
     tc_before_sync();
-    ok = __syncthreads_and(ok);
+    __syncthreads();
     tc_after_sync();
     const uint32_t tmem = s_tmem;
-
-    if (ok && tid == 0) {
-        constexpr uint32_t idesc = idesc_bf16(128, COUT);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-#pragma unroll 1
-        for (int tap = 0; tap < 9; tap++) {
-            const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
+    float bias[COUT];
 #pragma unroll
-            for (int j = 0; j < CIN / 16; j++)
-                mma_bf16(tmem, smem_desc(a0 + 2 * j * kPlane + shift, kPlane, kHaloW * 16),
-                         smem_desc(b0 + (tap * NPL + 2 * j) * kLboB, kLboB, 128), idesc,
-                         (tap > 0 || j > 0) ? 1u : 0u);
-        }
-        mma_commit(&s_bar[1]);
-    }
-    if (ok) {
-        ok = mbar_wait_bounded(&s_bar[1], 0);
-        if (!ok) mbar_wait_bounded(&s_bar[1], 0);
-    }
-    ok = __syncthreads_and(ok);
-    if (!ok && tid == 0) atomicExch(&g_net_error, 1);
-    tc_after_sync();
+    for (int c = 0; c < COUT; c++) bias[c] = a.bias ? __ldg(a.bias + c) : 0.0f;
 
-    if (ok) {
+    bool ok = true;
+    int it = 0;
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x, it++) {
+        const int buf = it & 1;
+        ok = mbar_wait_bounded(&s_bar[buf], (uint32_t)((it >> 1) & 1));
+        ok = __syncthreads_and(ok);
+        if (!ok) break;
+        tc_after_sync();
+        if (tid == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, COUT);
+            const uint32_t a0 = smem_u32(sA + buf * kHalo), b0 = smem_u32(sB);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; tap++) {
+                const uint32_t shift = (uint32_t)(((tap / 3) * kHaloW + tap % 3) * 16);
+#pragma unroll
+                for (int j = 0; j < CIN / 16; j++)
+                    mma_bf16(tmem, smem_desc(a0 + 2 * j * kPlane + shift, kPlane, kHaloW * 16),
+                             smem_desc(b0 + (tap * NPL + 2 * j) * kLboB, kLboB, 128), idesc,
+                             (tap > 0 || j > 0) ? 1u : 0u);
+            }
+            mma_commit(&s_bar[2]);
+        }
+        ok = mbar_wait_bounded(&s_bar[2], (uint32_t)(it & 1));
+        if (!ok) mbar_wait_bounded(&s_bar[2], (uint32_t)(it & 1));
+        ok = __syncthreads_and(ok);
+        tc_after_sync();
+        if (!ok) break;
+        // The halo buffer is free again: fetch the block after next into it.
+        if (tid == 0 && b + 2 * (int)gridDim.x < nblk) load_halo(b + 2 * gridDim.x, buf);
+
         float acc[COUT];
 #pragma unroll
         for (int c = 0; c < COUT; c += 16) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, acc + c);
+        int x0, y0, img;
+        block_xy(b, x0, y0, img);
         const int y = y0 + (tid >> 3), x = x0 + (tid & 7);
         if (y < a.H && x < a.W) {
             const int64_t p = ((int64_t)img * a.H + y) * a.W + x;
@@ -467,11 +496,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
             uint32_t outw[COUT / 2];
 #pragma unroll
             for (int c = 0; c < COUT; c += 2) {
-                float v0 = acc[c], v1 = acc[c + 1];
-                if (a.bias) {
-                    v0 = __fadd_rn(v0, __ldg(a.bias + c));
-                    v1 = __fadd_rn(v1, __ldg(a.bias + c + 1));
-                }
+                float v0 = __fadd_rn(acc[c], bias[c]), v1 = __fadd_rn(acc[c + 1], bias[c + 1]);
                 if (a.relu) {
                     v0 = fmaxf(v0, 0.0f);
                     v1 = fmaxf(v1, 0.0f);
@@ -487,7 +512,11 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
                 *reinterpret_cast<uint4*>(a.Y + p * COUT + 2 * c) = make_uint4(outw[c], outw[c + 1], outw[c + 2],
                                                                                outw[c + 3]);
         }
+        // Every warp has read the accumulator before the next block's MMAs overwrite it.
+        tc_before_sync();
+        __syncthreads();
     }
+    if (!ok && tid == 0) atomicExch(&g_net_error, 1);
     tc_before_sync();
     __syncthreads();
     if (warp == 0) tmem_free(tmem, 32);
@@ -1100,7 +1129,17 @@ cudaError_t launch_conv(const ConvArgs& a, int cin, int cout, cudaStream_t st)
     }
     CUtensorMap map;
     if (!halo_map(&map, a.X, a.n, a.H, a.W, cin)) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((a.W + kBlkW - 1) / kBlkW), (unsigned)((a.H + kBlkH - 1) / kBlkH), (unsigned)a.n);
+    // Persistent grid: a few CTAs per SM, each walking output blocks.
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess)
+            sms = 148;
+        cudaGetLastError();
+    }
+    const int64_t nblk = (int64_t)((a.W + kBlkW - 1) / kBlkW) * ((a.H + kBlkH - 1) / kBlkH) * a.n;
+    const dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)sms * 4));
     if (cin == 16 && cout == 16) k_conv_tma<16, 16><<<grid, kConvThreads, conv_tma_smem<16, 16>(), st>>>(map, a);
     else if (cin == 16 && cout == 32) k_conv_tma<16, 32><<<grid, kConvThreads, conv_tma_smem<16, 32>(), st>>>(map, a);
     else if (cin == 32 && cout == 16) k_conv_tma<32, 16><<<grid, kConvThreads, conv_tma_smem<32, 16>(), st>>>(map, a);
