@@ -48,15 +48,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=120.0, help="seconds for the whole reference arm")
-    ap.add_argument("--batched-frames", type=int, default=16,
-                    help="frames of the mixed-size batch measured through a CUDA graph (0: skip)")
+    ap.add_argument("--batched-frames", type=int, default=64,
+                    help="frames of the mixed-size batch (640x480 .. 4096x2160) measured through a CUDA graph "
+                         "(0: skip)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="skip the median-fusion / backward-warp measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and measuring the learned tile proposer")
     ap.add_argument("--learned-train-frames", type=int, default=20000)
     ap.add_argument("--learned-cal-target", type=float, default=0.9999,
                     help="pixel recall the skip threshold is calibrated for on held-out frames")
-    ap.add_argument("--learned-eval-frames", type=int, default=16,
+    ap.add_argument("--learned-eval-frames", type=int, default=64,
                     help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")
     return ap.parse_args()
 
@@ -142,7 +143,7 @@ LAUNCHES_PER_DETECT = 9
 # DRAM bytes (read + write) per detect call of the scan stage (all its launches) from the ncu capture summarised in
 # profiles/, valid only for the kernel source it was taken on (sha256 prefix of csrc/occ_kernels.cu); reported as
 # null otherwise.
-MEASURED_TRAFFIC = {"scan": {"bytes": 83203840, "kernels_sha": "60a119739a322f65"}}
+MEASURED_TRAFFIC = {"scan": {"bytes": 84709120, "kernels_sha": "7b7939226a4b9b92"}}
 
 
 def kernels_sha() -> str:
@@ -349,7 +350,7 @@ def run_batched(args, dev, views, rank, world):
     import paper_2408_14050_gb300 as occ
     from paper_2408_14050_gb300 import autotune, shard
 
-    wl = scenes.mixed_batch(n_frames=args.batched_frames)
+    wl = scenes.mixed_batch(n_frames=args.batched_frames, workers=max(1, min(16, os.cpu_count() or 1)))
     Ds = [torch.from_numpy(f).to(dev) for f in wl.frames]
     px = sum(int(f.size) for f in wl.frames)
     V = len(views)
@@ -465,14 +466,14 @@ def run_learned(args, dev, views):
     del Dtr, Ltr
     # Calibration on held-out frames of the evaluation recipe (other seeds), for the recall target there.
     # The calibration target carries a margin over the 0.999 the evaluation must reach on frames it has not seen.
-    cal = scenes.mixed_batch(n_frames=2 * args.learned_eval_frames, config=33)
+    cal = scenes.mixed_batch(n_frames=2 * args.learned_eval_frames, config=33, workers=workers)
     cal_frames = [torch.from_numpy(f).to(dev) for f in cal.frames]
     cctx = occ.occ_create(dev.index, max_pixels=sum(int(f.numel()) for f in cal_frames), max_views=len(views))
     th, rec_cal, sk_cal = learned.calibrate(net, cctx, cal_frames, views, target_recall=args.learned_cal_target)
     cctx.close()
     del cal_frames
 
-    wl = scenes.mixed_batch(n_frames=args.learned_eval_frames)
+    wl = scenes.mixed_batch(n_frames=args.learned_eval_frames, workers=workers)
     frames = [torch.from_numpy(f).to(dev) for f in wl.frames]
     px = sum(int(f.numel()) for f in frames)
     ctx = occ.occ_create(dev.index, max_pixels=px, max_views=len(views))

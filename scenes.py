@@ -212,13 +212,24 @@ def array_3x3(frame: int = 0, H: int = 1080, W: int = 1920) -> Workload:
     return Workload(f"array3x3_{W}x{H}_8views", [make_scene(spec_array(H, W), seed_of(2, frame))], views_3x3())
 
 
-def mixed_batch(n_frames: int = 64, sizes=None, config: int = 3) -> Workload:
+def _array_scene(H: int, W: int, seed: int) -> np.ndarray:
+    return make_scene(spec_array(H, W), seed)
+
+
+def mixed_batch(n_frames: int = 64, sizes=None, config: int = 3, workers: int = 0) -> Workload:
     """n_frames maps of uneven resolution (equal counts of each size, seeded shuffle), eight views each.  Another
-    `config` draws other frames of the same recipe (e.g. held-out frames for calibration)."""
+    `config` draws other frames of the same recipe (e.g. held-out frames for calibration).  workers > 1 draws them
+    in a pool of spawned processes (same frames)."""
     sizes = sizes or MIXED_SIZES
     order = [sizes[i % len(sizes)] for i in range(n_frames)]
     perm = np.argsort(CounterRng(seed_of(config, 1 << 20), key=4).uniform(n_frames), kind="stable")
-    frames = [make_scene(spec_array(*order[i]), seed_of(config, f)) for f, i in enumerate(perm)]
+    jobs = [(*order[i], seed_of(config, f)) for f, i in enumerate(perm)]
+    if workers > 1 and n_frames > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            frames = pool.starmap(_array_scene, jobs, chunksize=1)
+    else:
+        frames = [_array_scene(*j) for j in jobs]
     return Workload(f"mixed_{n_frames}frames_8views", frames, views_3x3())
 
 
