@@ -95,6 +95,45 @@ __global__ void __launch_bounds__(kFuseThreads) k_median(const __grid_constant__
     if (bad) *a.status = OCC_ERR_NONFINITE_INPUT;
 }
 
+// Batcher's odd-even merge sorting network for 8 values (19 compare-exchanges).
+__device__ __forceinline__ void cex(float& a, float& b)
+{
+    const float lo = fminf(a, b), hi = fmaxf(a, b);
+    a = lo;
+    b = hi;
+}
+
+__device__ __forceinline__ void sort8(float (&v)[8])
+{
+    cex(v[0], v[1]); cex(v[2], v[3]); cex(v[4], v[5]); cex(v[6], v[7]);
+    cex(v[0], v[2]); cex(v[1], v[3]); cex(v[4], v[6]); cex(v[5], v[7]);
+    cex(v[1], v[2]); cex(v[5], v[6]);
+    cex(v[0], v[4]); cex(v[1], v[5]); cex(v[2], v[6]); cex(v[3], v[7]);
+    cex(v[2], v[4]); cex(v[3], v[5]);
+    cex(v[1], v[2]); cex(v[3], v[4]); cex(v[5], v[6]);
+}
+
+// Median of exactly N <= 8 maps (N a compile-time constant): the unused slots are the constant +inf, so the
+// compare-exchanges that involve them fold away, and the middle positions are known registers.
+template <int N>
+__global__ void __launch_bounds__(kFuseThreads) k_median_n(const __grid_constant__ MedianArgs a)
+{
+    static_assert(N >= 1 && N <= 8, "up to 8 maps");
+    const int x = blockIdx.x * kFuseThreads + threadIdx.x;
+    if (x >= a.W) return;
+    bool bad = false;
+    for (int y = blockIdx.y; y < a.H; y += gridDim.y) {
+        const int64_t off = (int64_t)y * a.pitch + x;
+        float v[8];
+#pragma unroll
+        for (int m = 0; m < 8; m++) v[m] = m < N ? median_in(__ldcs(a.maps[m] + off), bad) : __int_as_float(0x7f800000);
+        sort8(v);
+        const float med = (N & 1) ? v[N / 2] : __fmul_rn(__fadd_rn(v[N / 2 - 1], v[N / 2]), 0.5f);
+        a.D[(int64_t)y * a.d_pitch + x] = med;
+    }
+    if (bad) *a.status = OCC_ERR_NONFINITE_INPUT;
+}
+
 struct WarpArgs {
     const float* D;
     int H, W;
@@ -274,9 +313,20 @@ extern "C" int occ_fuse_median(const float* const* maps, int32_t n_maps, int32_t
     a.status = flag;
     const int cols = (W + kFuseThreads - 1) / kFuseThreads;
     const dim3 grid(cols, row_blocks(H, cols));
-    // One pixel per thread (full occupancy, eight 4-byte loads in flight per thread) measured faster than four
+    // One pixel per thread (full occupancy, up to eight 4-byte loads in flight per thread) measured faster than four
     // pixels per thread (16-byte loads, a quarter of the occupancy).
-    if (n_maps <= 8) k_median<8><<<grid, kFuseThreads, 0, st>>>(a);
+    if (n_maps <= 8) {
+        switch (n_maps) {
+        case 1: k_median_n<1><<<grid, kFuseThreads, 0, st>>>(a); break;
+        case 2: k_median_n<2><<<grid, kFuseThreads, 0, st>>>(a); break;
+        case 3: k_median_n<3><<<grid, kFuseThreads, 0, st>>>(a); break;
+        case 4: k_median_n<4><<<grid, kFuseThreads, 0, st>>>(a); break;
+        case 5: k_median_n<5><<<grid, kFuseThreads, 0, st>>>(a); break;
+        case 6: k_median_n<6><<<grid, kFuseThreads, 0, st>>>(a); break;
+        case 7: k_median_n<7><<<grid, kFuseThreads, 0, st>>>(a); break;
+        default: k_median_n<8><<<grid, kFuseThreads, 0, st>>>(a); break;
+        }
+    }
     else if (n_maps <= 16) k_median<16><<<grid, kFuseThreads, 0, st>>>(a);
     else if (n_maps <= 32) k_median<32><<<grid, kFuseThreads, 0, st>>>(a);
     else k_median<64><<<grid, kFuseThreads, 0, st>>>(a);
