@@ -371,19 +371,22 @@ def run_batched(args, dev, views, rank, world):
         g.replay()
     steps = max(3, min(args.steps, 20))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
     torch.cuda.synchronize()
+    clocks.start()
     e0.record()
     for _ in range(steps):
         g.replay()
     e1.record()
     torch.cuda.synchronize()
+    clk = clocks.stop()
     t = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     if occ.occ_get_status(ctx) != occ.OCC_OK:
         raise RuntimeError("batched detect failed")
     ctx.close()
     return {"value": round(steps * world * px * V / t / 1e6, 1), "unit": UNIT, "ms_per_step": round(t / steps * 1e3, 3),
             "frames": len(Ds), "pixels_per_frame_set": px, "views": V, "steps": steps, "cuda_graph": True,
-            "tuning": tuning, "l2": "inputs and outputs larger than L2"}
+            "tuning": tuning, "l2": "inputs and outputs larger than L2", "clocks": clk}
 
 
 def run_fusion(args, dev, frame, views):

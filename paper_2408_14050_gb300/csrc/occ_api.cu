@@ -56,6 +56,28 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 namespace occ {
 
+// The smallest binary32 s >= 0 whose correctly rounded square root exceeds gamma (+inf if none is finite).  The
+// rounded square root is non-decreasing in s, so fl(sqrt(s)) > gamma holds exactly for s >= this value; the
+// candidate test of Eq. 2 then needs no square root on the device.  Host sqrtf is the IEEE correctly rounded square
+// root, like the device's __fsqrt_rn.
+float sqrt_threshold(float gamma)
+{
+    if (gamma < 0.0f) return 0.0f;
+    uint32_t lo = 0, hi = 0x7f800000u;   // bit patterns of 0 and +inf; order of patterns = order of values
+    auto f = [](uint32_t b) {
+        float x;
+        std::memcpy(&x, &b, sizeof(x));
+        return x;
+    };
+    if (!(std::sqrt(f(hi - 1)) > gamma)) return f(hi);
+    while (lo < hi) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (std::sqrt(f(mid)) > gamma) hi = mid;
+        else lo = mid + 1;
+    }
+    return f(lo);
+}
+
 int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p_in, Args& a)
 {
     occ_params p;
@@ -78,6 +100,7 @@ int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p_in
         a.view[v].ridx = u;
     }
     a.gamma = p.gamma;
+    a.e2min = sqrt_threshold(p.gamma);
     a.zeta = p.zeta;
     a.beta = p.beta;
     a.Lover = p.L > 0 ? p.L : 0;

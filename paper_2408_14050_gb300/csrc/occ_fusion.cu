@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kWarpThreads) k_warp(const __grid_constant__ W
 // pixels' positions are computed first and their sixteen gathers issued together (out-of-range or occluded pixels
 // read a clamped, valid address and are zeroed afterwards), so that the gathers of a view overlap.
 struct WarpTap {
-    int64_t o00, o01, o10, o11;
+    int o00, o01, o10, o11;   // element offsets (the host checks that H x img_pitch fits in 31 bits)
     float fx, fy;
     bool ok;
 };
@@ -209,10 +209,11 @@ __device__ __forceinline__ WarpTap warp_tap(const WarpArgs& a, int v, int x, int
     const int y1 = y0 + 1 < a.H ? y0 + 1 : y0;
     t.fx = __fsub_rn(t.ok ? sx : 0.0f, fx0);
     t.fy = __fsub_rn(t.ok ? sy : 0.0f, fy0);
-    t.o00 = (int64_t)y0 * a.img_pitch + x0;
-    t.o01 = (int64_t)y0 * a.img_pitch + x1;
-    t.o10 = (int64_t)y1 * a.img_pitch + x0;
-    t.o11 = (int64_t)y1 * a.img_pitch + x1;
+    const int ip = (int)a.img_pitch;
+    t.o00 = y0 * ip + x0;
+    t.o01 = y0 * ip + x1;
+    t.o10 = y1 * ip + x0;
+    t.o11 = y1 * ip + x1;
     return t;
 }
 
@@ -223,7 +224,7 @@ __device__ __forceinline__ float bilinear(float fx, float fy, float i00, float i
     return __fadd_rn(top, __fmul_rn(fy, __fsub_rn(bot, top)));
 }
 
-__global__ void __launch_bounds__(kWarpThreads) k_warp4(const __grid_constant__ WarpArgs a)
+__global__ void __launch_bounds__(kWarpThreads, 5) k_warp4(const __grid_constant__ WarpArgs a)
 {
     const int q = blockIdx.x * kWarpThreads + threadIdx.x;
     const int x = 4 * q;
@@ -361,7 +362,8 @@ extern "C" int occ_warp_views(const float* D, int32_t H, int32_t W, int64_t pitc
     a.M = M;
     a.out = out;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if ((W & 3) == 0 && (pitch & 3) == 0 && aligned16(D) && aligned16(out) && (!M || (reinterpret_cast<uintptr_t>(M) & 3) == 0)) {
+    if ((W & 3) == 0 && (pitch & 3) == 0 && aligned16(D) && aligned16(out) &&
+        (!M || (reinterpret_cast<uintptr_t>(M) & 3) == 0) && (int64_t)H * img_pitch < ((int64_t)1 << 31)) {
         const int qcols = (W / 4 + kWarpThreads - 1) / kWarpThreads;
         k_warp4<<<dim3(qcols, row_blocks(H, qcols)), kWarpThreads, 0, st>>>(a);
     } else {

@@ -84,6 +84,7 @@ struct PlanEntry {
 struct Args {
     int32_t nf, nv, nr;           // frames, views, distinct ratios
     float gamma, zeta, beta;
+    float e2min;                  // smallest s >= 0 with fl(sqrt(s)) > gamma: E > gamma exactly when E_x^2 + E_y^2 >= e2min
     int32_t Lover;                // > 0: fixed scan length; else Eq. 3 per frame and view
     int32_t N;
     int32_t use_fb;               // the line kernel runs first: the warp kernels take only the lines it flagged

@@ -130,8 +130,9 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
                     const float dd = one ? dn[j] : __fmul_rn(r, dn[j]);
                     ex[j] = (x0 + j + 1 < W) ? __fsub_rn(rr, dr) : 0.0f;
                     ey[j] = hasd ? __fsub_rn(dd, dr) : 0.0f;
-                    const float e = __fsqrt_rn(__fadd_rn(__fmul_rn(ex[j], ex[j]), __fmul_rn(ey[j], ey[j])));
-                    pe[j] = valid[j] && (e > a.gamma);
+                    // E > gamma (Eq. 2) without the square root: E_x^2 + E_y^2 >= e2min is the same test.
+                    const float e2 = __fadd_rn(__fmul_rn(ex[j], ex[j]), __fmul_rn(ey[j], ey[j]));
+                    pe[j] = valid[j] && (e2 >= a.e2min);
                 }
                 for (int v = 0; v < a.nv; v++) {
                     if (a.view[v].ridx != u) continue;
@@ -161,44 +162,101 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
                 for (int v = 0; v < a.nv; v++) F.hits[(int64_t)v * tpv + t] = 0;
         }
 
-        // Compaction: warp totals per view, then one reservation per block and view.
-        for (int v = 0; v < a.nv; v++) {
-            uint32_t tot = 0;
+        // Compaction: warp totals per view, then one reservation per block and view; candidates keep pixel order.
+        if (a.nv <= 8) {
+            // Up to 8 views: the thread's candidate counts (0..4) of all views packed in bytes of one 64-bit word,
+            // so that one warp scan gives every view's prefix (a warp's total per view is at most 128).
+            uint32_t vm[8];
+            uint64_t packed = 0;
 #pragma unroll
-            for (int j = 0; j < 4; j++) tot += __popc(__ballot_sync(kFull, (bits[j] >> v) & 1ull));
-            if (lane == 0) s_tot[warp][v] = tot;
-        }
-        __syncthreads();
-        if (threadIdx.x < a.nv) {
-            const int v = threadIdx.x;
-            uint32_t sum = 0;
+            for (int v = 0; v < 8; v++) {
+                vm[v] = 0;
 #pragma unroll
-            for (int w = 0; w < kEdgeWarps; w++) sum += s_tot[w][v];
-            uint32_t base = sum ? atomicAdd(&F.hdr[HDR_COUNT + v], sum) : 0u;
-#pragma unroll
-            for (int w = 0; w < kEdgeWarps; w++) {
-                s_base[w][v] = base;
-                base += s_tot[w][v];
+                for (int j = 0; j < 4; j++) vm[v] |= (uint32_t)((bits[j] >> v) & 1ull) << j;
+                packed |= (uint64_t)__popc(vm[v]) << (8 * v);
             }
-        }
-        __syncthreads();
-        for (int v = 0; v < a.nv; v++) {
-            unsigned bal[4];
-            uint32_t pre = 0;
+            uint64_t incl = packed;
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                bal[j] = __ballot_sync(kFull, (bits[j] >> v) & 1ull);
-                pre += __popc(bal[j] & lt);
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
             }
-            uint32_t pos = s_base[warp][v] + pre;
+            const uint64_t total = __shfl_sync(kFull, incl, 31);
+            const uint64_t excl = incl - packed;
+            if (lane == 0)
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if ((bits[j] >> v) & 1ull) {
-                    if ((int64_t)pos < F.cap)
-                        F.cand[(int64_t)v * F.cap + pos] = ((uint32_t)y << 16) | (uint32_t)(x0 + j);
-                    else
-                        atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
-                    pos++;
+                for (int v = 0; v < 8; v++)
+                    if (v < a.nv) s_tot[warp][v] = (uint32_t)((total >> (8 * v)) & 0xffu);
+            __syncthreads();
+            if (threadIdx.x < a.nv) {
+                const int v = threadIdx.x;
+                uint32_t sum = 0;
+#pragma unroll
+                for (int w = 0; w < kEdgeWarps; w++) sum += s_tot[w][v];
+                uint32_t base = sum ? atomicAdd(&F.hdr[HDR_COUNT + v], sum) : 0u;
+#pragma unroll
+                for (int w = 0; w < kEdgeWarps; w++) {
+                    s_base[w][v] = base;
+                    base += s_tot[w][v];
+                }
+            }
+            __syncthreads();
+            if (packed) {
+#pragma unroll
+                for (int v = 0; v < 8; v++) {
+                    uint32_t m = vm[v];
+                    if (v >= a.nv || !m) continue;
+                    uint32_t pos = s_base[warp][v] + (uint32_t)((excl >> (8 * v)) & 0xffu);
+                    while (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        if ((int64_t)pos < F.cap)
+                            F.cand[(int64_t)v * F.cap + pos] = ((uint32_t)y << 16) | (uint32_t)(x0 + j);
+                        else
+                            atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
+                        pos++;
+                    }
+                }
+            }
+        } else {
+            for (int v = 0; v < a.nv; v++) {
+                uint32_t tot = 0;
+#pragma unroll
+                for (int j = 0; j < 4; j++) tot += __popc(__ballot_sync(kFull, (bits[j] >> v) & 1ull));
+                if (lane == 0) s_tot[warp][v] = tot;
+            }
+            __syncthreads();
+            if (threadIdx.x < a.nv) {
+                const int v = threadIdx.x;
+                uint32_t sum = 0;
+#pragma unroll
+                for (int w = 0; w < kEdgeWarps; w++) sum += s_tot[w][v];
+                uint32_t base = sum ? atomicAdd(&F.hdr[HDR_COUNT + v], sum) : 0u;
+#pragma unroll
+                for (int w = 0; w < kEdgeWarps; w++) {
+                    s_base[w][v] = base;
+                    base += s_tot[w][v];
+                }
+            }
+            __syncthreads();
+            for (int v = 0; v < a.nv; v++) {
+                unsigned bal[4];
+                uint32_t pre = 0;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    bal[j] = __ballot_sync(kFull, (bits[j] >> v) & 1ull);
+                    pre += __popc(bal[j] & lt);
+                }
+                uint32_t pos = s_base[warp][v] + pre;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if ((bits[j] >> v) & 1ull) {
+                        if ((int64_t)pos < F.cap)
+                            F.cand[(int64_t)v * F.cap + pos] = ((uint32_t)y << 16) | (uint32_t)(x0 + j);
+                        else
+                            atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
+                        pos++;
+                    }
                 }
             }
         }
