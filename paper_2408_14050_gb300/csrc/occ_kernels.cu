@@ -753,9 +753,11 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
     pos(tk[0], 0, pn, on);
     float dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
     int tnext = nk > 1 ? tk[1] : 0;
+    float gk = (float)(-h) - 1.0f;   // g = k - h as a float counter (exact: |g| < 2^24)
     for (int k = 0; k < nk; k++) {
         const int p = pn;
         const float dv = dn;
+        gk += 1.0f;
         if (k + 1 < nk) {
             const int t = tnext;
             if (k + 2 < nk) tnext = tk[k + 2];
@@ -765,7 +767,7 @@ __device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, con
         if (p < 0) continue;
         LineSample s;
         s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
-        s.w = __fsub_rn((float)(k - h), s.v);
+        s.w = __fsub_rn(gk, s.v);
         s.p = p;
         s.k = k;
         if (k0 < 0) k0 = k;
@@ -841,6 +843,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
         rot_init(R);
         int hit = 0;
         int k = k0 + 1;
+        float gk = (float)(k0 + 1 - h);   // g of sample k as a float counter (exact: |g| < 2^24)
 #define OCC_ROT_STEP(J)                                                                        \
         {                                                                                      \
             if (k > k1 + 1) break;                                                             \
@@ -854,7 +857,11 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
                     pos(t, k + 1, pn, on);                                                     \
                     dn = __ldg(F.D + on);                                                      \
                 }                                                                              \
-                const LineSample s = make(k, p, dv);                                           \
+                LineSample s;                                                                  \
+                s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);                               \
+                s.w = __fsub_rn(gk, s.v);                                                      \
+                s.p = p;                                                                       \
+                s.k = k;                                                                       \
                 const bool sb = later_before(s, buf);                                          \
                 e = sb ? s : buf;                                                              \
                 if (!sb) buf = s;                                                              \
@@ -863,6 +870,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
             }                                                                                  \
             rot_push<J, kHits>(R, e, a.zeta, a.beta, Ov, hit);                                 \
             k++;                                                                               \
+            gk += 1.0f;                                                                        \
         }
         for (;;) {
             OCC_ROT_STEP(0) OCC_ROT_STEP(1) OCC_ROT_STEP(2) OCC_ROT_STEP(3)

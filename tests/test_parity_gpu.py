@@ -258,3 +258,30 @@ def test_invalid_arguments(ctx):
             occ.occ_detect(ctx, D, views)
     with pytest.raises(occ.OccError):
         occ.occ_detect(ctx, D, [(0.0, 1.0)] * 25)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.1, 0.25, 1.0, 3.0])
+def test_edge_threshold_boundaries_exact(ctx, gamma):
+    """Forward differences placed on and around the edge threshold of Eq. 2 (a few ulps either side, and pairs
+    E_x, E_y whose squares sum to the boundary), so that the strict E > gamma is tested where rounding decides it."""
+    rng = np.random.default_rng(int(gamma * 100) + 1)
+    g = np.float32(gamma)
+    near = [g]
+    v = g
+    for _ in range(4):
+        v = np.nextafter(v, np.float32(np.inf))
+        near.append(v)
+    v = g
+    for _ in range(4):
+        v = np.nextafter(v, np.float32(-np.inf))
+        near.append(v)
+    near = np.array(near + [np.float32(gamma) * np.float32(np.sqrt(0.5))] * 4, dtype=np.float32)
+    H, W = 40, 2 * 96
+    D = np.zeros((H, W), np.float32)
+    for y in range(H):
+        cols = rng.choice(near, W // 2)
+        D[y, 1::2] = cols
+        if y % 2:                                       # vertical differences as well
+            D[y] += rng.choice(near, W) * np.float32(0.5)
+    D = np.abs(D).astype(np.float32)
+    assert_exact(ctx, D, [(0.0, 1.0), (45.0, 1.4142135), (90.0, 1.0), (180.0, 2.0)], dict(gamma=gamma, L=12))
