@@ -137,6 +137,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.pref_cls = sc.pref + (nf * nv + 1);
     a.ptab = sc.ptab;
     a.status = sc.status;
+    a.line_ctr = sc.status + 1;   // the status region has room for the counter
     a.max_quads = 0;
     a.max_px = 0;
     a.hits = 0;
@@ -145,7 +146,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     FrameChunk chunk;
     std::memset(&chunk, 0, sizeof(chunk));
     chunk.dst = sc.frames;
-    int64_t cand_off = 0, fb_off = 0;
+    int64_t cand_off = 0, fb_off = 0, px_views = 0;
     bool wide = false;
     for (int f = 0; f < nf; f++) {
         FrameArg& F = chunk.f[f % kFramesPerChunk];
@@ -171,6 +172,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         F.prop = fr[f].prop;
         F.hits = fr[f].hits;
         if (F.hits) a.hits = 1;
+        px_views += (int64_t)F.H * F.W * nv;
         F.tiles_x = (F.W + kTile - 1) / kTile;
         F.tiles_y = (F.H + kTile - 1) / kTile;
         const int quads = F.H * ((F.W + 3) / 4);
@@ -184,11 +186,13 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         }
     }
     if (cand_off > sc.cand_entries || (lines && fb_off > sc.fb_entries)) return OCC_ERR_INVALID_ARG;
+    // Above about four 1920x1080 frames of 8 views, static chunks let warps drift over more data than L2 holds.
+    a.line_dyn = px_views > (int64_t)64 * 1024 * 1024 ? 1 : 0;
 
     auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], st) == cudaSuccess; };
     if (cudaMemsetAsync(sc.hdr, 0, sizeof(uint32_t) * HDR_WORDS * nf, st) != cudaSuccess ||
         cudaMemsetAsync(sc.stats, 0, sizeof(unsigned long long) * 2 * sc.max_views * nf, st) != cudaSuccess ||
-        cudaMemsetAsync(sc.status, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(sc.status, 0, 2 * sizeof(uint32_t), st) != cudaSuccess ||
         (lines && cudaMemsetAsync(sc.fb, 0, sizeof(uint32_t) * fb_off, st) != cudaSuccess))
         return OCC_ERR_CUDA;
     // Size classes of the warp kernels that can receive work: with a fixed L only one.

@@ -90,6 +90,7 @@ struct Args {
     int32_t use_fb;               // the line kernel runs first: the warp kernels take only the lines it flagged
     int32_t line_max_runs;        // the line kernel keeps lines of at most this many macro-runs (1 or 2)
     int32_t hits;                 // some frame asks for per-tile hit flags
+    int32_t line_dyn;             // the line kernel takes its chunks from a counter (large calls)
     int32_t max_quads;            // max over frames of H * ceil(W / 4)
     int64_t max_px;               // max over frames of n_views * H * W
     ViewArg view[kMaxViews];
@@ -100,6 +101,7 @@ struct Args {
     uint32_t* pref_cls;           // [kNumClasses][nf * nv + 1] the same restricted to each size class
     int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact
     uint32_t* status;             // OR of every frame's status bits
+    uint32_t* line_ctr;           // work counter of the line kernel, zero at the start of a call
 };
 
 // At most kFramesPerChunk frame records travel in the parameters of one k_frames launch (under 4 KB).

@@ -900,7 +900,7 @@ __device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F,
 
 constexpr int kStatsSmem = 512;   // (frame, view) statistics accumulated in shared memory before going global
 
-template <bool kWide, bool kHits, bool kHalf4>
+template <bool kWide, bool kHits, bool kHalf4, bool kDyn>
 __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_constant__ Args a)
 {
     constexpr int kWarps = kLineThreads / 32;
@@ -951,8 +951,14 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
         }
     };
 
-    const uint64_t stride = (uint64_t)gridDim.x * kLineThreads;
-    for (uint64_t b0 = ((uint64_t)blockIdx.x * kWarps + warp) * 32; b0 < total; b0 += stride) {
+    // Work distribution in chunks of 32 lines.  Small calls: warp w takes chunks w, w + n_warps, ... (static).
+    // Large calls (kDyn): after its first chunk a warp takes the next one from a counter, so that the lines in
+    // flight stay within a narrow window of the item order (one frame and view at a time) however far warps drift
+    // apart, and the D and O planes they touch stay in L2 for large frames and long batches.
+    const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+    for (uint64_t chunk = (uint64_t)blockIdx.x * kWarps + warp;;) {
+        const uint64_t b0 = chunk * 32;
+        if (b0 >= total) break;
         // Pass 1 for 32 lines, one per lane.
         const uint64_t item = b0 + lane;
         int runs = 0;
@@ -1001,6 +1007,13 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
             n2 -= 32;
         }
         __syncwarp();
+        if constexpr (kDyn) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(a.line_ctr, 1u);
+            chunk = nwarps + __shfl_sync(kFull, c, 0);
+        } else {
+            chunk += nwarps;
+        }
     }
     // Drain the queues.
     if (lane < n1) run1(q1[lane]);
@@ -1389,7 +1402,7 @@ cudaError_t configure_kernels(int* lines_bps, int scan_bps[kNumClasses + 1])
                                   (int)scan_smem<1024, kWpb1>())) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_scan<4096, kWpb2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)scan_smem<4096, kWpb2>())) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false, false, true>, kLineThreads, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(lines_bps, k_scan_lines<false, false, true, false>, kLineThreads, 0)) !=
         cudaSuccess)
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&scan_bps[0], k_scan<256, kWpb0>, kWpb0 * 32,
@@ -1430,21 +1443,26 @@ cudaError_t launch_plan(const Args& a, cudaStream_t st)
 
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st)
 {
-    // N = 8 (the default) takes the rotating window; wide frames and hit flags are the rarer variants.
+    // N = 8 (the default) takes the rotating window; wide frames and hit flags are the rarer variants; large calls
+    // take their chunks from a counter.
     const bool h4 = a.N == 8;
-    if (!wide && !a.hits) {
-        if (h4) k_scan_lines<false, false, true><<<grid, kLineThreads, 0, st>>>(a);
-        else k_scan_lines<false, false, false><<<grid, kLineThreads, 0, st>>>(a);
-    } else if (!wide) {
-        if (h4) k_scan_lines<false, true, true><<<grid, kLineThreads, 0, st>>>(a);
-        else k_scan_lines<false, true, false><<<grid, kLineThreads, 0, st>>>(a);
-    } else if (!a.hits) {
-        if (h4) k_scan_lines<true, false, true><<<grid, kLineThreads, 0, st>>>(a);
-        else k_scan_lines<true, false, false><<<grid, kLineThreads, 0, st>>>(a);
+#define OCC_LINES(W, HI, DY)                                                                       \
+    do {                                                                                           \
+        if (h4) k_scan_lines<W, HI, true, DY><<<grid, kLineThreads, 0, st>>>(a);                   \
+        else k_scan_lines<W, HI, false, DY><<<grid, kLineThreads, 0, st>>>(a);                     \
+    } while (0)
+    if (a.line_dyn) {
+        if (!wide && !a.hits) OCC_LINES(false, false, true);
+        else if (!wide) OCC_LINES(false, true, true);
+        else if (!a.hits) OCC_LINES(true, false, true);
+        else OCC_LINES(true, true, true);
     } else {
-        if (h4) k_scan_lines<true, true, true><<<grid, kLineThreads, 0, st>>>(a);
-        else k_scan_lines<true, true, false><<<grid, kLineThreads, 0, st>>>(a);
+        if (!wide && !a.hits) OCC_LINES(false, false, false);
+        else if (!wide) OCC_LINES(false, true, false);
+        else if (!a.hits) OCC_LINES(true, false, false);
+        else OCC_LINES(true, true, false);
     }
+#undef OCC_LINES
     return cudaGetLastError();
 }
 

@@ -1129,15 +1129,12 @@ cudaError_t launch_conv(const ConvArgs& a, int cin, int cout, cudaStream_t st)
     }
     CUtensorMap map;
     if (!halo_map(&map, a.X, a.n, a.H, a.W, cin)) return cudaErrorInvalidValue;
-    // Persistent grid: a few CTAs per SM, each walking output blocks.
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                      cudaSuccess)
-            sms = 148;
-        cudaGetLastError();
-    }
+    // Persistent grid: a few CTAs per SM of the current device, each walking output blocks.
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+        sms = 148;
+    cudaGetLastError();
     const int64_t nblk = (int64_t)((a.W + kBlkW - 1) / kBlkW) * ((a.H + kBlkH - 1) / kBlkH) * a.n;
     const dim3 grid((unsigned)std::min<int64_t>(nblk, (int64_t)sms * 4));
     if (cin == 16 && cout == 16) k_conv_tma<16, 16><<<grid, kConvThreads, conv_tma_smem<16, 16>(), st>>>(map, a);
