@@ -1135,28 +1135,70 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
 
         // Eq. 4: positions, bounds, V = D_r at the nearest pixel, W = g - V.
         int k0 = -1, kl = -1, n = 0;
-        for (int base = 0; base < nk; base += 32) {
-            const int k = base + lane;
-            bool ok = false;
-            if (k < nk) {
-                const float g = (float)(k - h);
-                const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
-                const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
-                ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
-                if (ok) {
-                    const int px = (int)rx, py = (int)ry;
-                    const float dv = __ldg(F.D + (int64_t)py * F.pitch + px);
-                    const float V = one ? dv : __fmul_rn(va.r, dv);
-                    S.uw[k] = __fsub_rn(g, V);
-                    S.uv[k] = V;
-                    S.upix[k] = py * W + px;
-                }
-            }
+        auto record = [&](int base, bool ok) {
             const unsigned b = __ballot_sync(kFull, ok);
             if (b) {
                 if (k0 < 0) k0 = base + __ffs(b) - 1;
                 kl = base + 31 - __clz(b);
                 n += __popc(b);
+            }
+        };
+        if constexpr (CAP <= 256) {
+            // Every lane's gathers (at most CAP / 32) are issued before any is used.
+            constexpr int kSl = CAP / 32;
+            float dvs[kSl];
+            int pxs[kSl];
+            bool oks[kSl];
+#pragma unroll
+            for (int i = 0; i < kSl; i++) {
+                const int k = i * 32 + lane;
+                oks[i] = false;
+                dvs[i] = 0.0f;
+                pxs[i] = 0;
+                if (k < nk) {
+                    const float g = (float)(k - h);
+                    const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
+                    const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
+                    oks[i] = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
+                    if (oks[i]) {
+                        const int px = (int)rx, py = (int)ry;
+                        dvs[i] = __ldg(F.D + (int64_t)py * F.pitch + px);
+                        pxs[i] = py * W + px;
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kSl; i++) {
+                const int base = i * 32;
+                if (base >= nk) break;
+                const int k = base + lane;
+                if (oks[i]) {
+                    const float V = one ? dvs[i] : __fmul_rn(va.r, dvs[i]);
+                    S.uw[k] = __fsub_rn((float)(k - h), V);
+                    S.uv[k] = V;
+                    S.upix[k] = pxs[i];
+                }
+                record(base, oks[i]);
+            }
+        } else {
+            for (int base = 0; base < nk; base += 32) {
+                const int k = base + lane;
+                bool ok = false;
+                if (k < nk) {
+                    const float g = (float)(k - h);
+                    const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
+                    const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
+                    ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
+                    if (ok) {
+                        const int px = (int)rx, py = (int)ry;
+                        const float dv = __ldg(F.D + (int64_t)py * F.pitch + px);
+                        const float V = one ? dv : __fmul_rn(va.r, dv);
+                        S.uw[k] = __fsub_rn(g, V);
+                        S.uv[k] = V;
+                        S.upix[k] = py * W + px;
+                    }
+                }
+                record(base, ok);
             }
         }
         // The samples inside the image form one interval of k (positions are monotone in g).
