@@ -141,16 +141,25 @@ class ClockSampler:
 LAUNCHES_PER_DETECT = 9
 
 # DRAM bytes (read + write) per detect call of the scan stage (all its launches) from the ncu capture summarised in
-# profiles/, valid only for the kernel source it was taken on (sha256 prefix of csrc/occ_kernels.cu); reported as
-# null otherwise.
-MEASURED_TRAFFIC = {"scan": {"bytes": 83853696, "kernels_sha": "8db6557aaf2b3286"}}
+# profiles/, valid only for the kernel code it was taken on (sha256 prefix of csrc/occ_kernels.cu without comments
+# and blank space); reported as null otherwise.
+MEASURED_TRAFFIC = {"scan": {"bytes": 83853696, "kernels_sha": "a2e1f3f12a1e8a8d"}}
+
+
+def code_sha(src: str) -> str:
+    """sha256 prefix of a CUDA source with its comments and blank space removed: comment edits do not change it."""
+    import hashlib
+    import re
+    code = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    code = re.sub(r"//[^\n]*", " ", code)
+    code = re.sub(r"\s+", " ", code).strip()
+    return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
 def kernels_sha() -> str:
-    import hashlib
     path = os.path.join(ROOT, "paper_2408_14050_gb300", "csrc", "occ_kernels.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    with open(path, encoding="utf-8") as f:
+        return code_sha(f.read())
 
 
 def measured_traffic(kernel: str):

@@ -1,13 +1,20 @@
 // occ_kernels.cu -- sm_103a kernels of the fast edge-aware occlusion detection (Sippel, Seiler, Kaup, ICIP 2024,
 // Section 3).
 //
-//   k_edges  one pass over D: Eq. 1 forward differences on D_r = fl(r D) for every distinct baseline ratio, the
-//            candidate predicate of Eq. 2 for every view, warp-ballot compaction of the candidate lists, the min/max
-//            reduction Eq. 3 needs, the non-finite check, the optional E / A maps, and the zeroing of O.
-//   k_scan   one warp per candidate: the scan line of Eq. 4 (positions, gather of V, warp W = G - V), the sort by
-//            (W, k) as a merge of the line's monotone runs, the neighbour test of Eq. 5, and the accumulation of
-//            the counts into O (Eq. 6, summed over all scan lines).
-//   k_mask   M = (O > 0) (Eq. 6).
+//   k_frames      frame records of a batch, from launch parameters into device memory.
+//   k_tables      per view, the scan-line pixel offsets round(fl(cos a * g)), round(fl(sin a * g)) for every g.
+//   k_edges       one pass over D: Eq. 1 forward differences on D_r = fl(r D) for every distinct baseline ratio,
+//                 the candidate predicate of Eq. 2 for every view (optionally restricted to proposed tiles), the
+//                 compaction of the candidate lists, the min/max reduction Eq. 3 needs, the non-finite check, the
+//                 optional E / A maps, the zeroing of O and of the tile hit flags.
+//   k_plan        per frame and view: the scan length (Eq. 3), its size class, the candidate counts, and the prefix
+//                 sums that number the scan work.
+//   k_scan_lines  one thread per scan line for lines whose sort is one or two streams through a one-slot buffer:
+//                 Eq. 4 positions and gathers, the warp W = G - V, the sort, the neighbour test of Eq. 5 and the
+//                 accumulation into O (Eq. 6); other lines are flagged for k_scan.
+//   k_scan        one warp per scan line (any line, any N): the same steps with the sort as a merge of the line's
+//                 monotone runs or a bitonic network.
+//   k_mask        M = (O > 0) (Eq. 6).
 //
 // Every floating-point operation that decides a candidate, a position, an order or a count is an explicit
 // round-to-nearest binary32 intrinsic (__fmul_rn, __fadd_rn, __fsub_rn, __fsqrt_rn) and the file is compiled with
