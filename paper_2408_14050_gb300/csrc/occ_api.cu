@@ -20,6 +20,7 @@ struct occ_ctx {
     void* d_block = nullptr;                   // one allocation for headers, statistics, tables and plan
     uint32_t* d_cand = nullptr;
     uint32_t* d_fb = nullptr;
+    uint32_t* d_brk = nullptr;
     int32_t* d_O_scratch = nullptr;            // [max_views][max_pixels], allocated on first use
     float* d_D_stage = nullptr;                // occ_detect_host staging, allocated on first use
     uint8_t* d_M_stage = nullptr;
@@ -137,7 +138,10 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.pref_cls = sc.pref + (nf * nv + 1);
     a.ptab = sc.ptab;
     a.status = sc.status;
-    a.line_ctr = sc.status + 1;   // the status region has room for the counter
+    a.line_ctr = sc.status + 1;   // the status region has room for the counters
+    a.brk = sc.brk;
+    a.brk_count = sc.status + 2;
+    a.brk_cap = (uint32_t)(sc.brk_entries < (int64_t)UINT32_MAX ? sc.brk_entries : (int64_t)UINT32_MAX);
     a.max_quads = 0;
     a.max_px = 0;
     a.hits = 0;
@@ -192,7 +196,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], st) == cudaSuccess; };
     if (cudaMemsetAsync(sc.hdr, 0, sizeof(uint32_t) * HDR_WORDS * nf, st) != cudaSuccess ||
         cudaMemsetAsync(sc.stats, 0, sizeof(unsigned long long) * 2 * sc.max_views * nf, st) != cudaSuccess ||
-        cudaMemsetAsync(sc.status, 0, 2 * sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(sc.status, 0, 3 * sizeof(uint32_t), st) != cudaSuccess ||
         (lines && cudaMemsetAsync(sc.fb, 0, sizeof(uint32_t) * fb_off, st) != cudaSuccess))
         return OCC_ERR_CUDA;
     // Size classes of the warp kernels that can receive work: with a fixed L only one.
@@ -282,6 +286,7 @@ void occ_destroy(occ_ctx* ctx)
         cudaFree(ctx->d_block);
         cudaFree(ctx->d_cand);
         cudaFree(ctx->d_fb);
+        cudaFree(ctx->d_brk);
         cudaFree(ctx->d_O_scratch);
         cudaFree(ctx->d_D_stage);
         cudaFree(ctx->d_M_stage);
@@ -325,9 +330,12 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     const size_t total = sz_hdr + sz_stats + sz_status + sz_frames + sz_plan + sz_pref + sz_tab;
     sc.cand_entries = ctx->cand_cap * max_views;
     sc.fb_entries = (ctx->cand_cap / 32 + kMaxFrames + 1) * (int64_t)max_views;
+    // One entry per candidate: the list of broken lines cannot fill up.
+    sc.brk_entries = sc.cand_entries;
     bool ok = scratch_grids(sc) == cudaSuccess && cudaMalloc(&ctx->d_block, total) == cudaSuccess &&
               cudaMalloc(&ctx->d_cand, sizeof(uint32_t) * (size_t)sc.cand_entries) == cudaSuccess &&
               cudaMalloc(&ctx->d_fb, sizeof(uint32_t) * (size_t)sc.fb_entries) == cudaSuccess &&
+              cudaMalloc(&ctx->d_brk, sizeof(uint32_t) * (size_t)sc.brk_entries) == cudaSuccess &&
               cudaMemset(ctx->d_block, 0, total) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -344,6 +352,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     sc.ptab = reinterpret_cast<int32_t*>(p);
     sc.cand = ctx->d_cand;
     sc.fb = ctx->d_fb;
+    sc.brk = ctx->d_brk;
     *out = ctx;
     return OCC_OK;
 }

@@ -102,6 +102,9 @@ struct Args {
     int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact
     uint32_t* status;             // OR of every frame's status bits
     uint32_t* line_ctr;           // work counter of the line kernel, zero at the start of a call
+    uint32_t* brk;                // work items of the lines of more than one macro-run, for the merge kernel
+    uint32_t* brk_count;          // entries written to brk, zero at the start of a call
+    uint32_t brk_cap;             // entries brk holds: at least the candidates a call can have
 };
 
 // At most kFramesPerChunk frame records travel in the parameters of one k_frames launch (under 4 KB).
@@ -143,6 +146,8 @@ struct Scratch {
     int64_t cand_entries;
     uint32_t* fb;                  // line-flag pool (words)
     int64_t fb_entries;
+    uint32_t* brk;                 // list of lines for the merge kernel (cand_entries entries)
+    int64_t brk_entries;
     int32_t max_frames, max_views;
     int32_t sms;                   // multiprocessors of the device
     int32_t lines_bps_max;         // resident blocks per SM of the line kernel

@@ -19,7 +19,6 @@
 // Every floating-point operation that decides a candidate, a position, an order or a count is an explicit
 // round-to-nearest binary32 intrinsic (__fmul_rn, __fadd_rn, __fsub_rn, __fsqrt_rn) and the file is compiled with
 // --fmad=false, so the results are bit-identical to a plain one-operation-at-a-time binary32 evaluation.
-#include <climits>
 #include <cstdint>
 
 #include "occ_internal.cuh"
@@ -486,6 +485,7 @@ struct LineSample {
 struct LineJob {
     int x, y;       // candidate
     int f, v;       // frame, view
+    int idx;        // index in the (frame, view) candidate list
     int h;          // half scan length
     int k0, k1;     // first / last k inside the image
     int ks;         // start of the second macro-run
@@ -552,7 +552,7 @@ __device__ __forceinline__ void window_init(LineWindow& W)
 
 template <bool kHits>
 __device__ __forceinline__ void window_push(LineWindow& W, const LineSample& e, int half, float zeta, float beta,
-                                            int32_t* Ov)
+                                            int32_t* Ov, int sgn = 1)
 {
     const float eb = __fadd_rn(e.v, beta);
     int eo = 0;
@@ -569,7 +569,7 @@ __device__ __forceinline__ void window_push(LineWindow& W, const LineSample& e, 
         const int ol = half == 1 ? W.o0 : (half == 2 ? W.o1 : (half == 3 ? W.o2 : W.o3));
         const int pl = half == 1 ? W.p0 : (half == 2 ? W.p1 : (half == 3 ? W.p2 : W.p3));
         if (ol) {
-            atomicAdd(Ov + pl, ol);
+            atomicAdd(Ov + pl, sgn * ol);
             if (kHits) W.hit = 1;
         }
     } else {
@@ -613,7 +613,7 @@ __device__ __forceinline__ void rot_init(RotWindow& R)
 
 template <int J, bool kHits>
 __device__ __forceinline__ void rot_push(RotWindow& R, const LineSample& e, float zeta, float beta, int32_t* Ov,
-                                         int& hit)
+                                         int& hit, int sgn = 1)
 {
     const float eb = __fadd_rn(e.v, beta);
     int eo = 0;
@@ -624,7 +624,7 @@ __device__ __forceinline__ void rot_push(RotWindow& R, const LineSample& e, floa
         R.o[i] += (close && R.b[i] < e.v) ? 1 : 0;
     }
     if (R.o[J]) {
-        atomicAdd(Ov + R.p[J], R.o[J]);
+        atomicAdd(Ov + R.p[J], sgn * R.o[J]);
         if (kHits) hit = 1;
     }
     R.w[J] = e.w;
@@ -724,229 +724,163 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
 #undef OCC_MERGE_STEP
 }
 
-// Pass 1 with the next sample's load issued before the current one is used.
-template <bool kWide>
-__device__ __forceinline__ int line_runs_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int cx, int cy, int h,
-                                           int& k0, int& k1, int& ks, int& n)
+// First and last k of a scan line inside the image.  Each coordinate of a sample is a rounding of a monotone
+// function of g, so the samples inside the image form one interval of k, which holds k = h (the candidate itself);
+// its ends are found by bisection on both sides of h.
+__device__ __forceinline__ void line_range(const FrameArg& F, const ViewArg& va, const int32_t* tab, int cx, int cy,
+                                           int h, int& k0, int& k1)
 {
-    const int nk = 2 * h + 1;
-    int runs = 0;
-    LineSample buf{0.f, 0.f, 0, 0}, last{-INFINITY, 0.f, 0, -1};
-    k0 = -1; k1 = -1; ks = -1; n = 0;
-    // Position of sample k from its table word t: pixel index and element offset in D (pixel -1 outside the image).
-    auto pos = [&](int t, int k, int& pix, int64_t& off) {
-        int px, py;
-        pix = -1;
-        off = 0;
-        if (t != kTabExact) {
-            px = cx + (int)(int16_t)(t & 0xFFFF);
-            py = cy + (t >> 16);
-        } else {
+    const int* tk = tab + (kTabHalf - h);
+    auto inside = [&](int k) -> bool {
+        const int t = tk[k];
+        if (t == kTabExact) {
             const float g = (float)(k - h);
             const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
             const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
-            if (!((rx >= 0.0f) && (rx < (float)F.W) && (ry >= 0.0f) && (ry < (float)F.H))) return;
-            px = (int)rx;
-            py = (int)ry;
+            return (rx >= 0.0f) && (rx < (float)F.W) && (ry >= 0.0f) && (ry < (float)F.H);
         }
-        if (!((unsigned)px < (unsigned)F.W && (unsigned)py < (unsigned)F.H)) return;
-        pix = py * F.W + px;
-        off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
+        const int px = cx + (int)(int16_t)(t & 0xFFFF), py = cy + (t >> 16);
+        return (unsigned)px < (unsigned)F.W && (unsigned)py < (unsigned)F.H;
     };
-    // Loads run ahead: the table word two samples ahead, D one sample ahead.
-    const int* tk = tab + (kTabHalf - h);
-    int pn;
-    int64_t on;
-    pos(tk[0], 0, pn, on);
-    float dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
-    int tnext = nk > 1 ? tk[1] : 0;
-    float gk = (float)(-h) - 1.0f;   // g = k - h as a float counter (exact: |g| < 2^24)
-    for (int k = 0; k < nk; k++) {
-        const int p = pn;
-        const float dv = dn;
-        gk += 1.0f;
-        if (k + 1 < nk) {
-            const int t = tnext;
-            if (k + 2 < nk) tnext = tk[k + 2];
-            pos(t, k + 1, pn, on);
-            dn = (pn >= 0) ? __ldg(F.D + on) : 0.0f;
+    int lo0 = 0, hi0 = h;           // k0 lies in [lo0, hi0]
+    int lo1 = h, hi1 = 2 * h;       // k1 lies in [lo1, hi1]
+    if (inside(0)) hi0 = 0;
+    if (inside(2 * h)) lo1 = 2 * h;
+    while (lo0 < hi0 || lo1 < hi1) {
+        if (lo0 < hi0) {
+            const int m = (lo0 + hi0) >> 1;
+            if (inside(m)) hi0 = m; else lo0 = m + 1;
         }
-        if (p < 0) continue;
-        LineSample s;
-        s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
-        s.w = __fsub_rn(gk, s.v);
-        s.p = p;
-        s.k = k;
-        if (k0 < 0) k0 = k;
-        k1 = k;
-        n++;
-        if (runs == 0) {
-            buf = s;
-            runs = 1;
-            continue;
-        }
-        if (later_before(s, buf)) {
-            if (later_before(s, last)) {    // s would be emitted out of order: it starts a new macro-run
-                if (++runs > 2) return 3;
-                ks = k;
-                buf = s;
-                last.w = -INFINITY;
-                last.k = -1;
-                continue;
-            }
-            last = s;
-        } else {
-            last = buf;
-            buf = s;
+        if (lo1 < hi1) {
+            const int m = (lo1 + hi1 + 1) >> 1;
+            if (inside(m)) lo1 = m; else hi1 = m - 1;
         }
     }
-    // The valid samples form one interval of k (positions are monotone in g); if not, the warp kernel reports it.
-    if (n > 0 && k1 - k0 + 1 != n) return 3;
-    return runs;
+    k0 = lo0;
+    k1 = lo1;
 }
 
-// Pass 2 for a single macro-run [k0, k1], loads one sample ahead.
-template <bool kWide, bool kHits, bool kHalf4>
-__device__ __forceinline__ bool line_counts1_p(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov,
-                                               int cx, int cy, int h, int half, int k0, int k1)
+// Pixel index and element offset in D of sample k (inside the image) from its table word t.
+template <bool kWide>
+__device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, int cx, int cy, int h, int t, int k,
+                                         int& pix, int64_t& off)
 {
-    LineWindow Wn;
-    window_init(Wn);
-    auto pos = [&](int t, int k, int& pix, int64_t& off) {
-        int px, py;
-        if (t != kTabExact) {
-            px = cx + (int)(int16_t)(t & 0xFFFF);
-            py = cy + (t >> 16);
-        } else {
-            const float g = (float)(k - h);
-            px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
-            py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
-        }
-        pix = py * F.W + px;
-        off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
-    };
-    const int* tk = tab + (kTabHalf - h);
-    auto make = [&](int k, int p, float dv) -> LineSample {
-        LineSample s;
-        s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);
-        s.w = __fsub_rn((float)(k - h), s.v);
-        s.p = p;
-        s.k = k;
-        return s;
-    };
-    int pn;
-    int64_t on;
-    pos(tk[k0], k0, pn, on);
-    float dn = __ldg(F.D + on);
-    LineSample buf = make(k0, pn, dn);
-    if (k0 + 1 <= k1) {
-        pos(tk[k0 + 1], k0 + 1, pn, on);
-        dn = __ldg(F.D + on);
-    }
-    int tnext = k0 + 2 <= k1 ? tk[k0 + 2] : 0;   // table word of the sample after the one in flight
-    if constexpr (kHalf4) {
-        // The emitted stream is min(sample k, buffer) for k = k0 + 1 .. k1, then the buffer: n samples.
-        RotWindow R;
-        rot_init(R);
-        int hit = 0;
-        int k = k0 + 1;
-        float gk = (float)(k0 + 1 - h);   // g of sample k as a float counter (exact: |g| < 2^24)
-#define OCC_ROT_STEP(J)                                                                        \
-        {                                                                                      \
-            if (k > k1 + 1) break;                                                             \
-            LineSample e;                                                                      \
-            if (k <= k1) {                                                                     \
-                const int p = pn;                                                              \
-                const float dv = dn;                                                           \
-                if (k + 1 <= k1) {                                                             \
-                    const int t = tnext;                                                       \
-                    if (k + 2 <= k1) tnext = tk[k + 2];                                        \
-                    pos(t, k + 1, pn, on);                                                     \
-                    dn = __ldg(F.D + on);                                                      \
-                }                                                                              \
-                LineSample s;                                                                  \
-                s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);                               \
-                s.w = __fsub_rn(gk, s.v);                                                      \
-                s.p = p;                                                                       \
-                s.k = k;                                                                       \
-                const bool sb = later_before(s, buf);                                          \
-                e = sb ? s : buf;                                                              \
-                if (!sb) buf = s;                                                              \
-            } else {                                                                           \
-                e = buf;                                                                       \
-            }                                                                                  \
-            rot_push<J, kHits>(R, e, a.zeta, a.beta, Ov, hit);                                 \
-            k++;                                                                               \
-            gk += 1.0f;                                                                        \
-        }
-        for (;;) {
-            OCC_ROT_STEP(0) OCC_ROT_STEP(1) OCC_ROT_STEP(2) OCC_ROT_STEP(3)
-        }
-#undef OCC_ROT_STEP
-        return rot_flush(R, Ov, hit);
+    int px, py;
+    if (t != kTabExact) {
+        px = cx + (int)(int16_t)(t & 0xFFFF);
+        py = cy + (t >> 16);
     } else {
-    for (int k = k0 + 1; k <= k1; k++) {
-        const int p = pn;
-        const float dv = dn;
-        if (k + 1 <= k1) {
-            const int t = tnext;
-            if (k + 2 <= k1) tnext = tk[k + 2];
-            pos(t, k + 1, pn, on);
-            dn = __ldg(F.D + on);
+        const float g = (float)(k - h);
+        px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
+        py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
+    }
+    pix = py * F.W + px;
+    off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
+}
+
+// One pass over a line that takes it to be a single macro-run: samples k0 .. k1 through the one-slot buffer, each
+// emitted sample tested (Eq. 5) against the N/2 emitted before it, final counts to O (Eq. 6).  Every lane of the warp
+// calls it (live = false: no line).  The emitted stream must not go backwards; where it would (the sample about to
+// be emitted precedes the last one emitted), a second macro-run starts there: the lane stops and returns that k, its
+// counts so far still in O.  Returns -1 when the line was one macro-run (hit: a non-zero count went to O).  With
+// sgn = -1 every count is negated: the same stream again, which makes the same pushes and stops at the same k, takes
+// a broken line's counts back out of O.
+//
+// The stream is padded so that every lane pushes from its first step and loads one sample ahead from the start: the
+// buffer starts with a sample of W = -inf and the first "current" sample is another (V = +inf); after k1 the
+// current sample has W = +inf, which flushes the buffer.  Samples of infinite W are never close (Eq. 5) to any
+// other, so they leave no count, and the n samples of the line take n + 2 pushes.
+template <bool kWide, bool kHits, bool kHalf4>
+__device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab,
+                                           int32_t* Ov, int cx, int cy, int h, int half, int k0, int k1, bool live,
+                                           int sgn, bool& hit)
+{
+    const float kInf = __int_as_float(0x7f800000);
+    const int* tk = tab + (kTabHalf - h);
+    RotWindow R;
+    LineWindow Wn;
+    LineSample buf;
+    float lastw, dn, gq;
+    int pn, tnext = 0, kq, left = 0, ks = -1, ht = 0;
+    int64_t on;
+    bool go = live;
+    if (live) {
+        if constexpr (kHalf4) rot_init(R); else window_init(Wn);
+        buf.w = -kInf;
+        buf.v = kInf;
+        buf.p = 0;
+        buf.k = 0;
+        lastw = -kInf;
+        pn = 0;
+        dn = kInf;
+        kq = k0 - 1;
+        gq = (float)(k0 - 1 - h);
+        tnext = tk[k0];
+        left = k1 - k0 + 3;
+    }
+    // One step: the sample in flight becomes current, the next one is loaded; the smaller of current and buffer is
+    // emitted unless that would go backwards.
+#define OCC_STREAM_STEP(PUSH)                                                                  \
+    if (go) {                                                                                  \
+        const int p = pn;                                                                      \
+        const float dv = dn;                                                                   \
+        if (kq < k1) {                                                                         \
+            const int t = tnext;                                                               \
+            if (kq + 2 <= k1) tnext = tk[kq + 2];                                              \
+            line_pos<kWide>(F, va, cx, cy, h, t, kq + 1, pn, on);                              \
+            dn = __ldg(F.D + on);                                                              \
+        } else {                                                                               \
+            dn = -kInf;                                                                        \
+        }                                                                                      \
+        LineSample s;                                                                          \
+        s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);                                       \
+        s.w = __fsub_rn(gq, s.v);                                                              \
+        s.p = p;                                                                               \
+        s.k = 0;                                                                               \
+        const bool sb = later_before(s, buf);                                                  \
+        if (sb && s.w < lastw) {                                                               \
+            go = false;                                                                        \
+            ks = kq;                                                                           \
+        } else {                                                                               \
+            const LineSample e = sb ? s : buf;                                                 \
+            if (!sb) buf = s;                                                                  \
+            PUSH;                                                                              \
+            lastw = e.w;                                                                       \
+            go = --left != 0;                                                                  \
+        }                                                                                      \
+        kq++;                                                                                  \
+        gq += 1.0f;                                                                            \
+    }
+    for (;;) {
+        if (!__any_sync(kFull, go)) break;
+        if constexpr (kHalf4) {
+            OCC_STREAM_STEP((rot_push<0, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<1, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<2, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<3, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
+        } else {
+            OCC_STREAM_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov, sgn)))
+            OCC_STREAM_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov, sgn)))
         }
-        const LineSample s = make(k, p, dv);
-        const bool sb = later_before(s, buf);
-        const LineSample e = sb ? s : buf;
-        if (!sb) buf = s;
-        window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov);
     }
-    window_push<kHits>(Wn, buf, half, a.zeta, a.beta, Ov);
-    return window_flush(Wn, Ov);
-    }
+#undef OCC_STREAM_STEP
+    if (!live || ks >= 0) return ks;
+    if constexpr (kHalf4) hit = rot_flush(R, Ov, ht);
+    else hit = window_flush(Wn, Ov);
+    return -1;
 }
 
 constexpr int kStatsSmem = 512;   // (frame, view) statistics accumulated in shared memory before going global
 
-template <bool kWide, bool kHits, bool kHalf4, bool kDyn>
-__global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_constant__ Args a)
-{
-    constexpr int kWarps = kLineThreads / 32;
-    constexpr int kQ = 64;                  // per-warp queue of jobs of each kind
-    __shared__ unsigned long long s_st[2 * kStatsSmem];
-    __shared__ LineJob s_q[kWarps][2][kQ];
-    const int nfv = a.nf * a.nv;
-    for (int i = threadIdx.x; i < 2 * kStatsSmem; i += blockDim.x) s_st[i] = 0;
-    __syncthreads();
-    const uint32_t total = a.pref_all[nfv];
-    const int half = a.N >> 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    LineJob* q1 = s_q[warp][0];
-    LineJob* q2 = s_q[warp][1];
-    int n1 = 0, n2 = 0;   // queue lengths (warp-uniform)
-
-    // kHits: some frame of the batch asks for per-tile hit flags.
-    auto mark_hit = [&](const FrameArg& F, const LineJob& jb) {
-        if (F.hits)
-            F.hits[(int64_t)jb.v * F.tiles_x * F.tiles_y + (jb.y / kTile) * F.tiles_x + jb.x / kTile] = 1;
-    };
-    auto run1 = [&](const LineJob& jb) {
-        const FrameArg& F = a.frames[jb.f];
-        const bool hit = line_counts1_p<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
-                                                       F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
-                                                       jb.k0, jb.k1);
-        if (kHits && hit) mark_hit(F, jb);
-    };
-    auto run2 = [&](const LineJob& jb) {
-        const FrameArg& F = a.frames[jb.f];
-        const bool hit = line_counts2<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
-                                                     F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
-                                                     jb.k0, jb.k1, jb.ks);
-        if (kHits && hit) mark_hit(F, jb);
-    };
-    int cur = -1;   // (frame, view) of the statistics being accumulated
+// Per-(frame, view) statistics of the lines a block completes: accumulated per thread while its lines stay in one
+// (frame, view), then in shared memory, then once per block in global memory.
+struct LineStats {
+    unsigned long long* s_st;
+    int cur = -1;
     unsigned long long acc_n = 0, acc_p = 0;
-    auto flush = [&]() {
+
+    __device__ void flush(const Args& a)
+    {
         if (cur < 0) return;
         if (cur < kStatsSmem) {
             atomicAdd(&s_st[2 * cur], acc_n);
@@ -956,83 +890,233 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
             atomicAdd(&a.frames[f].stats[2 * v], acc_n);
             atomicAdd(&a.frames[f].stats[2 * v + 1], acc_p);
         }
-    };
-
-    // Work distribution in chunks of 32 lines.  Small calls: warp w takes chunks w, w + n_warps, ... (static).
-    // Large calls (kDyn): after its first chunk a warp takes the next one from a counter, so that the lines in
-    // flight stay within a narrow window of the item order (one frame and view at a time) however far warps drift
-    // apart, and the D and O planes they touch stay in L2 for large frames and long batches.
-    const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
-    for (uint64_t chunk = (uint64_t)blockIdx.x * kWarps + warp;;) {
-        const uint64_t b0 = chunk * 32;
-        if (b0 >= total) break;
-        // Pass 1 for 32 lines, one per lane.
-        const uint64_t item = b0 + lane;
-        int runs = 0;
-        LineJob jb{0, 0, 0, 0, 0, 0, 0, 0};
-        if (item < total) {
-            const int i = item_owner(a.pref_all, nfv, (uint32_t)item);
-            const int f = i / a.nv, v = i - f * a.nv;
-            const FrameArg& F = a.frames[f];
-            const int64_t idx = (int64_t)(item - a.pref_all[i]);
-            const uint32_t cw = F.cand[(int64_t)v * F.cap + idx];
-            jb.x = (int)(cw & 0xFFFFu);
-            jb.y = (int)(cw >> 16);
-            jb.f = f;
-            jb.v = v;
-            jb.h = a.plan[i].h;
-            int n;
-            runs = line_runs_p<kWide>(a, F, a.view[v], a.ptab + (int64_t)v * kTabLen, jb.x, jb.y, jb.h, jb.k0,
-                                      jb.k1, jb.ks, n);
-            if (runs > a.line_max_runs) {
-                atomicOr(&F.fb[(int64_t)v * F.fb_words + (idx >> 5)], 1u << (idx & 31));
-            } else if (runs > 0) {
-                if (i != cur) {
-                    flush();
-                    cur = i;
-                    acc_n = acc_p = 0;
-                }
-                acc_n += (unsigned long long)n;
-                acc_p += pair_count(n, half);
-            }
-        }
-        if (runs > a.line_max_runs) runs = 0;
-        // Queue the lines by kind (warp-level compaction).
-        const unsigned m1 = __ballot_sync(kFull, runs == 1), m2 = __ballot_sync(kFull, runs == 2);
-        if (runs == 1) q1[n1 + __popc(m1 & lt)] = jb;
-        if (runs == 2) q2[n2 + __popc(m2 & lt)] = jb;
-        n1 += __popc(m1);
-        n2 += __popc(m2);
-        __syncwarp();
-        // Pass 2 for full warps of one kind.
-        if (n1 >= 32) {
-            run1(q1[n1 - 32 + lane]);
-            n1 -= 32;
-        }
-        if (n2 >= 32) {
-            run2(q2[n2 - 32 + lane]);
-            n2 -= 32;
-        }
-        __syncwarp();
-        if constexpr (kDyn) {
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(a.line_ctr, 1u);
-            chunk = nwarps + __shfl_sync(kFull, c, 0);
-        } else {
-            chunk += nwarps;
-        }
     }
-    // Drain the queues.
-    if (lane < n1) run1(q1[lane]);
-    if (lane < n2) run2(q2[lane]);
-    flush();
+    __device__ void add(const Args& a, int i, int n, int half)
+    {
+        if (i != cur) {
+            flush(a);
+            cur = i;
+            acc_n = acc_p = 0;
+        }
+        acc_n += (unsigned long long)n;
+        acc_p += pair_count(n, half);
+    }
+};
+
+__device__ __forceinline__ void stats_init(unsigned long long* s_st)
+{
+    for (int i = threadIdx.x; i < 2 * kStatsSmem; i += blockDim.x) s_st[i] = 0;
     __syncthreads();
+}
+
+__device__ __forceinline__ void stats_publish(const Args& a, const unsigned long long* s_st)
+{
+    __syncthreads();
+    const int nfv = a.nf * a.nv;
     const int ns = nfv < kStatsSmem ? nfv : kStatsSmem;
     for (int i = threadIdx.x; i < 2 * ns; i += blockDim.x)
         if (s_st[i]) {
             const int fv = i >> 1, f = fv / a.nv, v = fv - f * a.nv;
             atomicAdd(&a.frames[f].stats[2 * v + (i & 1)], s_st[i]);
         }
+}
+
+// A line's candidate, half length and k range inside the image from its work item.
+__device__ __forceinline__ LineJob line_job(const Args& a, uint32_t item)
+{
+    LineJob jb;
+    const int nfv = a.nf * a.nv;
+    const int i = item_owner(a.pref_all, nfv, item);
+    const int f = i / a.nv, v = i - f * a.nv;
+    const FrameArg& F = a.frames[f];
+    const int64_t idx = (int64_t)(item - a.pref_all[i]);
+    const uint32_t cw = F.cand[(int64_t)v * F.cap + idx];
+    jb.x = (int)(cw & 0xFFFFu);
+    jb.y = (int)(cw >> 16);
+    jb.f = f;
+    jb.v = v;
+    jb.idx = (int)idx;
+    jb.h = a.plan[i].h;
+    jb.ks = -1;
+    line_range(F, a.view[v], a.ptab + (int64_t)v * kTabLen, jb.x, jb.y, jb.h, jb.k0, jb.k1);
+    return jb;
+}
+
+__device__ __forceinline__ uint32_t* line_flag_word(const Args& a, const LineJob& jb)
+{
+    const FrameArg& F = a.frames[jb.f];
+    return &F.fb[(int64_t)jb.v * F.fb_words + (jb.idx >> 5)];
+}
+
+// kHits: some frame of the batch asks for per-tile hit flags.
+__device__ __forceinline__ void line_mark_hit(const FrameArg& F, const LineJob& jb)
+{
+    if (F.hits) F.hits[(int64_t)jb.v * F.tiles_x * F.tiles_y + (jb.y / kTile) * F.tiles_x + jb.x / kTile] = 1;
+}
+
+// The replay of a broken line's stream with the counts negated (every lane calls it; live: this lane has a line);
+// returns the k where the second macro-run starts.  Kept out of line: an inlined copy of the stream next to the merge
+// costs the merge kernel registers.
+template <bool kWide, bool kHits, bool kHalf4>
+__device__ __noinline__ int line_undo(const Args& a, const LineJob& jb, bool live)
+{
+    const FrameArg& F = a.frames[jb.f];
+    bool hit = false;
+    return line_stream<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                                             F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, a.N >> 1, jb.k0, jb.k1,
+                                             live, -1, hit);
+}
+
+// Next chunk of 32 work items of a warp.  Small calls: warp w takes chunks w, w + n_warps, ... (static).  Large calls
+// (kDyn): after its first chunk a warp takes the next one from a counter, so that the lines in flight stay within a
+// narrow window of the item order (one frame and view at a time) however far warps drift apart, and the D and O
+// planes they touch stay in L2 for large frames and long batches.
+template <bool kDyn>
+__device__ __forceinline__ uint64_t next_chunk(uint64_t chunk, uint64_t nwarps, uint32_t* ctr, int lane)
+{
+    if constexpr (kDyn) {
+        uint32_t c = 0;
+        if (lane == 0) c = atomicAdd(ctr, 1u);
+        return nwarps + __shfl_sync(kFull, c, 0);
+    } else {
+        return chunk + nwarps;
+    }
+}
+
+template <bool kWide, bool kHits, bool kHalf4, bool kDyn>
+__global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_constant__ Args a)
+{
+    constexpr int kWarps = kLineThreads / 32;
+    __shared__ unsigned long long s_st[2 * kStatsSmem];
+    stats_init(s_st);
+    const uint32_t total = a.pref_all[a.nf * a.nv];
+    const int half = a.N >> 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    LineStats stats{s_st};
+    const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+    for (uint64_t chunk = (uint64_t)blockIdx.x * kWarps + warp;;) {
+        const uint64_t b0 = chunk * 32;
+        if (b0 >= total) break;
+        // One line per lane.
+        const uint64_t item = b0 + lane;
+        const bool live = item < total;
+        LineJob jb{0, 0, 0, 0, 0, 0, 0, 0, -1};
+        if (live) jb = line_job(a, (uint32_t)item);
+        const FrameArg& F = a.frames[jb.f];
+        bool hit = false;
+        const int ks = line_stream<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                                                         F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
+                                                         jb.k0, jb.k1, live, 1, hit);
+        if (live && ks < 0) {
+            stats.add(a, jb.f * a.nv + jb.v, jb.k1 - jb.k0 + 1, half);
+            if (kHits && hit) line_mark_hit(F, jb);
+        }
+        // More than one macro-run: the line goes to the merge kernel's list, its counts so far still in O.  The list
+        // has an entry for every candidate the call can hold, so it cannot fill up; the check only guards the store.
+        const bool broken = live && ks >= 0;
+        const unsigned mb = __ballot_sync(kFull, broken);
+        if (mb) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(a.brk_count, (uint32_t)__popc(mb));
+            base = __shfl_sync(kFull, base, 0);
+            const uint32_t pos = base + (uint32_t)__popc(mb & lt);
+            if (broken) {
+                if (pos < a.brk_cap) a.brk[pos] = (uint32_t)item;
+                else atomicOr(a.status, ST_INTERNAL);
+            }
+        }
+        chunk = next_chunk<kDyn>(chunk, nwarps, a.line_ctr, lane);
+    }
+    stats.flush(a);
+    stats_publish(a, s_st);
+}
+
+// Whether samples ks .. k1 of a line (inside the image) form one macro-run, that is, whether a line whose second
+// macro-run starts at ks has exactly two.  The same test as the stream's: the one-slot buffer's output must not go
+// backwards.  Loads run one sample ahead.
+template <bool kWide>
+__device__ __forceinline__ bool line_one_run_from(const FrameArg& F, const ViewArg& va, const int32_t* tab, int cx,
+                                                  int cy, int h, int ks, int k1)
+{
+    const int* tk = tab + (kTabHalf - h);
+    const float r = va.r;
+    int pix;
+    int64_t on;
+    line_pos<kWide>(F, va, cx, cy, h, tk[ks], ks, pix, on);
+    float dv = __ldg(F.D + on);
+    float bufw = __fsub_rn((float)(ks - h), (r == 1.0f) ? dv : __fmul_rn(r, dv));
+    float lastw = -__int_as_float(0x7f800000);
+    int tnext = ks + 1 <= k1 ? tk[ks + 1] : 0;
+    if (ks < k1) {
+        line_pos<kWide>(F, va, cx, cy, h, tnext, ks + 1, pix, on);
+        dv = __ldg(F.D + on);
+        if (ks + 2 <= k1) tnext = tk[ks + 2];
+    }
+    float g = (float)(ks + 1 - h);
+    for (int k = ks + 1; k <= k1; k++) {
+        const float d = dv;
+        if (k < k1) {
+            line_pos<kWide>(F, va, cx, cy, h, tnext, k + 1, pix, on);
+            dv = __ldg(F.D + on);
+            if (k + 2 <= k1) tnext = tk[k + 2];
+        }
+        const float w = __fsub_rn(g, (r == 1.0f) ? d : __fmul_rn(r, d));
+        g += 1.0f;
+        if (w < bufw) {
+            if (w < lastw) return false;
+            lastw = w;
+        } else {
+            lastw = bufw;
+            bufw = w;
+        }
+    }
+    return true;
+}
+
+// k_merge_lines: the lines k_scan_lines listed (more than one macro-run), one thread per line, 32 consecutive list
+// entries per warp.  First the line's stream again with the counts negated, which takes its partial counts back out
+// of O and finds ks, the start of its second macro-run.  Then, when the line kernels keep two-macro-run lines
+// (line_max_runs = 2), a line whose samples from ks on are one macro-run has exactly two and goes through the
+// two-buffer merge (Eq. 5 and Eq. 6 as in the stream); every other line is flagged for the warp kernel.
+template <bool kWide, bool kHits, bool kHalf4>
+__global__ void __launch_bounds__(kLineThreads, 3) k_merge_lines(const __grid_constant__ Args a)
+{
+    constexpr int kWarps = kLineThreads / 32;
+    __shared__ unsigned long long s_st[2 * kStatsSmem];
+    stats_init(s_st);
+    const uint32_t n = min(*a.brk_count, a.brk_cap);
+    const int half = a.N >> 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    LineStats stats{s_st};
+    const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
+    for (uint64_t b = (uint64_t)blockIdx.x * kWarps + warp; b * 32 < n; b += nwarps) {
+        const uint64_t e = b * 32 + lane;
+        const bool valid = e < n;
+        LineJob jb{0, 0, 0, 0, 0, 0, 0, 0, -1};
+        if (valid) jb = line_job(a, a.brk[e]);
+        jb.ks = line_undo<kWide, kHits, kHalf4>(a, jb, valid);
+        bool two = false;
+        if (valid) {
+            if (a.line_max_runs >= 2 && jb.ks >= 0)
+                two = line_one_run_from<kWide>(a.frames[jb.f], a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen, jb.x,
+                                               jb.y, jb.h, jb.ks, jb.k1);
+            if (!two) atomicOr(line_flag_word(a, jb), 1u << (jb.idx & 31));
+        }
+        // The lanes leave the run test at different times: the merge starts together.
+        __syncwarp();
+        if (two) {
+            const FrameArg& F = a.frames[jb.f];
+            const bool hit = line_counts2<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                                                                F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h,
+                                                                half, jb.k0, jb.k1, jb.ks);
+            if (kHits && hit) line_mark_hit(F, jb);
+            stats.add(a, jb.f * a.nv + jb.v, jb.k1 - jb.k0 + 1, half);
+        }
+        __syncwarp();
+    }
+    stats.flush(a);
+    stats_publish(a, s_st);
 }
 
 // ------------------------------------------------------------------------------------------------------------------
@@ -1493,12 +1577,15 @@ cudaError_t launch_plan(const Args& a, cudaStream_t st)
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st)
 {
     // N = 8 (the default) takes the rotating window; wide frames and hit flags are the rarer variants; large calls
-    // take their chunks from a counter.
+    // take their chunks from a counter.  The merge kernel follows: it takes the broken lines' counts back and merges
+    // those of two macro-runs.
     const bool h4 = a.N == 8;
 #define OCC_LINES(W, HI, DY)                                                                       \
     do {                                                                                           \
         if (h4) k_scan_lines<W, HI, true, DY><<<grid, kLineThreads, 0, st>>>(a);                   \
         else k_scan_lines<W, HI, false, DY><<<grid, kLineThreads, 0, st>>>(a);                     \
+        if (h4) k_merge_lines<W, HI, true><<<grid, kLineThreads, 0, st>>>(a);                      \
+        else k_merge_lines<W, HI, false><<<grid, kLineThreads, 0, st>>>(a);                        \
     } while (0)
     if (a.line_dyn) {
         if (!wide && !a.hits) OCC_LINES(false, false, true);

@@ -15,8 +15,9 @@ namespace {
 
 // The scratch every call shares, laid out as the one-frame scratch of a context: the frame header, the per-view
 // statistics, the batch status word, the frame record, the plan and its prefix sums, the scan-line position tables,
-// the bit per candidate marking lines left to the warp kernels, then the candidate lists ([n_views][H*W] entries of
-// the current call).  One array per device that loads the library; it lives until the process exits.
+// the bit per candidate marking lines left to the warp kernels, the list of lines for the merge kernel, then the
+// candidate lists ([n_views][H*W] entries of the current call).  One array per device that loads the library; it
+// lives until the process exits.
 constexpr size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffHdr = 0;
 constexpr size_t kOffStats = kOffHdr + align_up(sizeof(uint32_t) * HDR_WORDS);
@@ -27,7 +28,9 @@ constexpr size_t kOffPref = kOffPlan + align_up(sizeof(PlanEntry) * OCC_MAX_VIEW
 constexpr size_t kOffTab = kOffPref + align_up(sizeof(uint32_t) * (1 + kNumClasses) * (OCC_MAX_VIEWS + 1));
 constexpr size_t kFlagWords = OCC_NOALLOC_MAX_PIXEL_VIEWS / 32 + OCC_MAX_VIEWS;
 constexpr size_t kOffFlags = kOffTab + align_up(sizeof(int32_t) * kTabLen * OCC_MAX_VIEWS);
-constexpr size_t kOffCand = kOffFlags + align_up(sizeof(uint32_t) * kFlagWords);
+constexpr size_t kBrkEntries = OCC_NOALLOC_MAX_PIXEL_VIEWS;
+constexpr size_t kOffBrk = kOffFlags + align_up(sizeof(uint32_t) * kFlagWords);
+constexpr size_t kOffCand = kOffBrk + align_up(sizeof(uint32_t) * kBrkEntries);
 constexpr size_t kScratchBytes = kOffCand + sizeof(uint32_t) * (size_t)OCC_NOALLOC_MAX_PIXEL_VIEWS;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
@@ -65,6 +68,8 @@ void setup_device(DeviceSetup& s)
     sc.ptab = reinterpret_cast<int32_t*>(p + kOffTab);
     sc.fb = reinterpret_cast<uint32_t*>(p + kOffFlags);
     sc.fb_entries = (int64_t)kFlagWords;
+    sc.brk = reinterpret_cast<uint32_t*>(p + kOffBrk);
+    sc.brk_entries = (int64_t)kBrkEntries;
     sc.cand = reinterpret_cast<uint32_t*>(p + kOffCand);
     sc.cand_entries = OCC_NOALLOC_MAX_PIXEL_VIEWS;
     sc.max_frames = 1;
