@@ -9,9 +9,11 @@
 //                 optional E / A maps, the zeroing of O and of the tile hit flags.
 //   k_plan        per frame and view: the scan length (Eq. 3), its size class, the candidate counts, and the prefix
 //                 sums that number the scan work.
-//   k_scan_lines  one thread per scan line for lines whose sort is one or two streams through a one-slot buffer:
-//                 Eq. 4 positions and gathers, the warp W = G - V, the sort, the neighbour test of Eq. 5 and the
-//                 accumulation into O (Eq. 6); other lines are flagged for k_scan.
+//   k_scan_lines  one thread per scan line, every line once as one stream through a one-slot buffer: Eq. 4
+//                 positions and gathers, the warp W = G - V, the sort, the neighbour test of Eq. 5 and the
+//                 accumulation into O (Eq. 6); a line that turns out to need more lists itself for k_merge_lines.
+//   k_merge_lines one thread per listed line: the stream again with negated counts (which takes its partial counts
+//                 back), then the two-buffer merge for lines of two macro-runs; longer lines are flagged for k_scan.
 //   k_scan        one warp per scan line (any line, any N): the same steps with the sort as a merge of the line's
 //                 monotone runs or a bitonic network.
 //   k_mask        M = (O > 0) (Eq. 6).
@@ -459,21 +461,23 @@ __global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Args a)
 }
 
 // ------------------------------------------------------------------------------------------------------------------
-// k_scan_lines: Eq. 4 - Eq. 6 with one thread per candidate, for N <= 2 * kLineMaxHalf.
+// k_scan_lines, k_merge_lines: Eq. 4 - Eq. 6 with one thread per candidate, for N <= 2 * kLineMaxHalf.
 //
 // A one-slot buffer that always emits the smaller of the buffered and the arriving sample turns a sequence into
 // sorted order exactly when no sample has to move back by more than one place -- the usual effect of noise, which
 // lowers a W just below its predecessor's.  A scan line that crosses an edge breaks into a few such stretches
 // ("macro-runs"): where a whole run of foreground samples falls behind the background, the buffer's output would go
-// backwards, and a new macro-run starts there.
-//   Pass 1 (every candidate of a batch): positions, gather of V, W = g - V (Eq. 4 and the warp) for every k; the
-//     range of samples inside the image and the start of the second macro-run.  Lines of more than two macro-runs
-//     are flagged for the warp scan kernel.
-//   Pass 2, single macro-run lines, then two-macro-run lines (compacted, so that each warp runs one kind): the
-//     samples again through one-slot buffers (two buffers merged by (W, k) for two macro-runs), which gives the
-//     sorted order of the line.  Every emitted sample is tested (Eq. 5) against the N/2 samples emitted just before
-//     it, kept in registers with their running counts, each pair once for both of its ends; a sample whose N/2
-//     successors have all been emitted is final and its count goes to O (Eq. 6).
+// backwards, and a new macro-run starts there.  About three lines in four are one macro-run.
+//   k_scan_lines (every candidate of a batch): the k range inside the image by bisection, then one pass that takes
+//     the line to be one macro-run: positions, gather of V, W = g - V (Eq. 4 and the warp), the one-slot buffer,
+//     and for every emitted sample the test (Eq. 5) against the N/2 samples emitted just before it, kept in registers
+//     with their running counts, each pair once for both of its ends; a sample whose N/2 successors have all been
+//     emitted is final and its count goes to O (Eq. 6).  A line whose output would go backwards stops there and is
+//     listed.
+//     The lane then looks for a third macro-run in the rest of the line, without counting, in the steps it would
+//     otherwise wait for the rest of its warp; lines of more than two macro-runs are flagged for the warp kernel.
+//   k_merge_lines (listed lines): the same stream with negated counts up to the same point takes the partial counts
+//     back; a line of two macro-runs goes through two one-slot buffers merged by (W, k).
 
 constexpr int kLineThreads = 256;
 
@@ -645,7 +649,7 @@ __device__ __forceinline__ bool rot_flush(const RotWindow& R, int32_t* Ov, int h
     return hit != 0;
 }
 
-// Pass 2 for two macro-runs [k0, ks - 1] and [ks, k1], each read through its own one-slot buffer; the merge emits
+// A line of two macro-runs [k0, ks - 1] and [ks, k1], each read through its own one-slot buffer; the merge emits
 // the smaller head, and the chosen run reads at most one sample per step.
 template <bool kWide, bool kHits, bool kHalf4>
 __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab, int32_t* Ov, int cx,
@@ -781,10 +785,11 @@ __device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, i
 // One pass over a line that takes it to be a single macro-run: samples k0 .. k1 through the one-slot buffer, each
 // emitted sample tested (Eq. 5) against the N/2 emitted before it, final counts to O (Eq. 6).  Every lane of the warp
 // calls it (live = false: no line).  The emitted stream must not go backwards; where it would (the sample about to
-// be emitted precedes the last one emitted), a second macro-run starts there: the lane stops and returns that k, its
-// counts so far still in O.  Returns -1 when the line was one macro-run (hit: a non-zero count went to O).  With
-// sgn = -1 every count is negated: the same stream again, which makes the same pushes and stops at the same k, takes
-// a broken line's counts back out of O.
+// be emitted precedes the last one emitted), a second macro-run starts there, and the function returns that k with
+// the line's counts so far still in O.  Until the rest of the warp is done the lane goes on through the remaining
+// samples without counting (zeta < 0: no pair is close, Eq. 5) to see whether a third macro-run starts (more).
+// Returns -1 when the line was one macro-run (hit: a non-zero count went to O).  With sgn = -1 every count is
+// negated and the stream stops at the first break: the same pushes again take a broken line's counts back out of O.
 //
 // The stream is padded so that every lane pushes from its first step and loads one sample ahead from the start: the
 // buffer starts with a sample of W = -inf and the first "current" sample is another (V = +inf); after k1 the
@@ -793,7 +798,7 @@ __device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, i
 template <bool kWide, bool kHits, bool kHalf4>
 __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, const ViewArg& va, const int32_t* tab,
                                            int32_t* Ov, int cx, int cy, int h, int half, int k0, int k1, bool live,
-                                           int sgn, bool& hit)
+                                           int sgn, bool& hit, bool& more)
 {
     const float kInf = __int_as_float(0x7f800000);
     const int* tk = tab + (kTabHalf - h);
@@ -803,7 +808,9 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
     float lastw, dn, gq;
     int pn, tnext = 0, kq, left = 0, ks = -1, ht = 0;
     int64_t on;
-    bool go = live;
+    bool go = live, dry = false;
+    float zl = a.zeta;   // zeta of the pair test (Eq. 5); -1 once the lane only looks for a further macro-run
+    more = false;
     if (live) {
         if constexpr (kHalf4) rot_init(R); else window_init(Wn);
         buf.w = -kInf;
@@ -839,8 +846,22 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
         s.k = 0;                                                                               \
         const bool sb = later_before(s, buf);                                                  \
         if (sb && s.w < lastw) {                                                               \
-            go = false;                                                                        \
-            ks = kq;                                                                           \
+            if (dry) {                                                                         \
+                go = false;                                                                    \
+                more = true;                                                                   \
+            } else {                                                                           \
+                ks = kq;                                                                       \
+                if (sgn > 0) {                                                                 \
+                    dry = true;                                                                \
+                    zl = -1.0f;                                                                \
+                    if constexpr (kHalf4) { R.o[0] = R.o[1] = R.o[2] = R.o[3] = 0; }           \
+                    else { Wn.o0 = Wn.o1 = Wn.o2 = Wn.o3 = 0; }                                \
+                    buf = s;                                                                   \
+                    lastw = -kInf;                                                             \
+                } else {                                                                       \
+                    go = false;                                                                \
+                }                                                                              \
+            }                                                                                  \
         } else {                                                                               \
             const LineSample e = sb ? s : buf;                                                 \
             if (!sb) buf = s;                                                                  \
@@ -854,13 +875,13 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
     for (;;) {
         if (!__any_sync(kFull, go)) break;
         if constexpr (kHalf4) {
-            OCC_STREAM_STEP((rot_push<0, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
-            OCC_STREAM_STEP((rot_push<1, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
-            OCC_STREAM_STEP((rot_push<2, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
-            OCC_STREAM_STEP((rot_push<3, kHits>(R, e, a.zeta, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<0, kHits>(R, e, zl, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<1, kHits>(R, e, zl, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<2, kHits>(R, e, zl, a.beta, Ov, ht, sgn)))
+            OCC_STREAM_STEP((rot_push<3, kHits>(R, e, zl, a.beta, Ov, ht, sgn)))
         } else {
-            OCC_STREAM_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov, sgn)))
-            OCC_STREAM_STEP((window_push<kHits>(Wn, e, half, a.zeta, a.beta, Ov, sgn)))
+            OCC_STREAM_STEP((window_push<kHits>(Wn, e, half, zl, a.beta, Ov, sgn)))
+            OCC_STREAM_STEP((window_push<kHits>(Wn, e, half, zl, a.beta, Ov, sgn)))
         }
     }
 #undef OCC_STREAM_STEP
@@ -961,10 +982,10 @@ template <bool kWide, bool kHits, bool kHalf4>
 __device__ __noinline__ int line_undo(const Args& a, const LineJob& jb, bool live)
 {
     const FrameArg& F = a.frames[jb.f];
-    bool hit = false;
+    bool hit = false, more = false;
     return line_stream<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
                                              F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, a.N >> 1, jb.k0, jb.k1,
-                                             live, -1, hit);
+                                             live, -1, hit, more);
 }
 
 // Next chunk of 32 work items of a warp.  Small calls: warp w takes chunks w, w + n_warps, ... (static).  Large calls
@@ -1004,17 +1025,19 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
         LineJob jb{0, 0, 0, 0, 0, 0, 0, 0, -1};
         if (live) jb = line_job(a, (uint32_t)item);
         const FrameArg& F = a.frames[jb.f];
-        bool hit = false;
+        bool hit = false, more = false;
         const int ks = line_stream<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
                                                          F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h, half,
-                                                         jb.k0, jb.k1, live, 1, hit);
+                                                         jb.k0, jb.k1, live, 1, hit, more);
         if (live && ks < 0) {
             stats.add(a, jb.f * a.nv + jb.v, jb.k1 - jb.k0 + 1, half);
             if (kHits && hit) line_mark_hit(F, jb);
         }
-        // More than one macro-run: the line goes to the merge kernel's list, its counts so far still in O.  The list
-        // has an entry for every candidate the call can hold, so it cannot fill up; the check only guards the store.
+        // More than one macro-run: the line goes to the merge kernel's list, its counts so far still in O; more than
+        // two: it is also flagged for the warp kernel now.  The list has an entry for every candidate the call can
+        // hold, so it cannot fill up; the check only guards the store.
         const bool broken = live && ks >= 0;
+        if (broken && more) atomicOr(line_flag_word(a, jb), 1u << (jb.idx & 31));
         const unsigned mb = __ballot_sync(kFull, broken);
         if (mb) {
             uint32_t base = 0;
@@ -1032,53 +1055,11 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
     stats_publish(a, s_st);
 }
 
-// Whether samples ks .. k1 of a line (inside the image) form one macro-run, that is, whether a line whose second
-// macro-run starts at ks has exactly two.  The same test as the stream's: the one-slot buffer's output must not go
-// backwards.  Loads run one sample ahead.
-template <bool kWide>
-__device__ __forceinline__ bool line_one_run_from(const FrameArg& F, const ViewArg& va, const int32_t* tab, int cx,
-                                                  int cy, int h, int ks, int k1)
-{
-    const int* tk = tab + (kTabHalf - h);
-    const float r = va.r;
-    int pix;
-    int64_t on;
-    line_pos<kWide>(F, va, cx, cy, h, tk[ks], ks, pix, on);
-    float dv = __ldg(F.D + on);
-    float bufw = __fsub_rn((float)(ks - h), (r == 1.0f) ? dv : __fmul_rn(r, dv));
-    float lastw = -__int_as_float(0x7f800000);
-    int tnext = ks + 1 <= k1 ? tk[ks + 1] : 0;
-    if (ks < k1) {
-        line_pos<kWide>(F, va, cx, cy, h, tnext, ks + 1, pix, on);
-        dv = __ldg(F.D + on);
-        if (ks + 2 <= k1) tnext = tk[ks + 2];
-    }
-    float g = (float)(ks + 1 - h);
-    for (int k = ks + 1; k <= k1; k++) {
-        const float d = dv;
-        if (k < k1) {
-            line_pos<kWide>(F, va, cx, cy, h, tnext, k + 1, pix, on);
-            dv = __ldg(F.D + on);
-            if (k + 2 <= k1) tnext = tk[k + 2];
-        }
-        const float w = __fsub_rn(g, (r == 1.0f) ? d : __fmul_rn(r, d));
-        g += 1.0f;
-        if (w < bufw) {
-            if (w < lastw) return false;
-            lastw = w;
-        } else {
-            lastw = bufw;
-            bufw = w;
-        }
-    }
-    return true;
-}
-
 // k_merge_lines: the lines k_scan_lines listed (more than one macro-run), one thread per line, 32 consecutive list
 // entries per warp.  First the line's stream again with the counts negated, which takes its partial counts back out
 // of O and finds ks, the start of its second macro-run.  Then, when the line kernels keep two-macro-run lines
-// (line_max_runs = 2), a line whose samples from ks on are one macro-run has exactly two and goes through the
-// two-buffer merge (Eq. 5 and Eq. 6 as in the stream); every other line is flagged for the warp kernel.
+// (line_max_runs = 2), a line the line kernel did not flag (exactly two macro-runs) goes through the two-buffer merge
+// (Eq. 5 and Eq. 6 as in the stream); every other line is left flagged for the warp kernel.
 template <bool kWide, bool kHits, bool kHalf4>
 __global__ void __launch_bounds__(kLineThreads, 3) k_merge_lines(const __grid_constant__ Args a)
 {
@@ -1098,12 +1079,13 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_merge_lines(const __grid_co
         jb.ks = line_undo<kWide, kHits, kHalf4>(a, jb, valid);
         bool two = false;
         if (valid) {
-            if (a.line_max_runs >= 2 && jb.ks >= 0)
-                two = line_one_run_from<kWide>(a.frames[jb.f], a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen, jb.x,
-                                               jb.y, jb.h, jb.ks, jb.k1);
-            if (!two) atomicOr(line_flag_word(a, jb), 1u << (jb.idx & 31));
+            // Lines of more than two macro-runs were flagged by the line kernel.
+            uint32_t* fw = line_flag_word(a, jb);
+            const uint32_t bit = 1u << (jb.idx & 31);
+            two = a.line_max_runs >= 2 && jb.ks >= 0 && !(*fw & bit);
+            if (!two) atomicOr(fw, bit);
         }
-        // The lanes leave the run test at different times: the merge starts together.
+        // The lanes leave the replay at different times: the merge starts together.
         __syncwarp();
         if (two) {
             const FrameArg& F = a.frames[jb.f];
