@@ -143,7 +143,7 @@ LAUNCHES_PER_DETECT = 10
 # DRAM bytes (read + write) per detect call of the scan stage (all its launches) from the ncu capture summarised in
 # profiles/, valid only for the kernel code it was taken on (sha256 prefix of csrc/occ_kernels.cu without comments
 # and blank space); reported as null otherwise.
-MEASURED_TRAFFIC = {"scan": {"bytes": 83853696, "kernels_sha": "a2e1f3f12a1e8a8d"}}
+MEASURED_TRAFFIC = {"scan": {"bytes": 112663211, "kernels_sha": "8b2112872e9746c6"}}
 
 
 def code_sha(src: str) -> str:
