@@ -833,7 +833,7 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
         const float dv = dn;                                                                   \
         if (kq < k1) {                                                                         \
             const int t = tnext;                                                               \
-            if (kq + 2 <= k1) tnext = tk[kq + 2];                                              \
+            tnext = tk[min(kq + 2, k1)];                                                       \
             line_pos<kWide>(F, va, cx, cy, h, t, kq + 1, pn, on);                              \
             dn = __ldg(F.D + on);                                                              \
         } else {                                                                               \

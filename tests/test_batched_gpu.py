@@ -63,6 +63,24 @@ def test_batch_of_mixed_sizes_matches_single_frame_calls(ctx):
         assert torch.equal(O, O1) and torch.equal(M, M1)
 
 
+def test_large_batch_takes_chunks_from_a_counter(ctx):
+    # Above 64 Mi pixel-views per call the line kernel hands out its chunks from a counter (a kernel variant of its
+    # own); the results are those of the single-frame calls, and of the oracle.
+    wl = scenes.mixed_batch(n_frames=5, sizes=[(1080, 1920)])
+    views = wl.views
+    assert sum(f.size for f in wl.frames) * len(views) > 64 * 1024 * 1024
+    Ds = [torch.from_numpy(f).cuda() for f in wl.frames]
+    Ms, Os = occ.occ_detect_batched(ctx, Ds, views)
+    assert occ.occ_get_status(ctx) == occ.OCC_OK
+    for D, M, O in zip(Ds, Ms, Os):
+        M1, O1 = occ.occ_detect(ctx, D, views)
+        assert torch.equal(O, O1) and torch.equal(M, M1)
+    po = oracle.default_params(gamma=1.0, zeta=2.0, beta=0.5, L=0, N=8)
+    for v, (a, r) in enumerate(views):
+        Oo, Mo, _ = oracle.detect_view(wl.frames[0], a, r, po)
+        assert np.array_equal(Os[0][v].cpu().numpy(), Oo) and np.array_equal(Ms[0][v].cpu().numpy(), Mo)
+
+
 def test_batch_captured_in_a_cuda_graph(ctx):
     views = scenes.views_3x3()
     first = uneven_frames(seed=1)

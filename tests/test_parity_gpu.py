@@ -144,11 +144,26 @@ def test_row_pitch(ctx, pad):
     assert_exact(ctx, D, [(0.0, 1.0), (45.0, 1.4142135), (250.0, 1.0)], dict(L=30), pitch_pad=pad)
 
 
-@pytest.mark.parametrize("kw", [dict(N=2), dict(N=4), dict(N=16), dict(N=64), dict(zeta=0.75), dict(zeta=3.5),
+@pytest.mark.parametrize("kw", [dict(N=2), dict(N=4), dict(N=6), dict(N=16), dict(N=64), dict(zeta=0.75), dict(zeta=3.5),
                                 dict(beta=0.0), dict(beta=2.0), dict(gamma=0.25), dict(gamma=3.0)])
 def test_parameters_exact(ctx, kw):
     D = scenes.make_scene(scenes.SPEC_STEREO, scenes.seed_of(1, 5))[:96, :160].copy()
     assert_exact(ctx, D, [(0.0, 1.0), (45.0, 1.4142135), (180.0, 1.0), (300.0, 2.0)], kw)
+
+
+@pytest.mark.parametrize("runs", [0, 1, 2])
+@pytest.mark.parametrize("N", [4, 8])
+def test_scan_work_mappings_exact(ctx, runs, N):
+    # A noisy map whose scan lines are one, two and more macro-runs, under each mapping of the scan work: every line
+    # on the warp kernel (0); the line kernel keeping lines of one macro-run (1), and of two as well (2).  The line
+    # kernel streams every line, takes broken lines' counts back out of O and hands them on; O, M and the work counts
+    # must not change.
+    D = noisy_map(120, 200, seed=11)
+    occ.occ_set_tuning(ctx, {"line_max_runs": runs, "line_blocks_per_sm": 1, "warp_lines_per_block": 8})
+    try:
+        assert_exact(ctx, D, [(0.0, 1.0), (45.0, 1.4142135), (160.0, 1.0), (270.0, 1.0)], dict(N=N))
+    finally:
+        occ.occ_set_tuning(ctx, None)
 
 
 @pytest.mark.parametrize("L", [1, 2, 254, 255, 256, 600, 1022, 1023, 2000, 4094])
