@@ -143,7 +143,7 @@ LAUNCHES_PER_DETECT = 10
 # DRAM bytes (read + write) per detect call of the scan stage (all its launches) from the ncu capture summarised in
 # profiles/, valid only for the kernel code it was taken on (sha256 prefix of csrc/occ_kernels.cu without comments
 # and blank space); reported as null otherwise.
-MEASURED_TRAFFIC = {"scan": {"bytes": 112663211, "kernels_sha": "8b2112872e9746c6"}}
+MEASURED_TRAFFIC = {"scan": {"bytes": 112777813, "kernels_sha": "7e6ba75de617e3ac"}}
 
 
 def code_sha(src: str) -> str:
@@ -252,11 +252,13 @@ def run_ours(args):
     value = args.steps * world * units_per_step / t_max / 1e6
     ms_per_step = t_max / args.steps * 1e3
 
-    # Dominant kernel and its roofline.  The scan of Eq. 4-5 runs as the line-per-thread kernel plus the warp
-    # kernels that take the lines it leaves; the samples and pair tests of a view are counted over both, so the
-    # roofline is taken over the scan stage as a whole (the sum of those launches' times).
+    # Dominant kernel and its roofline.  The scan of Eq. 4-5 runs as the line-per-thread kernels plus the warp
+    # kernels that take the lines they leave, the warp kernels beside the merge kernel on a second stream; the
+    # samples and pair tests of a view are counted over all of them, so the roofline is taken over the scan stage as
+    # a whole: the step's time less the stages before and after it (the warp kernels' own stage times overlap the
+    # line stage's).
     mean_stage = {k: statistics.fmean(s[k] for s in stage_ms) for k in stage_ms[0]}
-    scan_ms = sum(v for k, v in mean_stage.items() if k.startswith("scan"))
+    scan_ms = t_dev / args.steps * 1e3 - mean_stage["candidates"] - mean_stage["mask"]
     groups = {"scan": scan_ms, **{k: v for k, v in mean_stage.items() if not k.startswith("scan")}}
     dom = max(groups, key=groups.get)
     hbm_peak, peak_src = peaks()

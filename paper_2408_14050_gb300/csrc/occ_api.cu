@@ -29,7 +29,9 @@ struct occ_ctx {
     cudaStream_t last_stream = nullptr;
     bool profiling = false;
     bool profiled_call = false;
-    cudaEvent_t ev[OCC_NUM_STAGES + 1] = {};
+    bool forked_call = false;                  // its warp kernels ran on the side stream
+    cudaEvent_t ev[OCC_NUM_STAGES + 2] = {};   // stage boundaries, then the start of the side stream
+    SideStream side{};
 };
 
 namespace {
@@ -125,7 +127,8 @@ cudaError_t scratch_grids(Scratch& sc)
     return cudaSuccess;
 }
 
-int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev)
+int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev,
+               const SideStream* side, bool* forked)
 {
     const int nv = a.nv;
     const bool lines = (a.N / 2) <= kLineMaxHalf && sc.tuning.line_max_runs > 0;
@@ -209,14 +212,30 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
         launch_plan(a, st) != cudaSuccess || !mark(1))
         return OCC_ERR_CUDA;
-    if (lines && launch_scan_lines(a, sc.sms * sc.tuning.line_blocks_per_sm, wide, st) != cudaSuccess)
-        return OCC_ERR_CUDA;
+    const int lgrid = sc.sms * sc.tuning.line_blocks_per_sm;
+    if (lines && launch_scan_lines(a, lgrid, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
+    // When the line kernels keep lines of two macro-runs, k_scan_lines has flagged every line the warp kernels take,
+    // and the merge kernel and the warp kernels only add to O and the statistics: in calls below the size where the
+    // line kernel takes its chunks from a counter, the merge kernel's few lines per warp leave it latency-bound, and
+    // the warp kernels run beside it on the side stream.  Larger calls keep every multiprocessor busy on their own.
+    const bool fork = side && side->st && lines && a.line_max_runs >= 2 && !a.line_dyn;
+    if (forked) *forked = fork;
+    cudaStream_t wst = st;
+    if (fork) {
+        if (cudaEventRecord(side->fork, st) != cudaSuccess || cudaStreamWaitEvent(side->st, side->fork, 0) != cudaSuccess ||
+            (ev && cudaEventRecord(ev[OCC_NUM_STAGES + 1], side->st) != cudaSuccess))
+            return OCC_ERR_CUDA;
+        wst = side->st;
+    }
+    if (lines && launch_merge_lines(a, lgrid, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
     if (!mark(2)) return OCC_ERR_CUDA;
     for (int c = 0; c < kNumClasses; c++) {
         const int id = (c == 0 && sc.tuning.warp_lines_per_block == 4) ? kNumClasses : c;
-        if (run_cls[c] && launch_scan(a, id, sc.sms * sc.scan_bps[id], st) != cudaSuccess) return OCC_ERR_CUDA;
-        if (!mark(3 + c)) return OCC_ERR_CUDA;
+        if (run_cls[c] && launch_scan(a, id, sc.sms * sc.scan_bps[id], wst) != cudaSuccess) return OCC_ERR_CUDA;
+        if (ev && cudaEventRecord(ev[3 + c], wst) != cudaSuccess) return OCC_ERR_CUDA;
     }
+    if (fork && (cudaEventRecord(side->join, side->st) != cudaSuccess || cudaStreamWaitEvent(st, side->join, 0) != cudaSuccess))
+        return OCC_ERR_CUDA;
     if (launch_mask(a, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
     return OCC_OK;
 }
@@ -291,8 +310,11 @@ void occ_destroy(occ_ctx* ctx)
         cudaFree(ctx->d_D_stage);
         cudaFree(ctx->d_M_stage);
         cudaFree(ctx->d_O_stage);
-        for (int i = 0; i <= OCC_NUM_STAGES; i++)
+        for (int i = 0; i <= OCC_NUM_STAGES + 1; i++)
             if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+        if (ctx->side.fork) cudaEventDestroy(ctx->side.fork);
+        if (ctx->side.join) cudaEventDestroy(ctx->side.join);
+        if (ctx->side.st) cudaStreamDestroy(ctx->side.st);
     }
     delete ctx;
 }
@@ -336,7 +358,10 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
               cudaMalloc(&ctx->d_cand, sizeof(uint32_t) * (size_t)sc.cand_entries) == cudaSuccess &&
               cudaMalloc(&ctx->d_fb, sizeof(uint32_t) * (size_t)sc.fb_entries) == cudaSuccess &&
               cudaMalloc(&ctx->d_brk, sizeof(uint32_t) * (size_t)sc.brk_entries) == cudaSuccess &&
-              cudaMemset(ctx->d_block, 0, total) == cudaSuccess;
+              cudaMemset(ctx->d_block, 0, total) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&ctx->side.st, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->side.fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ctx->side.join, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         occ_destroy(ctx);
@@ -366,8 +391,10 @@ int ctx_run(occ_ctx* ctx, const FrameIn* fr, int nf, Args& a, void* stream)
     ctx->last_nf = nf;
     ctx->last_nv = a.nv;
     ctx->last_stream = st;
-    const int rc = run_frames(ctx->sc, fr, nf, a, st, ctx->profiling ? ctx->ev : nullptr);
+    bool forked = false;
+    const int rc = run_frames(ctx->sc, fr, nf, a, st, ctx->profiling ? ctx->ev : nullptr, &ctx->side, &forked);
     ctx->profiled_call = ctx->profiling && rc == OCC_OK;
+    ctx->forked_call = forked;
     return rc;
 }
 
@@ -478,7 +505,7 @@ int occ_set_profiling(occ_ctx* ctx, int enable)
     if (enable && !ctx->ev[0]) {
         DeviceGuard g(ctx->device);
         if (!g.ok) return OCC_ERR_CUDA;
-        for (int i = 0; i <= OCC_NUM_STAGES; i++)
+        for (int i = 0; i <= OCC_NUM_STAGES + 1; i++)
             if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) {
                 cudaGetLastError();
                 return OCC_ERR_CUDA;
@@ -497,14 +524,23 @@ int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n)
         cudaGetLastError();
         return OCC_ERR_CUDA;
     }
-    for (int i = 0; i < n; i++) {
-        float t = 0.0f;
-        if (cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) {
+    // Times of every event from the first; stage i lasts from its start to its end event.  When the warp kernels ran
+    // on the side stream, they start where the line kernel ended (the fork) and the mask starts at the later of
+    // the two streams' ends.
+    float t[OCC_NUM_STAGES + 2] = {};
+    const int ne = ctx->forked_call ? OCC_NUM_STAGES + 2 : OCC_NUM_STAGES + 1;
+    for (int i = 1; i < ne; i++)
+        if (cudaEventElapsedTime(&t[i], ctx->ev[0], ctx->ev[i]) != cudaSuccess) {
             cudaGetLastError();
             return OCC_ERR_CUDA;
         }
-        ms[i] = t;
+    float start[OCC_NUM_STAGES];
+    for (int i = 0; i < OCC_NUM_STAGES; i++) start[i] = t[i];
+    if (ctx->forked_call) {
+        start[2] = t[OCC_NUM_STAGES + 1];
+        start[OCC_NUM_STAGES - 1] = fmaxf(t[2], t[OCC_NUM_STAGES - 1]);
     }
+    for (int i = 0; i < n; i++) ms[i] = t[i + 1] - start[i];
     return OCC_OK;
 }
 

@@ -122,6 +122,7 @@ cudaError_t launch_edges(const Args& a, cudaStream_t st);
 cudaError_t launch_plan(const Args& a, cudaStream_t st);
 // The line-per-thread scan over every view; wide = true when some frame's offsets need 64 bits.
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);
+cudaError_t launch_merge_lines(const Args& a, int grid, bool wide, cudaStream_t st);
 // cls = kNumClasses launches the class-0 kernel with 4-warp blocks.
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, cudaStream_t st);
@@ -173,9 +174,18 @@ struct FrameIn {
 // OCC_ERR_INVALID_ARG.
 int prepare_views(const occ_view* views, int32_t n_views, const occ_params* p, Args& a);
 
-// Queues the method (Eq. 1-6) for nf validated frames.  ev (profiling) is null or OCC_NUM_STAGES + 1 events.
-// Returns OCC_OK once queued, or OCC_ERR_CUDA.
-int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev);
+// A second stream and two events a context lends run_frames, so that the merge kernel and the warp kernels run side
+// by side (both only add to O and the statistics; the warp kernels' lines are flagged before either starts).
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+// Queues the method (Eq. 1-6) for nf validated frames on st (and side, when given).  ev (profiled calls) is null or
+// OCC_NUM_STAGES + 2 events: the stage boundaries and the point where the side stream starts; *forked tells whether
+// the warp kernels ran on the side stream.  Returns OCC_OK once queued, or OCC_ERR_CUDA.
+int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev,
+               const SideStream* side = nullptr, bool* forked = nullptr);
 
 // Occupancy of the persistent scan kernels on the current device (also sets their shared-memory opt-ins) and the
 // default tuning.

@@ -1559,15 +1559,12 @@ cudaError_t launch_plan(const Args& a, cudaStream_t st)
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st)
 {
     // N = 8 (the default) takes the rotating window; wide frames and hit flags are the rarer variants; large calls
-    // take their chunks from a counter.  The merge kernel follows: it takes the broken lines' counts back and merges
-    // those of two macro-runs.
+    // take their chunks from a counter.
     const bool h4 = a.N == 8;
 #define OCC_LINES(W, HI, DY)                                                                       \
     do {                                                                                           \
         if (h4) k_scan_lines<W, HI, true, DY><<<grid, kLineThreads, 0, st>>>(a);                   \
         else k_scan_lines<W, HI, false, DY><<<grid, kLineThreads, 0, st>>>(a);                     \
-        if (h4) k_merge_lines<W, HI, true><<<grid, kLineThreads, 0, st>>>(a);                      \
-        else k_merge_lines<W, HI, false><<<grid, kLineThreads, 0, st>>>(a);                        \
     } while (0)
     if (a.line_dyn) {
         if (!wide && !a.hits) OCC_LINES(false, false, true);
@@ -1581,6 +1578,22 @@ cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t s
         else OCC_LINES(true, true, false);
     }
 #undef OCC_LINES
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_lines(const Args& a, int grid, bool wide, cudaStream_t st)
+{
+    const bool h4 = a.N == 8;
+#define OCC_MERGE(W, HI)                                                                           \
+    do {                                                                                           \
+        if (h4) k_merge_lines<W, HI, true><<<grid, kLineThreads, 0, st>>>(a);                      \
+        else k_merge_lines<W, HI, false><<<grid, kLineThreads, 0, st>>>(a);                        \
+    } while (0)
+    if (!wide && !a.hits) OCC_MERGE(false, false);
+    else if (!wide) OCC_MERGE(false, true);
+    else if (!a.hits) OCC_MERGE(true, false);
+    else OCC_MERGE(true, true);
+#undef OCC_MERGE
     return cudaGetLastError();
 }
 
