@@ -53,6 +53,7 @@ def parse():
                          "(0: skip)")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fusion", action="store_true", help="skip the median-fusion / backward-warp measurement")
+    ap.add_argument("--no-stress", action="store_true", help="skip the 4096x2160, 24-view measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip training and measuring the learned tile proposer")
     ap.add_argument("--learned-train-frames", type=int, default=20000)
     ap.add_argument("--learned-cal-target", type=float, default=0.9999,
@@ -310,6 +311,7 @@ def run_ours(args):
     batched = None
     if args.batched_frames > 0:
         batched = run_batched(args, dev, views, rank, world)
+    stress = None if args.no_stress else run_stress(args, dev, rank, world)
     fusion = None if args.no_fusion else run_fusion(args, dev, frames[0], views)
     learned_res = None if args.no_learned else run_learned(args, dev, views)
 
@@ -335,6 +337,7 @@ def run_ours(args):
             "clocks": clk,
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
             "batched": batched,
+            "stress": stress,
             "fusion_and_warp": fusion,
             "learned": learned_res,
             "work": {"samples_per_step": samples, "pair_tests_per_step": pairs,
@@ -398,6 +401,62 @@ def run_batched(args, dev, views, rank, world):
     return {"value": round(steps * world * px * V / t / 1e6, 1), "unit": UNIT, "ms_per_step": round(t / steps * 1e3, 3),
             "frames": len(Ds), "pixels_per_frame_set": px, "views": V, "steps": steps, "cuda_graph": True,
             "tuning": tuning, "l2": "inputs and outputs larger than L2", "clocks": clk}
+
+
+def run_stress(args, dev, rank, world):
+    """The 4096x2160 map with noise sigma 0.5 and 2 % salt outliers, 24 views on the rings of a 5x5 array (r up to
+    2.83, scan lines up to about 740 samples): the same call as the main step, on the workload where Eq. 2 passes most
+    pixels and the scan stage dominates."""
+    import torch
+
+    import paper_2408_14050_gb300 as occ
+    from paper_2408_14050_gb300 import shard
+
+    wl = scenes.stress_5x5()
+    D = torch.from_numpy(wl.frames[0]).to(dev)
+    H, W = D.shape
+    V = len(wl.views)
+    ctx = occ.occ_create(dev.index, max_pixels=H * W, max_views=V)
+    M = torch.empty((V, H, W), dtype=torch.uint8, device=dev)
+    O = torch.empty((V, H, W), dtype=torch.int32, device=dev)
+    p = occ.occ_default_params()
+    occ.occ_detect(ctx, D, wl.views, p, M=M, O=O)
+    if occ.occ_get_status(ctx) != occ.OCC_OK:
+        raise RuntimeError("stress detect failed")
+    st = occ.occ_get_stats(ctx, V)
+    samples = sum(v["samples"] for v in st)
+    pairs = sum(v["pair_tests"] for v in st)
+    cands = sum(v["candidates"] for v in st)
+    steps = max(3, min(args.steps, 10))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record()
+    for _ in range(steps):
+        occ.occ_detect(ctx, D, wl.views, p, M=M, O=O)
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+    occ.occ_set_profiling(ctx, True)
+    occ.occ_detect(ctx, D, wl.views, p, M=M, O=O)
+    stage = occ.occ_get_timings(ctx)
+    occ.occ_set_profiling(ctx, False)
+    if occ.occ_get_status(ctx) != occ.OCC_OK:
+        raise RuntimeError("stress detect failed")
+    ctx.close()
+    ms = t / steps * 1e3
+    ops = 8 * samples + 3 * pairs
+    scan_ms = ms - stage["candidates"] - stage["mask"]
+    alu_peak = 152 * 128 * 2.07e9
+    return {"value": round(steps * world * H * W * V / t / 1e6, 1), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "workload": f"stress_5x5_{W}x{H}_{V}views", "views": "alpha 0..345 step 15, r = ring / max(|cos|, |sin|)",
+            "candidates": cands, "samples": samples, "pair_tests": pairs,
+            "samples_per_s": round(samples / (ms / 1e3)),
+            "scan_alu_frac": round(ops / (scan_ms / 1e3) / alu_peak, 4),
+            "stage_ms": {k: round(v, 3) for k, v in stage.items()}, "steps": steps,
+            "l2": "inputs and outputs larger than L2", "clocks": clk}
 
 
 def run_fusion(args, dev, frame, views):

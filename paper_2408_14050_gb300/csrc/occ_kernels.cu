@@ -15,7 +15,7 @@
 //   k_merge_lines one thread per listed line: the stream again with negated counts (which takes its partial counts
 //                 back), then the two-buffer merge for lines of two macro-runs; longer lines are flagged for k_scan.
 //   k_scan        one warp per scan line (any line, any N): the same steps with the sort as a merge of the line's
-//                 monotone runs or a bitonic network.
+//                 monotone runs or, for many runs, a counting sort by W bucket.
 //   k_mask        M = (O > 0) (Eq. 6).
 //
 // Every floating-point operation that decides a candidate, a position, an order or a count is an explicit
@@ -1110,7 +1110,8 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_merge_lines(const __grid_co
 // not larger than its own; its rank is its index plus the first count minus the number of samples of earlier runs
 // with larger W.  Runs whose W range does not straddle the sample's W contribute nothing or everything, so only
 // straddling runs need a binary search, and a sample that no other run straddles keeps its index.  A line that is
-// one run is already sorted; a line with more than kMaxRuns runs goes through a bitonic network.
+// one run is already sorted; a line with more than kMaxRuns runs goes through a counting sort by W bucket and
+// transposition passes within the buckets.
 // Occlusion test (Eq. 5).  Every pair of sorted positions (q, q+d), d <= N/2, is tested once from its lower end:
 // |fl(W_q - W_{q+d})| is symmetric, and |dW| grows with d in sorted order, so the pairs found this way are exactly
 // the ones the walk of Eq. 5 reaches from either end.  q is hit when V_q + beta < V_{q+d}, and q+d when
@@ -1125,7 +1126,7 @@ struct ScanSmem {
     int32_t upix[CAP];  // pixel by k
     float sw[CAP];      // sorted W (hit counters when the line is one run)
     float sv[CAP];      // sorted V (hit counters when the line is one run)
-    int32_t spix[CAP];  // sorted pixel (index buffer of the bitonic fallback)
+    int32_t spix[CAP];  // sorted pixel (index buffer of the bucket sort)
     int32_t runs[kMaxRuns + 2];
     float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
     float run_hi[kMaxRuns + 1];   // last (largest) W of each run
@@ -1360,32 +1361,68 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                     S.spix[rank] = upix[i];
                 }
             } else {
-                // Many runs: bitonic sort of (W, index) over the next power of two.
-                int Pn = 32;
-                while (Pn < n) Pn <<= 1;
-                for (int i = lane; i < Pn; i += 32) {
-                    S.sw[i] = (i < n) ? uw[i] : INFINITY;
-                    S.spix[i] = (i < n) ? i : INT_MAX;
+                // Many runs: a counting sort by the bucket (int)(fl(W - W_min) * scale) -- a non-decreasing function of W,
+                // so it orders the samples of different buckets -- then odd-even transposition passes by (W, index)
+                // until none swaps, which orders the samples within a bucket.  Buckets are about one W unit wide, at
+                // most CAP of them, so most hold a sample or two.
+                float wlo = INFINITY, whi = -INFINITY;
+                for (int i = lane; i < n; i += 32) {
+                    wlo = fminf(wlo, uw[i]);
+                    whi = fmaxf(whi, uw[i]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    wlo = fminf(wlo, __shfl_xor_sync(kFull, wlo, o));
+                    whi = fmaxf(whi, __shfl_xor_sync(kFull, whi, o));
+                }
+                const float span = __fsub_rn(whi, wlo);
+                int B = CAP;
+                float scale = 1.0f;
+                if (span < (float)(CAP - 1)) B = (int)span + 1;
+                else scale = (float)(CAP - 1) / span;
+                auto bucket = [&](float w) { return min((int)(__fsub_rn(w, wlo) * scale), B - 1); };
+                int* cnt = reinterpret_cast<int*>(S.sw);
+                for (int b = lane; b < B; b += 32) cnt[b] = 0;
+                __syncwarp();
+                for (int i = lane; i < n; i += 32) atomicAdd(&cnt[bucket(uw[i])], 1);
+                __syncwarp();
+                // Exclusive prefix sums of the counts, 32 buckets at a time.
+                int carry = 0;
+                for (int b0 = 0; b0 < B; b0 += 32) {
+                    const int b = b0 + lane;
+                    const int c = b < B ? cnt[b] : 0;
+                    int incl = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    if (b < B) cnt[b] = carry + incl - c;
+                    carry += __shfl_sync(kFull, incl, 31);
                 }
                 __syncwarp();
-                for (int size = 2; size <= Pn; size <<= 1) {
-                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                        for (int t = lane; t < (Pn >> 1); t += 32) {
-                            const int i = 2 * t - (t & (stride - 1));
-                            const int jj = i + stride;
-                            const float wi = S.sw[i], wj = S.sw[jj];
-                            const int ii = S.spix[i], ij = S.spix[jj];
-                            const bool gt = (wi > wj) || (wi == wj && ii > ij);
-                            if (gt == ((i & size) == 0)) {
-                                S.sw[i] = wj; S.sw[jj] = wi;
-                                S.spix[i] = ij; S.spix[jj] = ii;
+                for (int i = lane; i < n; i += 32) S.spix[atomicAdd(&cnt[bucket(uw[i])], 1)] = i;
+                __syncwarp();
+                for (;;) {
+                    bool swapped = false;
+#pragma unroll
+                    for (int par = 0; par < 2; par++) {
+                        for (int i = 2 * lane + par; i + 1 < n; i += 64) {
+                            const int ia = S.spix[i], ib = S.spix[i + 1];
+                            const float wa = uw[ia], wb = uw[ib];
+                            if (wa > wb || (wa == wb && ia > ib)) {
+                                S.spix[i] = ib;
+                                S.spix[i + 1] = ia;
+                                swapped = true;
                             }
                         }
                         __syncwarp();
                     }
+                    if (!__any_sync(kFull, swapped)) break;
                 }
                 for (int q = lane; q < n; q += 32) {
                     const int idx = S.spix[q];
+                    S.sw[q] = uw[idx];
                     S.sv[q] = uv[idx];
                     S.spix[q] = upix[idx];
                 }
