@@ -1123,10 +1123,9 @@ template <int CAP>
 struct ScanSmem {
     float uw[CAP];      // W by k; after the sort, hit counters
     float uv[CAP];      // V by k; after the sort, hit counters
-    int32_t upix[CAP];  // pixel by k
-    float sw[CAP];      // sorted W (hit counters when the line is one run)
+    float sw[CAP];      // sorted W (hit counters when the line is one run; bucket counts during the bucket sort)
     float sv[CAP];      // sorted V (hit counters when the line is one run)
-    int32_t spix[CAP];  // sorted pixel (index buffer of the bucket sort)
+    uint16_t sidx[CAP]; // sample index (k - k0) of each sorted position
     int32_t runs[kMaxRuns + 2];
     float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
     float run_hi[kMaxRuns + 1];   // last (largest) W of each run
@@ -1221,24 +1220,18 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
             // Every lane's gathers (at most CAP / 32) are issued before any is used.
             constexpr int kSl = CAP / 32;
             float dvs[kSl];
-            int pxs[kSl];
             bool oks[kSl];
 #pragma unroll
             for (int i = 0; i < kSl; i++) {
                 const int k = i * 32 + lane;
                 oks[i] = false;
                 dvs[i] = 0.0f;
-                pxs[i] = 0;
                 if (k < nk) {
                     const float g = (float)(k - h);
                     const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
                     const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
                     oks[i] = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
-                    if (oks[i]) {
-                        const int px = (int)rx, py = (int)ry;
-                        dvs[i] = __ldg(F.D + (int64_t)py * F.pitch + px);
-                        pxs[i] = py * W + px;
-                    }
+                    if (oks[i]) dvs[i] = __ldg(F.D + (int64_t)(int)ry * F.pitch + (int)rx);
                 }
             }
 #pragma unroll
@@ -1250,7 +1243,6 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                     const float V = one ? dvs[i] : __fmul_rn(va.r, dvs[i]);
                     S.uw[k] = __fsub_rn((float)(k - h), V);
                     S.uv[k] = V;
-                    S.upix[k] = pxs[i];
                 }
                 record(base, oks[i]);
             }
@@ -1264,12 +1256,10 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                     const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
                     ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
                     if (ok) {
-                        const int px = (int)rx, py = (int)ry;
-                        const float dv = __ldg(F.D + (int64_t)py * F.pitch + px);
+                        const float dv = __ldg(F.D + (int64_t)(int)ry * F.pitch + (int)rx);
                         const float V = one ? dv : __fmul_rn(va.r, dv);
                         S.uw[k] = __fsub_rn(g, V);
                         S.uv[k] = V;
-                        S.upix[k] = py * W + px;
                     }
                 }
                 record(base, ok);
@@ -1284,7 +1274,6 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         __syncwarp();
         const float* uw = S.uw + k0;
         const float* uv = S.uv + k0;
-        const int32_t* upix = S.upix + k0;
 
         // Runs: a new run starts after every descent W[i+1] < W[i].
         int R = 1;
@@ -1301,15 +1290,14 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
 
         const float* sw;
         const float* sv;
-        const int32_t* spix;
         int* cnt_own;
         int* cnt_up;
         if (R == 1) {
-            sw = uw; sv = uv; spix = upix;
+            sw = uw; sv = uv;
             cnt_own = reinterpret_cast<int*>(S.sv);
             cnt_up = reinterpret_cast<int*>(S.sw);
         } else {
-            sw = S.sw; sv = S.sv; spix = S.spix;
+            sw = S.sw; sv = S.sv;
             cnt_own = reinterpret_cast<int*>(S.uv);
             cnt_up = reinterpret_cast<int*>(S.uw);
             if (R <= kMaxRuns) {
@@ -1358,7 +1346,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                     }
                     S.sw[rank] = wi;
                     S.sv[rank] = uv[i];
-                    S.spix[rank] = upix[i];
+                    S.sidx[rank] = (uint16_t)i;
                 }
             } else {
                 // Many runs: a counting sort by the bucket (int)(fl(W - W_min) * scale) -- a non-decreasing function of W,
@@ -1401,18 +1389,18 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                     carry += __shfl_sync(kFull, incl, 31);
                 }
                 __syncwarp();
-                for (int i = lane; i < n; i += 32) S.spix[atomicAdd(&cnt[bucket(uw[i])], 1)] = i;
+                for (int i = lane; i < n; i += 32) S.sidx[atomicAdd(&cnt[bucket(uw[i])], 1)] = (uint16_t)i;
                 __syncwarp();
                 for (;;) {
                     bool swapped = false;
 #pragma unroll
                     for (int par = 0; par < 2; par++) {
                         for (int i = 2 * lane + par; i + 1 < n; i += 64) {
-                            const int ia = S.spix[i], ib = S.spix[i + 1];
+                            const int ia = S.sidx[i], ib = S.sidx[i + 1];
                             const float wa = uw[ia], wb = uw[ib];
                             if (wa > wb || (wa == wb && ia > ib)) {
-                                S.spix[i] = ib;
-                                S.spix[i + 1] = ia;
+                                S.sidx[i] = (uint16_t)ib;
+                                S.sidx[i + 1] = (uint16_t)ia;
                                 swapped = true;
                             }
                         }
@@ -1421,10 +1409,9 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                     if (!__any_sync(kFull, swapped)) break;
                 }
                 for (int q = lane; q < n; q += 32) {
-                    const int idx = S.spix[q];
+                    const int idx = S.sidx[q];
                     S.sw[q] = uw[idx];
                     S.sv[q] = uv[idx];
-                    S.spix[q] = upix[idx];
                 }
             }
         }
@@ -1461,13 +1448,16 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
             cnt_own[q] = o;
         }
         __syncwarp();
-        // Eq. 6: add every sample's count to the occlusion sum of its pixel.
+        // Eq. 6: add every sample's count to the occlusion sum of its pixel, found again from its k (Eq. 4).
         int32_t* Ov = F.O + (int64_t)v * F.H * F.W;
         bool hit = false;
         for (int q = lane; q < n; q += 32) {
             const int o = cnt_own[q] + cnt_up[q];
             if (o) {
-                atomicAdd(Ov + spix[q], o);
+                const float g = (float)(k0 + (R == 1 ? q : (int)S.sidx[q]) - h);
+                const int px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
+                const int py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
+                atomicAdd(Ov + py * W + px, o);
                 hit = true;
             }
         }
