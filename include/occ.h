@@ -147,7 +147,9 @@ int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, con
  * Each frame's candidate lists get the context's per-pixel share of its capacity (all of a frame's pixels with the
  * default max_candidates, so they never overflow).  occ_get_status reports the OR of every frame's conditions;
  * occ_get_stats sums candidates, samples and pair tests over the frames and reports the largest L.  Returns OCC_OK
- * once queued, OCC_ERR_INVALID_ARG or OCC_ERR_CUDA.
+ * once queued, OCC_ERR_INVALID_ARG, OCC_ERR_CAPACITY (before any work is queued) when the frames' candidate lists
+ * together hold more than 2^32 - 1 entries (n_views times each frame's share; split the batch or create the context
+ * with a smaller max_candidates), or OCC_ERR_CUDA.
  */
 int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, const int32_t* H, const int32_t* W,
                        const occ_view* views, int32_t n_views, const occ_params* p, uint8_t* const* M,

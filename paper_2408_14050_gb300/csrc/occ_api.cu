@@ -193,6 +193,8 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         }
     }
     if (cand_off > sc.cand_entries || (lines && fb_off > sc.fb_entries)) return OCC_ERR_INVALID_ARG;
+    // The scan kernels number the candidates of a call (every frame and view) with 32-bit work items.
+    if (cand_off > (int64_t)UINT32_MAX) return OCC_ERR_CAPACITY;
     // Above about four 1920x1080 frames of 8 views, static chunks let warps drift over more data than L2 holds.
     a.line_dyn = px_views > (int64_t)64 * 1024 * 1024 ? 1 : 0;
 
