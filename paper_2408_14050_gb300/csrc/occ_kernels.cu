@@ -522,6 +522,24 @@ __device__ __forceinline__ bool line_sample(const Args& a, const FrameArg& F, co
     return true;
 }
 
+// Pixel index and element offset in D of sample k (inside the image) from its table word t.
+template <bool kWide>
+__device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, int cx, int cy, int h, int t, int k,
+                                         int& pix, int64_t& off)
+{
+    int px, py;
+    if (t != kTabExact) {
+        px = cx + (int)(int16_t)(t & 0xFFFF);
+        py = cy + (t >> 16);
+    } else {
+        const float g = (float)(k - h);
+        px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
+        py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
+    }
+    pix = py * F.W + px;
+    off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
+}
+
 // The sort key is (W, k).  A sample read later along a line has the larger k, so it precedes an earlier one exactly
 // when its W is smaller; a sample of the first macro-run has a smaller k than every sample of the second, so it
 // precedes one of the second exactly when its W is not larger.
@@ -680,6 +698,17 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
         hb = bufb;
         hbb = false;
     }
+    // Each run's next sample (k = kn) is loaded ahead: its D value and pixel, used when the run next advances.
+    const int* tk = tab + (kTabHalf - h);
+    float da = 0.0f, db = 0.0f;
+    int pa = 0, pb = 0;
+    auto load = [&](int k, float& d, int& p) {
+        int64_t off;
+        line_pos<kWide>(F, va, cx, cy, h, tk[k], k, p, off);
+        d = __ldg(F.D + off);
+    };
+    if (kna <= ea) load(kna, da, pa);
+    if (knb <= eb) load(knb, db, pb);
     // One merge step: the smaller head is emitted, its run advances by one sample through its buffer.
 #define OCC_MERGE_STEP(PUSH)                                                                   \
     {                                                                                          \
@@ -689,11 +718,17 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
         const int ke = ta ? ea : eb;                                                           \
         bool hbuf = ta ? hba : hbb;                                                            \
         LineSample buf = ta ? bufa : bufb;                                                     \
+        float d = ta ? da : db;                                                                \
+        int p = ta ? pa : pb;                                                                  \
         LineSample head = buf;                                                                 \
         bool has = false;                                                                      \
         if (kn <= ke) {                                                                        \
-            line_sample<kWide>(a, F, va, tab, cx, cy, h, kn, false, s);                        \
+            s.v = (va.r == 1.0f) ? d : __fmul_rn(va.r, d);                                     \
+            s.w = __fsub_rn((float)(kn - h), s.v);                                             \
+            s.p = p;                                                                           \
+            s.k = kn;                                                                          \
             kn++;                                                                              \
+            if (kn <= ke) load(kn, d, p);                                                      \
             const bool sb = later_before(s, buf);                                              \
             head = sb ? s : buf;                                                               \
             if (!sb) buf = s;                                                                  \
@@ -702,8 +737,8 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
             hbuf = false;                                                                      \
             has = true;                                                                        \
         }                                                                                      \
-        if (ta) { kna = kn; hba = hbuf; bufa = buf; ha = head; has_a = has; }                  \
-        else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; }                     \
+        if (ta) { kna = kn; hba = hbuf; bufa = buf; ha = head; has_a = has; da = d; pa = p; }  \
+        else { knb = kn; hbb = hbuf; bufb = buf; hb = head; has_b = has; db = d; pb = p; }     \
         PUSH;                                                                                  \
     }
     if constexpr (kHalf4) {
@@ -764,23 +799,6 @@ __device__ __forceinline__ void line_range(const FrameArg& F, const ViewArg& va,
     k1 = lo1;
 }
 
-// Pixel index and element offset in D of sample k (inside the image) from its table word t.
-template <bool kWide>
-__device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, int cx, int cy, int h, int t, int k,
-                                         int& pix, int64_t& off)
-{
-    int px, py;
-    if (t != kTabExact) {
-        px = cx + (int)(int16_t)(t & 0xFFFF);
-        py = cy + (t >> 16);
-    } else {
-        const float g = (float)(k - h);
-        px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
-        py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
-    }
-    pix = py * F.W + px;
-    off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
-}
 
 // One pass over a line that takes it to be a single macro-run: samples k0 .. k1 through the one-slot buffer, each
 // emitted sample tested (Eq. 5) against the N/2 emitted before it, final counts to O (Eq. 6).  Every lane of the warp
