@@ -410,7 +410,7 @@ def run_stress(args, dev, rank, world):
     import torch
 
     import paper_2408_14050_gb300 as occ
-    from paper_2408_14050_gb300 import shard
+    from paper_2408_14050_gb300 import autotune, shard
 
     wl = scenes.stress_5x5()
     D = torch.from_numpy(wl.frames[0]).to(dev)
@@ -420,6 +420,9 @@ def run_stress(args, dev, rank, world):
     M = torch.empty((V, H, W), dtype=torch.uint8, device=dev)
     O = torch.empty((V, H, W), dtype=torch.int32, device=dev)
     p = occ.occ_default_params()
+    tuning = occ.occ_get_tuning(ctx)[0]
+    if not args.no_autotune:
+        tuning, _ = autotune.autotune(ctx, [D], wl.views, reps=1, cache_path=None)
     occ.occ_detect(ctx, D, wl.views, p, M=M, O=O)
     if occ.occ_get_status(ctx) != occ.OCC_OK:
         raise RuntimeError("stress detect failed")
@@ -455,7 +458,7 @@ def run_stress(args, dev, rank, world):
             "candidates": cands, "samples": samples, "pair_tests": pairs,
             "samples_per_s": round(samples / (ms / 1e3)),
             "scan_alu_frac": round(ops / (scan_ms / 1e3) / alu_peak, 4),
-            "stage_ms": {k: round(v, 3) for k, v in stage.items()}, "steps": steps,
+            "stage_ms": {k: round(v, 3) for k, v in stage.items()}, "steps": steps, "tuning": tuning,
             "l2": "inputs and outputs larger than L2", "clocks": clk}
 
 

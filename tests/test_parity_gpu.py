@@ -173,8 +173,9 @@ def test_scan_length_classes_exact(ctx, L):
     assert_exact(ctx, D, [(0.0, 1.0), (30.0, 1.0), (180.0, 1.3)], dict(L=L))
 
 
-def test_many_runs_use_the_bitonic_fallback_exact(ctx):
-    # Salt-and-pepper maps break scan lines into many monotone runs (more than the merge handles).
+def test_many_runs_use_the_bucket_sort_exact(ctx):
+    # Salt-and-pepper maps break scan lines into many monotone runs (more than the run merge handles), which the warp
+    # kernel sorts by W bucket and transposition passes.
     rng = np.random.default_rng(5)
     D = rng.uniform(0, 40, (48, 200)).astype(np.float32)
     assert_exact(ctx, D, [(0.0, 1.0), (60.0, 1.0), (225.0, 2.5)], dict(L=300))
@@ -216,6 +217,27 @@ def test_repeat_is_deterministic(ctx):
     np.testing.assert_array_equal(a["O"], b["O"])
     np.testing.assert_array_equal(a["M"], b["M"])
     assert a["stats"] == b["stats"]
+
+
+def test_profiled_call_times_its_stages(ctx):
+    # With profiling on, a call records its stage boundaries; the warp kernels run on the context's second stream
+    # beside the merge kernel and their stages count from where they start.  The results do not change.
+    D = scenes.array_3x3(frame=1, H=540, W=960).frames[0]
+    views = scenes.views_3x3()
+    plain = run_gpu(ctx, D, views, both_params()[1])
+    with pytest.raises(occ.OccError):
+        occ.occ_get_timings(ctx)                  # no profiled call yet
+    occ.occ_set_profiling(ctx, True)
+    try:
+        prof = run_gpu(ctx, D, views, both_params()[1])
+        t = occ.occ_get_timings(ctx)
+    finally:
+        occ.occ_set_profiling(ctx, False)
+    np.testing.assert_array_equal(prof["O"], plain["O"])
+    np.testing.assert_array_equal(prof["M"], plain["M"])
+    assert set(t) == set(occ.STAGES)
+    assert all(v >= 0.0 for v in t.values()), t
+    assert t["scan_lines"] > 0.0 and t["candidates"] > 0.0 and t["mask"] > 0.0, t
 
 
 def test_host_buffer_entry_point(ctx):
