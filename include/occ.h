@@ -215,9 +215,10 @@ int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
  * fully reserved up front, or a framework that hands out only the tensors it manages).  The paper has no counterpart;
  * this is a deployment variant of the same computation with the same results.
  *
- * Its scratch (headers, counters and plan, 4 KB, scan-line position tables, 1 MiB, a bit per pixel and view, and
- * the candidate lists, 4 bytes per pixel and view) is one array of about 67 MiB built into the library: every GPU on which the library is used holds it until the
- * process exits.  The call itself allocates and frees nothing.  Every call on a device
+ * Its scratch (headers, counters and plan, 4 KB, scan-line position tables, 1 MiB, a bit per pixel and view, the
+ * candidate lists, 4 bytes per pixel and view, and the list of scan lines handed from the line kernel to the merge
+ * kernel, 4 more) is one array of about 131 MiB built into the library: every GPU on which the library is used holds
+ * it until the process exits.  The call itself allocates and frees nothing.  Every call on a device
  * shares that array and overwrites it, clearing first what must start at zero; two calls that may run at the same
  * time on the GPU (different streams, or different host threads) race on it and give wrong results, so serialise
  * them (one stream).  The first call on a device also looks up the array's device address and sets the kernels'
