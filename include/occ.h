@@ -137,6 +137,17 @@ int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, con
                     int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream);
 
 /*
+ * occ_detect_host without the wait: returns OCC_OK once the copy in, the detection and the copies out are queued on
+ * `stream` (or OCC_ERR_INVALID_ARG / OCC_ERR_CUDA without queueing anything).  D_host must stay unchanged, and
+ * M_host / O_host must not be read, until the stream reaches that point; occ_get_status(ctx, stream) then gives the
+ * call's device-detected status.  The copies run asynchronously only on pinned host memory.  Frames on two contexts
+ * and two streams overlap one frame's copies with the other's detection; calls on one context must not overlap on
+ * the GPU (they share its staging buffers), so a context takes its next frame on the same stream.
+ */
+int occ_detect_host_async(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,
+                          int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream);
+
+/*
  * The method for n_frames frames of possibly different sizes and the same views, queued as one batch: a handful of
  * launches for the whole batch (the candidate pass over every frame, one plan, one persistent launch of each scan
  * kernel over every frame, view and candidate, one mask pass), with results identical to n_frames occ_detect calls.

@@ -35,7 +35,7 @@ OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
 OCC_MAX_FRAMES = 1024
 
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
-            "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning",
+            "occ_detect_host_async", "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning",
             "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc", "occ_fuse_median", "occ_warp_views",
             "occ_detect_batched_tiles", "occ_net_create", "occ_net_destroy", "occ_net_set_params",
             "occ_net_get_params", "occ_net_forward", "occ_net_loss_grad", "occ_net_adam", "occ_net_propose",
@@ -112,6 +112,8 @@ def load(build_if_missing: bool = True):
         L.occ_detect_host.argtypes = [vp, vp, i32, i32, ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
                                       vp, vp, vp]
         L.occ_detect_host.restype = ctypes.c_int
+        L.occ_detect_host_async.argtypes = L.occ_detect_host.argtypes
+        L.occ_detect_host_async.restype = ctypes.c_int
         L.occ_detect_batched.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                          ctypes.POINTER(occ_view), i32, ctypes.POINTER(occ_params),
                                          ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -335,9 +337,11 @@ def occ_detect_batched(ctx: Context, Ds, views, params: occ_params | None = None
     return Ms, Os
 
 
-def occ_detect_host(ctx: Context, D, views, params: occ_params | None = None, M=None, O=None, stream=None):
+def occ_detect_host(ctx: Context, D, views, params: occ_params | None = None, M=None, O=None, stream=None,
+                    wait: bool = True):
     """The method on host buffers (numpy or CPU tensors; pinned memory is fastest): copies in, runs, copies M (and O
-    if given) back, waits.  Returns the status code."""
+    if given) back, and (wait) waits.  Returns (status code, M, O); with wait=False the code only says whether the work
+    was queued, M and O are complete once the stream gets there, and occ_get_status gives the device status."""
     import numpy as np
     H, W = D.shape
     nv = len(views)
@@ -351,9 +355,9 @@ def occ_detect_host(ctx: Context, D, views, params: occ_params | None = None, M=
             return ctypes.c_void_p(x.data_ptr())
         return ctypes.c_void_p(x.ctypes.data)
 
-    rc = load().occ_detect_host(ctx.handle, addr(D), H, W, _views(views), nv,
-                                ctypes.byref(params) if params is not None else None, addr(M), addr(O),
-                                _stream_handle(stream))
+    fn = load().occ_detect_host if wait else load().occ_detect_host_async
+    rc = fn(ctx.handle, addr(D), H, W, _views(views), nv, ctypes.byref(params) if params is not None else None,
+            addr(M), addr(O), _stream_handle(stream))
     ctx.last_views = nv
     return rc, M, O
 

@@ -602,8 +602,8 @@ int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views)
     return rc;
 }
 
-int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,
-                    int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream)
+int occ_detect_host_async(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,
+                          int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream)
 {
     if (!ctx || !D_host || !M_host || !views) return OCC_ERR_INVALID_ARG;
     if (H < 1 || W < 1 || (int64_t)H * W > ctx->max_pixels || n_views < 1 || n_views > ctx->max_views)
@@ -629,7 +629,14 @@ int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, con
     if (O_host && cudaMemcpyAsync(O_host, ctx->d_O_stage, sizeof(int32_t) * plane * n_views,
                                   cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return OCC_ERR_CUDA;
-    return occ_get_status(ctx, stream);
+    return OCC_OK;
+}
+
+int occ_detect_host(occ_ctx* ctx, const float* D_host, int32_t H, int32_t W, const occ_view* views,
+                    int32_t n_views, const occ_params* p, uint8_t* M_host, int32_t* O_host, void* stream)
+{
+    const int rc = occ_detect_host_async(ctx, D_host, H, W, views, n_views, p, M_host, O_host, stream);
+    return rc != OCC_OK ? rc : occ_get_status(ctx, stream);
 }
 
 }  // extern "C"

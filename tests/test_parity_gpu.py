@@ -255,6 +255,37 @@ def test_host_buffer_entry_point(ctx):
         np.testing.assert_array_equal(M[v].numpy(), Mo)
 
 
+def test_host_buffer_calls_queued_on_two_contexts():
+    # occ_detect_host_async on two contexts and two streams, frames alternating and overlapping on the GPU: every
+    # frame's M and O are those of the synchronous call.
+    views = scenes.views_3x3()
+    frames = [scenes.array_3x3(frame=f, H=270, W=480).frames[0] for f in range(4)]
+    ctxs = [occ.occ_create(0, max_pixels=270 * 480, max_views=8) for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pins = [torch.from_numpy(f).pin_memory() for f in frames]
+    Ms = [torch.empty((8, 270, 480), dtype=torch.uint8).pin_memory() for _ in frames]
+    Os = [torch.empty((8, 270, 480), dtype=torch.int32).pin_memory() for _ in frames]
+    try:
+        for i in range(len(frames)):
+            j = i & 1
+            if i >= 2:
+                assert occ.occ_get_status(ctxs[j], streams[j]) == occ.OCC_OK
+            rc, _, _ = occ.occ_detect_host(ctxs[j], pins[i], views, both_params()[1], M=Ms[i], O=Os[i],
+                                           stream=streams[j], wait=False)
+            assert rc == occ.OCC_OK
+        for j in range(2):
+            assert occ.occ_get_status(ctxs[j], streams[j]) == occ.OCC_OK
+        for i, D in enumerate(frames):
+            M = torch.empty((8, 270, 480), dtype=torch.uint8).pin_memory()
+            O = torch.empty((8, 270, 480), dtype=torch.int32).pin_memory()
+            rc, _, _ = occ.occ_detect_host(ctxs[0], pins[i], views, both_params()[1], M=M, O=O)
+            assert rc == occ.OCC_OK
+            assert torch.equal(M, Ms[i]) and torch.equal(O, Os[i])
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 # ---------------------------------------------------------------------------------------------------------------
 # Device-detected errors (status word; no fault, no trap)
 
