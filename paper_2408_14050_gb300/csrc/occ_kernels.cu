@@ -522,9 +522,11 @@ __device__ __forceinline__ bool line_sample(const Args& a, const FrameArg& F, co
     return true;
 }
 
-// Pixel index and element offset in D of sample k (inside the image) from its table word t.
+// Pixel index and element offset in D of sample k (inside the image) from its table word t; Wd and pitch are the
+// frame's width and row pitch, held by the caller (a field of the frame record in global memory would be read again
+// after every atomic add to O, which might alias it).
 template <bool kWide>
-__device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, int cx, int cy, int h, int t, int k,
+__device__ __forceinline__ void line_pos(int Wd, int64_t pitch, const ViewArg& va, int cx, int cy, int h, int t, int k,
                                          int& pix, int64_t& off)
 {
     int px, py;
@@ -536,8 +538,8 @@ __device__ __forceinline__ void line_pos(const FrameArg& F, const ViewArg& va, i
         px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), (float)cx));
         py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), (float)cy));
     }
-    pix = py * F.W + px;
-    off = kWide ? (int64_t)py * F.pitch + px : (int64_t)(py * (int)F.pitch + px);
+    pix = py * Wd + px;
+    off = kWide ? (int64_t)py * pitch + px : (int64_t)(py * (int)pitch + px);
 }
 
 // The sort key is (W, k).  A sample read later along a line has the larger k, so it precedes an earlier one exactly
@@ -704,7 +706,7 @@ __device__ __forceinline__ bool line_counts2(const Args& a, const FrameArg& F, c
     int pa = 0, pb = 0;
     auto load = [&](int k, float& d, int& p) {
         int64_t off;
-        line_pos<kWide>(F, va, cx, cy, h, tk[k], k, p, off);
+        line_pos<kWide>(F.W, F.pitch, va, cx, cy, h, tk[k], k, p, off);
         d = __ldg(F.D + off);
     };
     if (kna <= ea) load(kna, da, pa);
@@ -820,6 +822,10 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
 {
     const float kInf = __int_as_float(0x7f800000);
     const int* tk = tab + (kTabHalf - h);
+    const float* const Dp = F.D;
+    const int64_t pitch = F.pitch;
+    const int Wd = F.W;
+    const float r = va.r;
     RotWindow R;
     LineWindow Wn;
     LineSample buf;
@@ -852,13 +858,13 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
         if (kq < k1) {                                                                         \
             const int t = tnext;                                                               \
             tnext = tk[min(kq + 2, k1)];                                                       \
-            line_pos<kWide>(F, va, cx, cy, h, t, kq + 1, pn, on);                              \
-            dn = __ldg(F.D + on);                                                              \
+            line_pos<kWide>(Wd, pitch, va, cx, cy, h, t, kq + 1, pn, on);                      \
+            dn = __ldg(Dp + on);                                                               \
         } else {                                                                               \
             dn = -kInf;                                                                        \
         }                                                                                      \
         LineSample s;                                                                          \
-        s.v = (va.r == 1.0f) ? dv : __fmul_rn(va.r, dv);                                       \
+        s.v = (r == 1.0f) ? dv : __fmul_rn(r, dv);                                             \
         s.w = __fsub_rn(gq, s.v);                                                              \
         s.p = p;                                                                               \
         s.k = 0;                                                                               \
