@@ -144,6 +144,39 @@ def test_row_pitch(ctx, pad):
     assert_exact(ctx, D, [(0.0, 1.0), (45.0, 1.4142135), (250.0, 1.0)], dict(L=30), pitch_pad=pad)
 
 
+@pytest.mark.parametrize("runs", [2, 0])
+def test_row_pitch_beyond_32_bit_offsets(ctx, runs):
+    # A map whose last row starts more than 2^31 elements after its first: the kernels' element offsets into D take
+    # 64 bits (the wide variants of the line, merge and warp kernels).  The rows live in one 8.7 GB buffer.
+    H, W = 64, 96
+    pitch = (1 << 25) + (1 << 20)
+    assert (H - 1) * pitch + W > 2**31 - 1
+    D = noisy_map(H, W, seed=31)
+    big = torch.empty((H - 1) * pitch + W, dtype=torch.float32, device="cuda")
+    try:
+        Dt = big.as_strided((H, W), (pitch, 1))
+        Dt.copy_(torch.from_numpy(D).cuda())
+        views = [(0.0, 1.0), (45.0, 1.4142135), (160.0, 1.0), (270.0, 1.0)]
+        po, pg = both_params(N=8)
+        occ.occ_set_tuning(ctx, {"line_max_runs": runs, "line_blocks_per_sm": 1, "warp_lines_per_block": 8})
+        try:
+            M, O = occ.occ_detect(ctx, Dt, views, pg)
+            assert occ.occ_get_status(ctx) == occ.OCC_OK
+            stats = occ.occ_get_stats(ctx, len(views))
+        finally:
+            occ.occ_set_tuning(ctx, None)
+        M, O = M.cpu().numpy(), O.cpu().numpy()
+        for v, (a, r) in enumerate(views):
+            Ov, Mv, st = oracle.detect_view(D, a, r, po)
+            np.testing.assert_array_equal(O[v], Ov, err_msg=f"O view {v}")
+            np.testing.assert_array_equal(M[v], Mv, err_msg=f"M view {v}")
+            for k in ("candidates", "samples", "pair_tests", "L"):
+                assert stats[v][k] == st[k], (v, k)
+    finally:
+        del big
+        torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("kw", [dict(N=2), dict(N=4), dict(N=6), dict(N=16), dict(N=64), dict(zeta=0.75), dict(zeta=3.5),
                                 dict(beta=0.0), dict(beta=2.0), dict(gamma=0.25), dict(gamma=3.0)])
 def test_parameters_exact(ctx, kw):
