@@ -143,7 +143,8 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.status = sc.status;
     a.line_ctr = sc.status + 1;   // the status region has room for the counters
     a.brk = sc.brk;
-    a.brk_count = sc.status + 2;
+    a.brk_count = reinterpret_cast<unsigned long long*>(sc.status + 2);
+    a.merge_ctr = sc.status + 4;
     a.brk_cap = (uint32_t)(sc.brk_entries < (int64_t)UINT32_MAX ? sc.brk_entries : (int64_t)UINT32_MAX);
     a.max_quads = 0;
     a.max_px = 0;
@@ -201,7 +202,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], st) == cudaSuccess; };
     if (cudaMemsetAsync(sc.hdr, 0, sizeof(uint32_t) * HDR_WORDS * nf, st) != cudaSuccess ||
         cudaMemsetAsync(sc.stats, 0, sizeof(unsigned long long) * 2 * sc.max_views * nf, st) != cudaSuccess ||
-        cudaMemsetAsync(sc.status, 0, 3 * sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(sc.status, 0, 5 * sizeof(uint32_t), st) != cudaSuccess ||
         (lines && cudaMemsetAsync(sc.fb, 0, sizeof(uint32_t) * fb_off, st) != cudaSuccess))
         return OCC_ERR_CUDA;
     // Size classes of the warp kernels that can receive work: with a fixed L only one.

@@ -102,8 +102,12 @@ struct Args {
     int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact
     uint32_t* status;             // OR of every frame's status bits
     uint32_t* line_ctr;           // work counter of the line kernel, zero at the start of a call
-    uint32_t* brk;                // work items of the lines of more than one macro-run, for the merge kernel
-    uint32_t* brk_count;          // entries written to brk, zero at the start of a call
+    uint32_t* brk;                // lists of the merge kernel: from the front, the work items of the lines of more than
+                                  // one macro-run (replays); from the back, pairs (work item, ks) of the lines of two
+                                  // (merges), in the room the call's candidates leave free
+    unsigned long long* brk_count;  // entries at the front (low word), pairs at the back (high word; may exceed the
+                                    // room); zero at the start of a call
+    uint32_t* merge_ctr;          // batch counter of the merge kernel, zero at the start of a call
     uint32_t brk_cap;             // entries brk holds: at least the candidates a call can have
 };
 

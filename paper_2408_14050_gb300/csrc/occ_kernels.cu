@@ -830,10 +830,12 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
     LineWindow Wn;
     LineSample buf;
     float lastw, dn, gq;
-    int pn, tnext = 0, kq, left = 0, ks = -1, ht = 0;
+    int pn, tnext = 0, kq, left = 0, ht = 0;
     int64_t on;
-    bool go = live, dry = false;
-    float zl = a.zeta;   // zeta of the pair test (Eq. 5); -1 once the lane only looks for a further macro-run
+    bool go = live;
+    // zeta of the pair test (Eq. 5).  At the first break it becomes -(ks + 1): no pair is close any more, and the
+    // k where the second macro-run starts is kept without a register of its own.
+    float zl = a.zeta;
     more = false;
     if (live) {
         if constexpr (kHalf4) rot_init(R); else window_init(Wn);
@@ -870,14 +872,12 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
         s.k = 0;                                                                               \
         const bool sb = later_before(s, buf);                                                  \
         if (sb && s.w < lastw) {                                                               \
-            if (dry) {                                                                         \
+            if (zl < 0.0f) {                                                                   \
                 go = false;                                                                    \
                 more = true;                                                                   \
             } else {                                                                           \
-                ks = kq;                                                                       \
+                zl = -(float)(kq + 1);                                                         \
                 if (sgn > 0) {                                                                 \
-                    dry = true;                                                                \
-                    zl = -1.0f;                                                                \
                     if constexpr (kHalf4) { R.o[0] = R.o[1] = R.o[2] = R.o[3] = 0; }           \
                     else { Wn.o0 = Wn.o1 = Wn.o2 = Wn.o3 = 0; }                                \
                     buf = s;                                                                   \
@@ -909,7 +909,8 @@ __device__ __forceinline__ int line_stream(const Args& a, const FrameArg& F, con
         }
     }
 #undef OCC_STREAM_STEP
-    if (!live || ks >= 0) return ks;
+    if (!live) return -1;
+    if (zl < 0.0f) return (int)(-zl) - 1;
     if constexpr (kHalf4) hit = rot_flush(R, Ov, ht);
     else hit = window_flush(Wn, Ov);
     return -1;
@@ -999,9 +1000,9 @@ __device__ __forceinline__ void line_mark_hit(const FrameArg& F, const LineJob& 
     if (F.hits) F.hits[(int64_t)jb.v * F.tiles_x * F.tiles_y + (jb.y / kTile) * F.tiles_x + jb.x / kTile] = 1;
 }
 
-// The replay of a broken line's stream with the counts negated (every lane calls it; live: this lane has a line);
-// returns the k where the second macro-run starts.  Kept out of line: an inlined copy of the stream next to the merge
-// costs the merge kernel registers.
+// The replay of a broken line's stream with the counts negated (every lane calls it; live: this lane has a line): it
+// takes what the line kernel added back out of O, and returns the k where the second macro-run starts.  Kept out of
+// line: an inlined copy of the stream next to the merge costs the merge kernel registers.
 template <bool kWide, bool kHits, bool kHalf4>
 __device__ __noinline__ int line_undo(const Args& a, const LineJob& jb, bool live)
 {
@@ -1057,67 +1058,84 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_scan_lines(const __grid_con
             stats.add(a, jb.f * a.nv + jb.v, jb.k1 - jb.k0 + 1, half);
             if (kHits && hit) line_mark_hit(F, jb);
         }
-        // More than one macro-run: the line goes to the merge kernel's list, its counts so far still in O; more than
-        // two: it is also flagged for the warp kernel now.  The list has an entry for every candidate the call can
-        // hold, so it cannot fill up; the check only guards the store.
+        // More than one macro-run: the line's counts so far are still in O, and it goes to the front of the merge
+        // kernel's list, whose replay takes them back out; the list has an entry for every candidate the call can
+        // hold, so the front cannot fill up (the check only guards the store).  A line of exactly two macro-runs
+        // (when line_max_runs = 2) also takes a pair of entries (item, ks) from the back of the list, in the room the
+        // call's candidates leave free, for the two-run merge; every other broken line, and a two-run line that
+        // finds no room, is flagged for the warp kernel now.
         const bool broken = live && ks >= 0;
-        if (broken && more) atomicOr(line_flag_word(a, jb), 1u << (jb.idx & 31));
-        const unsigned mb = __ballot_sync(kFull, broken);
+        bool two = broken && !more && a.line_max_runs >= 2;
+        const unsigned mb = __ballot_sync(kFull, broken), m2 = __ballot_sync(kFull, two);
         if (mb) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(a.brk_count, (uint32_t)__popc(mb));
+            // One atomic reserves both: front entries in the low word, pairs in the high one (the front count never
+            // exceeds the candidates, so the low word cannot carry).
+            unsigned long long base = 0;
+            if (lane == 0)
+                base = atomicAdd(a.brk_count, ((unsigned long long)__popc(m2) << 32) | (unsigned long long)__popc(mb));
             base = __shfl_sync(kFull, base, 0);
-            const uint32_t pos = base + (uint32_t)__popc(mb & lt);
+            if (two) {
+                const uint32_t j = (uint32_t)(base >> 32) + (uint32_t)__popc(m2 & lt);
+                if (j < (a.brk_cap - total) / 2) {
+                    a.brk[a.brk_cap - 2 - 2 * j] = (uint32_t)item;
+                    a.brk[a.brk_cap - 1 - 2 * j] = (uint32_t)ks;
+                } else {
+                    two = false;
+                }
+            }
             if (broken) {
-                if (pos < a.brk_cap) a.brk[pos] = (uint32_t)item;
+                const uint32_t pos = (uint32_t)base + (uint32_t)__popc(mb & lt);
+                if (pos < total) a.brk[pos] = (uint32_t)item;
                 else atomicOr(a.status, ST_INTERNAL);
             }
         }
+        if (broken && !two) atomicOr(line_flag_word(a, jb), 1u << (jb.idx & 31));
         chunk = next_chunk<kDyn>(chunk, nwarps, a.line_ctr, lane);
     }
     stats.flush(a);
     stats_publish(a, s_st);
 }
 
-// k_merge_lines: the lines k_scan_lines listed (more than one macro-run), one thread per line, 32 consecutive list
-// entries per warp.  First the line's stream again with the counts negated, which takes its partial counts back out
-// of O and finds ks, the start of its second macro-run.  Then, when the line kernels keep two-macro-run lines
-// (line_max_runs = 2), a line the line kernel did not flag (exactly two macro-runs) goes through the two-buffer merge
-// (Eq. 5 and Eq. 6 as in the stream); every other line is left flagged for the warp kernel.
+// k_merge_lines: the lines k_scan_lines listed, one thread per list entry, 32 entries per warp; two kinds of work,
+// independent of each other (both only add to O and the statistics), so a line's two jobs can run on different
+// warps at the same time.  The pairs at the back of the list come first: the two-buffer merge of a line of exactly two
+// macro-runs [k0, ks - 1] and [ks, k1] by (W, k), with Eq. 5 and Eq. 6 as in the stream.  Then the entries at the
+// front: the stream of a broken line again with the counts negated, up to the point where it broke, which takes its
+// partial counts back out of O.  A warp's first batch is fixed by its index, the next ones come from a counter, so
+// that the longer merges do not pile up on the warps that drew two of them.
 template <bool kWide, bool kHits, bool kHalf4>
 __global__ void __launch_bounds__(kLineThreads, 3) k_merge_lines(const __grid_constant__ Args a)
 {
     constexpr int kWarps = kLineThreads / 32;
     __shared__ unsigned long long s_st[2 * kStatsSmem];
     stats_init(s_st);
-    const uint32_t n = min(*a.brk_count, a.brk_cap);
+    const uint32_t total = a.pref_all[a.nf * a.nv];
+    const unsigned long long cnt = *a.brk_count;
+    const uint32_t nr = min((uint32_t)cnt, total), nm = min((uint32_t)(cnt >> 32), (a.brk_cap - total) / 2);
+    const uint64_t nbm = (nm + 31u) / 32u, nb = nbm + (nr + 31u) / 32u;
     const int half = a.N >> 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     LineStats stats{s_st};
     const uint64_t nwarps = (uint64_t)gridDim.x * kWarps;
-    for (uint64_t b = (uint64_t)blockIdx.x * kWarps + warp; b * 32 < n; b += nwarps) {
-        const uint64_t e = b * 32 + lane;
-        const bool valid = e < n;
-        LineJob jb{0, 0, 0, 0, 0, 0, 0, 0, -1};
-        if (valid) jb = line_job(a, a.brk[e]);
-        jb.ks = line_undo<kWide, kHits, kHalf4>(a, jb, valid);
-        bool two = false;
-        if (valid) {
-            // Lines of more than two macro-runs were flagged by the line kernel.
-            uint32_t* fw = line_flag_word(a, jb);
-            const uint32_t bit = 1u << (jb.idx & 31);
-            two = a.line_max_runs >= 2 && jb.ks >= 0 && !(*fw & bit);
-            if (!two) atomicOr(fw, bit);
-        }
-        // The lanes leave the replay at different times: the merge starts together.
-        __syncwarp();
-        if (two) {
-            const FrameArg& F = a.frames[jb.f];
-            const bool hit = line_counts2<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
-                                                                F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h,
-                                                                half, jb.k0, jb.k1, jb.ks);
-            if (kHits && hit) line_mark_hit(F, jb);
-            stats.add(a, jb.f * a.nv + jb.v, jb.k1 - jb.k0 + 1, half);
+    for (uint64_t b = (uint64_t)blockIdx.x * kWarps + warp; b < nb; b = next_chunk<true>(b, nwarps, a.merge_ctr, lane)) {
+        if (b < nbm) {
+            const uint64_t e = b * 32 + lane;
+            if (e < nm) {
+                LineJob jb = line_job(a, a.brk[a.brk_cap - 2 - 2 * e]);
+                jb.ks = (int)a.brk[a.brk_cap - 1 - 2 * e];
+                const FrameArg& F = a.frames[jb.f];
+                const bool hit = line_counts2<kWide, kHits, kHalf4>(a, F, a.view[jb.v], a.ptab + (int64_t)jb.v * kTabLen,
+                                                                    F.O + (int64_t)jb.v * F.H * F.W, jb.x, jb.y, jb.h,
+                                                                    half, jb.k0, jb.k1, jb.ks);
+                if (kHits && hit) line_mark_hit(F, jb);
+                stats.add(a, jb.f * a.nv + jb.v, jb.k1 - jb.k0 + 1, half);
+            }
+        } else {
+            const uint64_t e = (b - nbm) * 32 + lane;
+            const bool valid = e < nr;
+            LineJob jb{0, 0, 0, 0, 0, 0, 0, 0, -1};
+            if (valid) jb = line_job(a, a.brk[e]);
+            line_undo<kWide, kHits, kHalf4>(a, jb, valid);
         }
         __syncwarp();
     }

@@ -342,6 +342,28 @@ def test_candidate_overflow_status():
         c.close()
 
 
+@pytest.mark.parametrize("spare", [0, 64])
+def test_two_run_lines_without_room_in_the_list_go_to_the_warp_kernel(spare):
+    # The line kernel's list of the merge kernel holds one entry per candidate the context can hold; the pairs of the
+    # two-run merges live in the entries the call's candidates leave free.  A context sized to the view's candidates
+    # leaves none (every two-run line falls back to the warp kernel), or room for 32 pairs; the results must not
+    # change.
+    D = noisy_map(120, 200, seed=11)
+    a, r = 45.0, 1.4142135
+    po, pg = both_params()
+    O, M, st = oracle.detect_view(D, a, r, po)
+    c = occ.occ_create(0, max_pixels=D.size, max_views=1, max_candidates=st["candidates"] + spare)
+    try:
+        g = run_gpu(c, D, [(a, r)], pg)
+        assert g["status"] == occ.OCC_OK, occ.occ_status_string(g["status"])
+        np.testing.assert_array_equal(g["O"][0], O)
+        np.testing.assert_array_equal(g["M"][0], M)
+        for k in ("candidates", "samples", "pair_tests", "L"):
+            assert g["stats"][0][k] == st[k], k
+    finally:
+        c.close()
+
+
 def test_scan_too_long_status(ctx):
     D = np.zeros((16, 16), np.float32)
     D[3, 3] = 3000.0      # Eq. 3 gives L = 6000 > OCC_MAX_SCAN
