@@ -200,9 +200,9 @@ int occ_get_tuning(occ_ctx* ctx, occ_tuning* t, int32_t* max_line_blocks_per_sm)
 /* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the
  * line-per-thread scan (Eq. 4-6 for the scan lines whose sort is a set of adjacent swaps, or two such stretches;
  * N <= 8), the warp scan kernels of the three scan-line size classes (2h+1 <= 256, <= 1024, <= 4096 samples; Eq. 4-6
- * for the remaining lines), and the mask (Eq. 6).  When the line kernels keep lines of two stretches, calls of up to
- * 64 Mi pixel-views run the warp scan kernels on a second stream of the context beside the end of the line-per-thread
- * stage: their stage times count from where they start, and the mask's from the later of the two. */
+ * for the remaining lines), and the mask (Eq. 6).  When the line-per-thread kernels run (line_max_runs >= 1), calls of
+ * up to 64 Mi pixel-views run the warp scan kernels on a second stream of the context beside the end of the
+ * line-per-thread stage: their stage times count from where they start, and the mask's from the later of the two. */
 #define OCC_NUM_STAGES 6
 
 /* enable != 0: later occ_detect calls record a CUDA event before and after each stage, so that

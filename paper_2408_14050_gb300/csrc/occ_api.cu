@@ -217,11 +217,11 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         return OCC_ERR_CUDA;
     const int lgrid = sc.sms * sc.tuning.line_blocks_per_sm;
     if (lines && launch_scan_lines(a, lgrid, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
-    // When the line kernels keep lines of two macro-runs, k_scan_lines has flagged every line the warp kernels take,
-    // and the merge kernel and the warp kernels only add to O and the statistics: in calls below the size where the
-    // line kernel takes its chunks from a counter, the merge kernel's few lines per warp leave it latency-bound, and
-    // the warp kernels run beside it on the side stream.  Larger calls keep every multiprocessor busy on their own.
-    const bool fork = side && side->st && lines && a.line_max_runs >= 2 && !a.line_dyn;
+    // k_scan_lines has flagged every line the warp kernels take, and the merge kernel and the warp kernels only add
+    // to O and the statistics: in calls below the size where the line kernel takes its chunks from a counter, the
+    // merge kernel's few batches per warp leave it latency-bound, and the warp kernels run beside it on the side
+    // stream.  Larger calls keep every multiprocessor busy on their own.
+    const bool fork = side && side->st && lines && !a.line_dyn;
     if (forked) *forked = fork;
     cudaStream_t wst = st;
     if (fork) {
