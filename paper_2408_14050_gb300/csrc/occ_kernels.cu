@@ -12,8 +12,9 @@
 //   k_scan_lines  one thread per scan line, every line once as one stream through a one-slot buffer: Eq. 4
 //                 positions and gathers, the warp W = G - V, the sort, the neighbour test of Eq. 5 and the
 //                 accumulation into O (Eq. 6); a line that turns out to need more lists itself for k_merge_lines.
-//   k_merge_lines one thread per listed line: the stream again with negated counts (which takes its partial counts
-//                 back), then the two-buffer merge for lines of two macro-runs; longer lines are flagged for k_scan.
+//   k_merge_lines one thread per list entry, two kinds of independent work items: the two-buffer merge of a line of
+//                 two macro-runs, and the stream of a broken line again with negated counts (which takes its
+//                 partial counts back); longer lines are flagged for k_scan by k_scan_lines.
 //   k_scan        one warp per scan line (any line, any N): the same steps with the sort as a merge of the line's
 //                 monotone runs or, for many runs, a counting sort by W bucket.
 //   k_mask        M = (O > 0) (Eq. 6).
@@ -477,7 +478,8 @@ __global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Args a)
 //     The lane then looks for a third macro-run in the rest of the line, without counting, in the steps it would
 //     otherwise wait for the rest of its warp; lines of more than two macro-runs are flagged for the warp kernel.
 //   k_merge_lines (listed lines): the same stream with negated counts up to the same point takes the partial counts
-//     back; a line of two macro-runs goes through two one-slot buffers merged by (W, k).
+//     back; a line of two macro-runs also goes, as a separate work item, through two one-slot buffers merged by
+//     (W, k).
 
 constexpr int kLineThreads = 256;
 
