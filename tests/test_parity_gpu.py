@@ -252,22 +252,34 @@ def test_repeat_is_deterministic(ctx):
     assert a["stats"] == b["stats"]
 
 
-def test_profiled_call_times_its_stages(ctx):
+@pytest.mark.parametrize("runs", [2, 1])
+def test_profiled_call_times_its_stages(runs):
     # With profiling on, a call records its stage boundaries; the warp kernels run on the context's second stream
-    # beside the merge kernel and their stages count from where they start.  The results do not change.
+    # beside the merge kernel (whichever lines the line kernel keeps) and their stages count from where they start.
+    # The results do not change, and they are the oracle's.
     D = scenes.array_3x3(frame=1, H=540, W=960).frames[0]
     views = scenes.views_3x3()
-    plain = run_gpu(ctx, D, views, both_params()[1])
-    with pytest.raises(occ.OccError):
-        occ.occ_get_timings(ctx)                  # no profiled call yet
-    occ.occ_set_profiling(ctx, True)
+    c = occ.occ_create(0, max_pixels=D.size, max_views=len(views))
     try:
-        prof = run_gpu(ctx, D, views, both_params()[1])
-        t = occ.occ_get_timings(ctx)
+        occ.occ_set_tuning(c, {"line_max_runs": runs, "line_blocks_per_sm": 3, "warp_lines_per_block": 8})
+        plain = run_gpu(c, D, views, both_params()[1])
+        with pytest.raises(occ.OccError):
+            occ.occ_get_timings(c)                # no profiled call yet
+        occ.occ_set_profiling(c, True)
+        try:
+            prof = run_gpu(c, D, views, both_params()[1])
+            t = occ.occ_get_timings(c)
+        finally:
+            occ.occ_set_profiling(c, False)
     finally:
-        occ.occ_set_profiling(ctx, False)
+        c.close()
     np.testing.assert_array_equal(prof["O"], plain["O"])
     np.testing.assert_array_equal(prof["M"], plain["M"])
+    po = both_params()[0]
+    for v, (a, r) in enumerate(views):
+        Oo, Mo, _ = oracle.detect_view(D, a, r, po)
+        np.testing.assert_array_equal(plain["O"][v], Oo, err_msg=f"O view {v}")
+        np.testing.assert_array_equal(plain["M"][v], Mo, err_msg=f"M view {v}")
     assert set(t) == set(occ.STAGES)
     assert all(v >= 0.0 for v in t.values()), t
     assert t["scan_lines"] > 0.0 and t["candidates"] > 0.0 and t["mask"] > 0.0, t
