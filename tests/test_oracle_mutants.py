@@ -4,7 +4,9 @@
 Each mutant is a mistake a reader of Section 3 could make: the sign of the warp, the direction of the beta test,
 swapped gradient components, a backward difference, Eq. 3 without its factor 2, floor instead of nearest rounding
 in Eq. 4, a neighbour window one short, the tie order of the sort, non-strict thresholds, h rounded down, clamping
-instead of dropping samples outside the image, cos/sin swapped, and Eq. 6 overwriting instead of accumulating.
+instead of dropping samples outside the image, cos/sin swapped, Eq. 6 overwriting instead of accumulating, and, in
+the backward warp of the registration step (Section 1), the wrong neighbour row or swapped horizontal / vertical
+interpolation weights.
 """
 import os
 import shutil
@@ -33,6 +35,10 @@ MUTANTS = {
                        "if (rx < 0) rx = 0; if (ry < 0) ry = 0; if (rx > W - 1) rx = W - 1; if (ry > H - 1) ry = H - 1;"),
     "cos_sin_swap": ("float ty = s * g;", "float ty = c * g;"),
     "mask_overwrites": ("O[srt[i].pix] += o;", "if (o) O[srt[i].pix] = o;"),
+    "warp_wrong_neighbour_row": ("int64_t y1 = y0 + 1 < H ? y0 + 1 : y0;", "int64_t y1 = y0 > 0 ? y0 - 1 : y0;"),
+    "warp_fx_fy_swap": ("out[i] = top + fy * (bot - top);", "out[i] = top + fx * (bot - top);"),
+    "warp_weights_swap": ("float top = i00 + fx * (i01 - i00);\n            float bot = i10 + fx * (i11 - i10);",
+                          "float top = i00 + fy * (i01 - i00);\n            float bot = i10 + fy * (i11 - i10);"),
 }
 
 

@@ -454,6 +454,66 @@ def test_warp_half_pixel_is_the_mean_and_mask_zeroes():
     assert out[2, 3] == 0 and out[2, 2] == exp[2, 2]
 
 
+def test_warp_vertical_half_pixel_is_the_mean_of_two_rows():
+    # d = 0.5 at alpha = 90: the center pixel (x, y) takes the peripheral image at (x, y - 0.5), the mean of rows
+    # y - 1 and y (fy = 0.5, fx = 0); at alpha = 270 it takes (x, y + 0.5), the mean of rows y and y + 1.  Rows whose
+    # position leaves [0, H - 1] give 0.  Integer image values keep every operation exact.
+    H, W = 7, 5
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 1000, (H, W)).astype(np.float32)
+    D = np.full((H, W), 0.5, np.float32)
+    mean = (img[:-1].astype(np.float64) + img[1:].astype(np.float64)) / 2
+    exp = np.zeros((H, W))
+    exp[1:] = mean
+    np.testing.assert_array_equal(oracle.warp_view(D, 90.0, 1.0, img), exp)
+    exp = np.zeros((H, W))
+    exp[:-1] = mean
+    np.testing.assert_array_equal(oracle.warp_view(D, 270.0, 1.0, img), exp)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_warp_diagonal_integer_shift(k):
+    # alpha = 45 degrees with the binary32 disparity d whose product fl(fl(cos 45) * d) is exactly the integer k: the
+    # center pixel (x, y) takes the peripheral pixel (x - k, y - k) exactly, on both axes at once.
+    c, s = oracle.direction(45.0)
+    assert c == s
+    d = np.float32(k * np.sqrt(2.0))
+    while np.float32(c * d) != np.float32(k):
+        d = np.nextafter(d, np.float32(np.inf) if np.float32(c * d) < k else np.float32(-np.inf))
+    H, W = 9, 11
+    img = np.arange(H * W, dtype=np.float32).reshape(H, W) * 3 + 1
+    out = oracle.warp_view(np.full((H, W), d, np.float32), 45.0, 1.0, img)
+    exp = np.zeros_like(img)
+    exp[k:, k:] = img[:-k, :-k]
+    np.testing.assert_array_equal(out, exp)
+
+
+@pytest.mark.parametrize("alpha,ratio", [(30.0, 1.0), (112.5, 1.7), (200.0, 1.0), (300.0, 2.25)])
+def test_warp_of_a_linear_ramp_is_the_ramp_at_the_source_position(alpha, ratio):
+    # Bilinear interpolation reproduces a linear function exactly, so warping the ramp I = a x + b y + c0 gives
+    # a sx + b sy + c0 at the source position (sx, sy) = (x - cos(alpha) fl(r D), y - sin(alpha) fl(r D)) of every
+    # pixel inside the image, up to one rounding per operation.  a != b, so swapped fx / fy weights or a wrong
+    # neighbour row or column show; fractional D puts fx and fy anywhere in [0, 1).
+    H, W = 12, 14
+    a, b, c0 = 0.75, -1.25, 40.0
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = (a * xx + b * yy + c0).astype(np.float32)
+    rng = np.random.default_rng(int(alpha))
+    D = rng.uniform(0.0, 3.0, (H, W)).astype(np.float32)
+    cs, sn = oracle.direction(alpha)
+    d = (np.float32(ratio) * D).astype(np.float32)
+    sx = (xx.astype(np.float32) - (cs * d).astype(np.float32)).astype(np.float32)
+    sy = (yy.astype(np.float32) - (sn * d).astype(np.float32)).astype(np.float32)
+    inside = (sx >= 0) & (sx <= W - 1) & (sy >= 0) & (sy <= H - 1)
+    assert 0.4 * H * W < inside.sum() < H * W
+    frac_y = sy[inside] - np.floor(sy[inside])
+    assert (frac_y > 0.1).sum() > 20
+    out = oracle.warp_view(D, alpha, ratio, img)
+    exp = np.where(inside, a * sx.astype(np.float64) + b * sy.astype(np.float64) + c0, 0.0)
+    np.testing.assert_allclose(out, exp, rtol=0, atol=1e-4)
+    assert (out[~inside] == 0).all()
+
+
 def test_median_signed_zero_and_nonfinite():
     a = np.full((2, 3), -0.0, np.float32)
     b = np.full((2, 3), 0.0, np.float32)
