@@ -233,8 +233,8 @@ int occ_get_timings(occ_ctx* ctx, float* ms, int32_t n);
  * shares that array and overwrites it, clearing first what must start at zero; two calls that may run at the same
  * time on the GPU (different streams, or different host threads) race on it and give wrong results, so serialise
  * them (one stream).  The first call on a device also looks up the array's device address and sets the kernels'
- * shared-memory limits for that device (once, under a lock, with that device current): make that first call before
- * any stream capture.
+ * shared-memory limits for that device (under a lock, with that device current; a set-up that fails is tried again
+ * by the next call): make that first call before any stream capture.
  *
  * Arguments are those of occ_detect on the current CUDA device (D, M, O device pointers, views and p host), except:
  * O is required; there are no E / A outputs; status (device int32, or NULL) receives, in stream order, 0 when the

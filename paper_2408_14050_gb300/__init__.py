@@ -219,6 +219,31 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _check_map(D):
+    """D: float32 [H][W] with unit column stride."""
+    import torch
+    if not isinstance(D, torch.Tensor) or D.dtype != torch.float32 or D.dim() != 2 or D.stride(1) != 1:
+        raise ValueError("D must be a float32 tensor [H][W] with unit column stride")
+
+
+def _check_outputs(D, specs):
+    """Every given (tensor, dtype, shape): that dtype and shape, contiguous; then D on the current CUDA device and
+    every tensor on D's device.  The kernels write shape-many elements, so a smaller buffer would be written past
+    its end.  Shapes and dtypes are checked before devices, so that these errors show without a GPU too."""
+    import torch
+    for t, dt, shape in specs:
+        if t is None:
+            continue
+        if t.dtype != dt or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError(f"output must be a contiguous {dt} tensor of shape {tuple(shape)}, "
+                             f"got {t.dtype} {tuple(t.shape)}")
+    if not D.is_cuda or D.device.index != torch.cuda.current_device():
+        raise ValueError("D must be a CUDA tensor on the current device")
+    for t, _, _ in specs:
+        if t is not None and t.device != D.device:
+            raise ValueError("outputs must be CUDA tensors on D's device")
+
+
 # ---------------------------------------------------------------------------------------------------------------
 # Context and calls
 
@@ -267,17 +292,15 @@ def occ_detect(ctx: Context, D, views, params: occ_params | None = None, M=None,
     """Queue the method on device tensors.  D: float32 CUDA tensor [H][W] (row stride may exceed W).  Returns
     (M uint8 [V][H][W], O int32 [V][H][W] or None).  Output tensors are allocated when not given."""
     import torch
-    if D.dtype != torch.float32 or D.dim() != 2 or not D.is_cuda or D.stride(1) != 1:
-        raise ValueError("D must be a float32 CUDA tensor [H][W] with unit column stride")
+    _check_map(D)
     H, W = D.shape
     nv = len(views)
     if M is None:
         M = torch.empty((nv, H, W), dtype=torch.uint8, device=D.device)
     if O is None and want_O:
         O = torch.empty((nv, H, W), dtype=torch.int32, device=D.device)
-    for t, dt in ((M, torch.uint8), (O, torch.int32), (E, torch.float32), (A, torch.float32)):
-        if t is not None and (t.dtype != dt or not t.is_contiguous() or not t.is_cuda):
-            raise ValueError("outputs must be contiguous CUDA tensors of the documented dtypes")
+    _check_outputs(D, ((M, torch.uint8, (nv, H, W)), (O, torch.int32, (nv, H, W)),
+                       (E, torch.float32, (H, W)), (A, torch.float32, (H, W))))
     rc = load().occ_detect(ctx.handle, _ptr(D), H, W, D.stride(0), _views(views), nv,
                            ctypes.byref(params) if params is not None else None, _ptr(M), _ptr(O), _ptr(E), _ptr(A),
                            _stream_handle(stream))
@@ -394,9 +417,17 @@ def occ_detect_noalloc(D, views, params: occ_params | None = None, M=None, O=Non
     """occ_detect on the current CUDA device without a context and without device allocation by the library (for
     callers that cannot allocate).  D, M [V][H][W] uint8, O [V][H][W] int32 and status (int32, 1 element, or None)
     are CUDA tensors owned by the caller.  Returns the host status code; the device status lands in `status`."""
+    import torch
     if M is None or O is None:
         raise ValueError("M and O must be given: this entry point allocates nothing")
+    _check_map(D)
     H, W = D.shape
+    nv = len(views)
+    if status is not None and (status.dtype != torch.int32 or status.numel() < 1):
+        raise ValueError("status must be an int32 tensor of at least one element")
+    _check_outputs(D, ((M, torch.uint8, (nv, H, W)), (O, torch.int32, (nv, H, W))))
+    if status is not None and status.device != D.device:
+        raise ValueError("status must be on D's device")
     return int(load().occ_detect_noalloc(_ptr(D), H, W, D.stride(0), _views(views), len(views),
                                          ctypes.byref(params) if params is not None else None, _ptr(M), _ptr(O),
                                          _ptr(status), _stream_handle(stream)))

@@ -1,10 +1,10 @@
 // occ_noalloc.cu -- occ_detect_noalloc: the detection of occ_detect for callers that must not allocate device
 // memory (see include/occ.h).  Its scratch is one file-scope device array, sized once at build time; no call here
 // allocates or frees anything.
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
-#include <functional>
 #include <mutex>
 
 #include "occ_internal.cuh"
@@ -38,24 +38,23 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 
 struct DeviceSetup {
-    std::once_flag once;
-    cudaError_t err = cudaErrorInitializationError;
+    std::mutex mu;
+    std::atomic<bool> done{false};   // set only after a set-up that succeeded; a failed one is tried again next call
     Scratch sc{};
 };
 
 DeviceSetup g_setup[kMaxDevices];
 
-// Runs once per device, with that device current: the device address of the scratch array, the shared-memory opt-ins
-// of the kernels and their persistent grid sizes.
-void setup_device(DeviceSetup& s)
+// Runs under the device's lock, with that device current, until it succeeds once: the device address of the
+// scratch array, the shared-memory opt-ins of the kernels and their persistent grid sizes.
+cudaError_t setup_device(DeviceSetup& s)
 {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e == cudaSuccess) e = scratch_grids(s.sc);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        s.err = e;
-        return;
+        return e;
     }
     unsigned char* p = static_cast<unsigned char*>(ptr);
     Scratch& sc = s.sc;
@@ -74,7 +73,7 @@ void setup_device(DeviceSetup& s)
     sc.cand_entries = OCC_NOALLOC_MAX_PIXEL_VIEWS;
     sc.max_frames = 1;
     sc.max_views = OCC_MAX_VIEWS;
-    s.err = cudaSuccess;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -105,8 +104,13 @@ extern "C" int occ_detect_noalloc(const float* D, int32_t H, int32_t W, int64_t 
         return OCC_ERR_CUDA;
     }
     DeviceSetup& s = g_setup[dev];
-    std::call_once(s.once, setup_device, std::ref(s));
-    if (s.err != cudaSuccess) return OCC_ERR_CUDA;
+    if (!s.done.load(std::memory_order_acquire)) {
+        std::lock_guard<std::mutex> lock(s.mu);
+        if (!s.done.load(std::memory_order_relaxed)) {
+            if (setup_device(s) != cudaSuccess) return OCC_ERR_CUDA;
+            s.done.store(true, std::memory_order_release);
+        }
+    }
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     // run_frames clears the header, statistics, status and line flags this call uses; the lists need no clearing.

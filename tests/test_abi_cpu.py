@@ -104,3 +104,45 @@ def test_invalid_arguments_rejected_before_any_device_work():
     v[0].ratio = float("nan")
     assert lib.occ_warp_views(fake, 4, 4, 0, v, 1, imgs, 0, None, fake, None) == occ.OCC_ERR_INVALID_ARG
     lib.occ_destroy(None)
+
+
+def test_wrappers_reject_wrong_dtypes_and_shapes_before_calling_the_library():
+    """The kernels write V*H*W elements of M and O: the bindings refuse buffers of another shape or dtype (and D of
+    another dtype or layout) with ValueError before anything reaches the library.  Shapes are checked before the
+    device, so CPU tensors show these errors."""
+    torch = pytest.importorskip("torch")
+    H, W, nv = 6, 9, 2
+    views = [(0.0, 1.0), (90.0, 1.0)]
+    D = torch.zeros((H, W), dtype=torch.float32)
+    M = torch.zeros((nv, H, W), dtype=torch.uint8)
+    O = torch.zeros((nv, H, W), dtype=torch.int32)
+    st = torch.zeros(1, dtype=torch.int32)
+    bad = [
+        dict(D=D.double()),
+        dict(D=torch.zeros((W, H), dtype=torch.float32).t()),          # unit row stride, not column stride
+        dict(D=D[None]),
+        dict(M=torch.zeros((H, W), dtype=torch.uint8)),                # one view's plane for two views
+        dict(M=M.to(torch.int32)),
+        dict(O=torch.zeros((nv, H, W - 1), dtype=torch.int32)),
+        dict(O=O.to(torch.int64)),
+        dict(O=torch.zeros((nv, W, H), dtype=torch.int32).transpose(1, 2)),
+        dict(status=torch.zeros(1, dtype=torch.int64)),
+        dict(status=torch.zeros(0, dtype=torch.int32)),
+    ]
+    for case in bad:
+        args = dict(D=D, M=M, O=O, status=st)
+        args.update(case)
+        with pytest.raises(ValueError):
+            occ.occ_detect_noalloc(args["D"], views, None, M=args["M"], O=args["O"], status=args["status"])
+    with pytest.raises(ValueError):
+        occ.occ_detect_noalloc(D, views, None, M=None, O=O)
+    for case in bad[:8]:
+        args = dict(D=D, M=M, O=O)
+        args.update(case)
+        with pytest.raises(ValueError):
+            occ.occ_detect(None, args["D"], views, None, M=args["M"], O=args["O"])
+    # Right shapes and dtypes, but on the CPU: refused for the device.
+    with pytest.raises(ValueError, match="CUDA"):
+        occ.occ_detect_noalloc(D, views, None, M=M, O=O, status=st)
+    with pytest.raises(ValueError, match="CUDA"):
+        occ.occ_detect(None, D, views, None, M=M, O=O)
