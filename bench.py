@@ -10,8 +10,12 @@ noise sigma 0.25) standing in for the paper's scenes.
   python bench.py [--gpus N] [--steps K] [--warmup W]          # this library (CUDA kernels through the C ABI)
   python bench.py --impl reference [--steps K] [--warmup W]     # the CPU oracle on the host cores
 
-With N > 1 the script runs under torchrun, one process per GPU; every rank runs its own frames (no data-path
-collective; weak scaling) and the slowest rank's time is reported.  Rank 0 prints one JSON line.
+With N > 1 the script runs one process per GPU: started without torchrun's environment it starts itself again under
+torch.distributed.run (127.0.0.1, N processes); every rank runs its own frames (no data-path collective; weak scaling)
+and the slowest rank's time is reported.  Rank 0 prints one JSON line.  --dry-run goes through the same launch and
+reduction over a gloo group without touching a GPU (each rank times a fixed host-side wait).
+
+  python bench.py --probe fusion|proposer     # a few launches of the kernels beside the detection, for ncu -k ...
 """
 from __future__ import annotations
 
@@ -60,6 +64,12 @@ def parse():
                     help="pixel recall the skip threshold is calibrated for on held-out frames")
     ap.add_argument("--learned-eval-frames", type=int, default=64,
                     help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="launch and reduce over ranks (gloo) without a GPU; prints the JSON line of that run")
+    ap.add_argument("--probe", choices=["fusion", "proposer"], default=None,
+                    help="run a few launches of the median fusion and backward warp (fusion) or of the learned "
+                         "proposer's forward and training step (proposer) on bench-sized inputs, then exit "
+                         "(for profiling with ncu -k)")
     return ap.parse_args()
 
 
@@ -697,9 +707,92 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def relaunch_under_torchrun(args) -> int:
+    """--gpus N > 1 started as a plain process: start N ranks of this script under torch.distributed.run (one node,
+    127.0.0.1, a free port) and return their exit status."""
+    import socket
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def run_dry(args):
+    """The multi-rank launch and timing reduction without a GPU: every rank waits a fixed time per step on the host,
+    the slowest rank's time is taken over a gloo group, rank 0 prints the line.  No kernel runs."""
+    import torch.distributed as dist
+
+    from paper_2408_14050_gb300 import shard
+    rank, world, _ = dist_env()
+    if world > 1:
+        dist.init_process_group("gloo")
+    units = 1920 * 1080 * 8
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        time.sleep(0.001 * (1 + rank))
+    t = shard.max_over_ranks(time.perf_counter() - t0)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": round(args.steps * world * units / t / 1e6, 1), "unit": UNIT,
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": round(t / args.steps * 1e3, 4), "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "none (dry run)",
+                          "config": {"workload": "dry run: host-side waits, no GPU",
+                                     "parallelism": f"replicas{world}" if world > 1 else "single"},
+                          "dry_run": True, "gpu_launches": 0}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_probe(args):
+    """A few launches of the kernels beside the detection on bench-sized inputs, for ncu -k: the median fusion of 8
+    stereo maps and the masked backward warp of 8 views on the 1920x1080 3x3-array frame (fusion), or the learned
+    tile proposer's forward pass on 8 frames of 256x192 three times and two training steps (proposer)."""
+    import torch
+
+    import paper_2408_14050_gb300 as occ
+    views = scenes.views_3x3()
+    if args.probe == "fusion":
+        f = scenes.array_3x3(frame=0).frames[0]
+        H, W = f.shape
+        maps = [torch.from_numpy(m).cuda() for m in scenes.stereo_maps(f, 8, seed=3)]
+        imgs = [torch.from_numpy(i).cuda() for i in scenes.peripheral_images(H, W, 8, seed=4)]
+        D = torch.empty((H, W), device="cuda")
+        with occ.occ_create(0, max_pixels=H * W, max_views=8) as ctx:
+            M, _ = occ.occ_detect(ctx, torch.from_numpy(f).cuda(), views)
+        out = torch.empty((8, H, W), device="cuda")
+        for _ in range(3):
+            occ.occ_fuse_median(maps, D=D)
+        for _ in range(3):
+            occ.occ_warp_views(D, views, imgs, M=M, out=out)
+    else:
+        Dn = torch.from_numpy(scenes.proposer_frames(8, 192, 256, seed=5)).cuda()
+        net = occ.Net(0, max_pixels=8 * 192 * 256, max_views=8)
+        net.set_params(scenes.net_init(1))
+        for _ in range(3):
+            net.forward(Dn, views)
+        labels = torch.ones((8, 8, 6, 8), dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            net.loss_grad(Dn, views, labels)
+        torch.cuda.synchronize()
+        if occ.occ_net_status() != occ.OCC_OK:
+            raise RuntimeError("a tensor-core wait of the network expired")
+        net.close()
+    torch.cuda.synchronize()
+    print(f"probe {args.probe} ok")
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_under_torchrun(args))
+    if args.probe:
+        run_probe(args)
+    elif args.dry_run:
+        run_dry(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

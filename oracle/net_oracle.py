@@ -178,3 +178,49 @@ def loss_and_grads(params, D, views, labels, pos_weight: float = 1.0, dtype=np.f
                 dX = dX + shifted(dpre, -dy, -dx) @ wb[:, t, :]
             dpre = rnd((dX * (X > 0)).astype(dtype))
     return loss, pack(grads, dWe, dbe, db0, dtype)
+
+
+def grad_magnitudes(params, D, views, labels, pos_weight: float = 1.0):
+    """For every gradient element, the sum of the absolute values of the terms that loss_and_grads adds up for it:
+    the same chain rule, in float64, with every factor replaced by its absolute value and every ReLU gate open.
+
+    A parity test bounds the difference between two evaluations of the gradient that round differently (other
+    summation order, a bf16 rounding that lands on the other side) by a small multiple of 2^-8 times this sum, element
+    by element: each of the roundings on a path through the network moves a term by at most that fraction of its
+    magnitude, and a gate that flips drops or adds a term that this sum already counts."""
+    layers, We, be, b0 = unpack(params, np.float64)
+    fw = forward(params, D, views, np.float64, rounding=True)
+    acts, g, z, s, enc = fw["acts"], fw["g"], fw["z"], fw["s"], fw["enc"]
+    y = np.asarray(labels, dtype=np.float64)
+    V, H, W = z.shape
+    n = s.size
+    sig = 1.0 / (1.0 + np.exp(-s))
+    ds = np.abs(pos_weight * y * (sig - 1)) / n + np.abs((1 - y) * sig) / n
+    dz = np.zeros_like(z)
+    for i, j, ys, xs in tiles(H, W):
+        zt = z[:, ys, xs]
+        e = np.exp(zt - zt.reshape(V, -1).max(axis=1)[:, None, None])
+        dz[:, ys, xs] = ds[:, i, j][:, None, None] * e / e.reshape(V, -1).sum(axis=1)[:, None, None]
+    f = acts[-1]
+    ag = np.abs(g)
+    df = np.einsum("vyx,vc->yxc", dz, ag)
+    dg = np.einsum("vyx,yxc->vc", dz, np.abs(f))
+    dWe = dg.T @ np.abs(enc)
+    dbe = dg.sum(axis=0)
+    db0 = dz.sum()
+    grads = [None] * len(layers)
+    dpre = df
+    for li in range(len(layers) - 1, -1, -1):
+        w, _ = layers[li]
+        X = np.abs(acts[li])
+        dW = np.zeros_like(w)
+        for t, (dy, dx) in enumerate(TAPS):
+            dW[:, t, :] = np.einsum("yxo,yxi->oi", dpre, shifted(X, dy, dx))
+        grads[li] = (dW, dpre.sum(axis=(0, 1)))
+        if li > 0:
+            wa = np.abs(bf16(w.astype(np.float32))).astype(np.float64)
+            dX = np.zeros_like(X)
+            for t, (dy, dx) in enumerate(TAPS):
+                dX = dX + shifted(dpre, -dy, -dx) @ wa[:, t, :]
+            dpre = dX
+    return pack(grads, dWe, dbe, db0, np.float64)

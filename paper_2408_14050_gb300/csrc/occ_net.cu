@@ -427,9 +427,16 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
     }
     __syncthreads();
-    if (tid == 0) {
-        if ((int)blockIdx.x < nblk) load_halo(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < nblk) load_halo(blockIdx.x + gridDim.x, 1);
+    // Halo loads issued into / waited for in each buffer (every thread keeps the same counts: the conditions are
+    // uniform).  A buffer is loaded again only after its previous load was waited for, so at most one is in flight.
+    int issued[2] = {0, 0}, consumed[2] = {0, 0};
+    if ((int)blockIdx.x < nblk) {
+        if (tid == 0) load_halo(blockIdx.x, 0);
+        issued[0]++;
+    }
+    if ((int)(blockIdx.x + gridDim.x) < nblk) {
+        if (tid == 0) load_halo(blockIdx.x + gridDim.x, 1);
+        issued[1]++;
     }
     for (int u = tid; u < COUT * KC; u += kConvThreads) {
         const int nrow = u % COUT, kc = u / COUT;
@@ -452,6 +459,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
         ok = mbar_wait_bounded(&s_bar[buf], (uint32_t)((it >> 1) & 1));
         ok = __syncthreads_and(ok);
         if (!ok) break;
+        consumed[buf]++;
         tc_after_sync();
         if (tid == 0) {
             constexpr uint32_t idesc = idesc_bf16(128, COUT);
@@ -473,7 +481,10 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
         tc_after_sync();
         if (!ok) break;
         // The halo buffer is free again: fetch the block after next into it.
-        if (tid == 0 && b + 2 * (int)gridDim.x < nblk) load_halo(b + 2 * gridDim.x, buf);
+        if (b + 2 * (int)gridDim.x < nblk) {
+            if (tid == 0) load_halo(b + 2 * gridDim.x, buf);
+            issued[buf]++;
+        }
 
         float acc[COUT];
 #pragma unroll
@@ -516,7 +527,13 @@ __global__ void __launch_bounds__(kConvThreads) k_conv_tma(const __grid_constant
         tc_before_sync();
         __syncthreads();
     }
-    if (!ok && tid == 0) atomicExch(&g_net_error, 1);
+    if (!ok && tid == 0) {
+        atomicExch(&g_net_error, 1);
+        // Left early: wait (bounded) for the halo loads still in flight, so that no bulk copy writes into this
+        // CTA's shared memory after it exits.  A load's completion is phase consumed[buf] of its barrier.
+        for (int q = 0; q < 2; q++)
+            if (issued[q] > consumed[q]) mbar_wait_bounded(&s_bar[q], (uint32_t)(consumed[q] & 1));
+    }
     tc_before_sync();
     __syncthreads();
     if (warp == 0) tmem_free(tmem, 32);

@@ -120,3 +120,35 @@ def test_batch_argument_checks(ctx):
     big = torch.zeros((4096, 4096), dtype=torch.float32, device="cuda")
     with pytest.raises(occ.OccError):                 # 2 x 16.8 M pixels > max_pixels
         occ.occ_detect_batched(ctx, [big, big], [(0.0, 1.0)])
+
+
+def test_batch_of_the_mixed_resolutions_against_the_oracle(ctx):
+    """One batch holding a 4096x2160, a 640x480 and a 1280x720 map of the mixed-resolution recipe (disparity 0-64,
+    eight views).  The two smaller frames are compared with the oracle whole; the 4096x2160 frame on a 24x24 window
+    per view, with the oracle run on every candidate whose scan line can reach the window (all of the window's O)."""
+    from test_parity_gpu import reach_mask
+    wl = scenes.mixed_batch(n_frames=3, sizes=[(2160, 4096), (480, 640), (720, 1280)], config=33)
+    views = wl.views
+    assert sorted(f.shape for f in wl.frames) == [(480, 640), (720, 1280), (2160, 4096)]
+    Ds = [torch.from_numpy(f).cuda() for f in wl.frames]
+    Ms, Os = occ.occ_detect_batched(ctx, Ds, views)
+    assert occ.occ_get_status(ctx) == occ.OCC_OK
+    po = oracle.default_params()
+    rng = np.random.default_rng(33)
+    for D, M, O in zip(wl.frames, Ms, Os):
+        H, W = D.shape
+        O_np, M_np = O.cpu().numpy(), M.cpu().numpy()
+        np.testing.assert_array_equal(M_np, (O_np > 0).astype(np.uint8))
+        for v, (a, r) in enumerate(views):
+            if H * W <= 1280 * 720:
+                Oo, Mo, _ = oracle.detect_view(D, a, r, po)
+                np.testing.assert_array_equal(O_np[v], Oo, err_msg=f"{W}x{H} view {v}")
+                np.testing.assert_array_equal(M_np[v], Mo, err_msg=f"{W}x{H} view {v}")
+            else:
+                h = (oracle.scan_length(D, r) + 1) // 2
+                c, s = (float(t) for t in oracle.direction(a))
+                bx, by = int(rng.integers(0, W - 24)), int(rng.integers(0, H - 24))
+                box = (bx, by, bx + 24, by + 24)
+                Oo, _ = oracle.detect_view_masked(D, a, r, po, reach_mask(H, W, box, c, s, h))
+                np.testing.assert_array_equal(O_np[v][by:by + 24, bx:bx + 24], Oo[by:by + 24, bx:bx + 24],
+                                              err_msg=f"{W}x{H} view {v} alpha={a}")

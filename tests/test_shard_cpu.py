@@ -59,3 +59,24 @@ def test_two_rank_gloo_group():
     assert not set(res[0][1]) & set(res[1][1])
     assert res[0][2] == res[1][2] == 2.0                 # the slowest rank's time
     assert res[0][3] == res[1][3] == float(sum(sizes))   # all units counted once
+
+
+def test_bench_gpus_2_starts_two_ranks_and_reports_the_slowest():
+    """bench.py --gpus 2, started as a plain process, starts two ranks under torch.distributed.run; in a dry run each
+    rank waits (1 + rank) ms per step on the host and the line reports both ranks' units over the slower rank's time
+    (max over a gloo group).  No GPU is touched."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR",
+                                                            "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", "2", "--dry-run", "--steps", "20",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=300, env=env, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    line = lines[0]
+    assert line["n_gpus"] == 2 and line["dry_run"] and line["scaling"] == "weak"
+    assert line["ms_per_step"] >= 2.0                     # rank 1's wait: the slowest rank sets the time
+    assert abs(line["value"] - 2 * 1920 * 1080 * 8 / (line["ms_per_step"] / 1e3) / 1e6) / line["value"] < 1e-3
