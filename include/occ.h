@@ -184,11 +184,19 @@ int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
  *   line_blocks_per_sm   resident 256-thread blocks per multiprocessor of the line-per-thread kernel, 1 .. the
  *                        occupancy limit (default: the limit).
  *   warp_lines_per_block lines in flight per block of the one-warp-per-line kernel for lines of <= 256 samples:
- *                        4 or 8 (default 8). */
+ *                        4 or 8 (default 8).
+ *   strip_px             the strip kernel, for the views whose scan lines stay on one row, column or diagonal
+ *                        (alpha a multiple of 45 degrees) when N = 8 and no side of a frame exceeds 4096 pixels:
+ *                        one block owns a strip of adjacent such lines of about strip_px pixels, holds D_r and O of
+ *                        it in shared memory and writes O and M once.  0 turns it off (every view takes the
+ *                        candidate-list kernels above); otherwise 4096 .. OCC_STRIP_PX_MAX, a multiple of 64
+ *                        (default 6144). */
+#define OCC_STRIP_PX_MAX 16384
 typedef struct {
     int32_t line_max_runs;
     int32_t line_blocks_per_sm;
     int32_t warp_lines_per_block;
+    int32_t strip_px;
 } occ_tuning;
 
 /* Sets the tuning of later calls (NULL: the defaults).  OCC_ERR_INVALID_ARG for out-of-range fields. */

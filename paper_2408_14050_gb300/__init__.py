@@ -31,6 +31,8 @@ OCC_NUM_STAGES = 6
 STAGES = ["candidates", "scan_lines", "scan_256", "scan_1024", "scan_4096", "mask"]
 
 OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
+OCC_STRIP_PX_MAX = 16384
+STRIP_PX_DEFAULT = 6144      # default occ_tuning.strip_px
 
 OCC_MAX_FRAMES = 1024
 
@@ -67,9 +69,10 @@ class occ_view_stats(ctypes.Structure):
 
 
 class occ_tuning(ctypes.Structure):
-    """Mapping of the scan work: line_max_runs (0, 1, 2), line_blocks_per_sm, warp_lines_per_block (4, 8)."""
+    """Mapping of the scan work: line_max_runs (0, 1, 2), line_blocks_per_sm, warp_lines_per_block (4, 8), strip_px
+    (0 = no strip kernel, else 4096 .. OCC_STRIP_PX_MAX pixels per strip, a multiple of 64)."""
     _fields_ = [("line_max_runs", ctypes.c_int32), ("line_blocks_per_sm", ctypes.c_int32),
-                ("warp_lines_per_block", ctypes.c_int32)]
+                ("warp_lines_per_block", ctypes.c_int32), ("strip_px", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -485,7 +488,7 @@ def occ_set_tuning(ctx: Context, tuning: dict | None = None):
     t = None
     if tuning is not None:
         t = occ_tuning(int(tuning["line_max_runs"]), int(tuning["line_blocks_per_sm"]),
-                       int(tuning["warp_lines_per_block"]))
+                       int(tuning["warp_lines_per_block"]), int(tuning.get("strip_px", STRIP_PX_DEFAULT)))
     rc = load().occ_set_tuning(ctx.handle, ctypes.byref(t) if t is not None else None)
     if rc != OCC_OK:
         raise OccError(rc, "occ_set_tuning")

@@ -1,5 +1,6 @@
-"""Autotuner of the mapping of the scan work (occ_tuning): how many macro-runs the line-per-thread kernel takes
-(0, 1, 2), its resident blocks per multiprocessor, and the warps per block of the one-warp-per-line kernel.
+"""Autotuner of the mapping of the scan work (occ_tuning): the strip kernel's tile shape (pixels per strip, hence
+lines per strip and blocks per multiprocessor; or no strip kernel), how many macro-runs the line-per-thread kernel
+takes (0, 1, 2), its resident blocks per multiprocessor, and the warps per block of the one-warp-per-line kernel.
 
 Every choice gives bit-identical M and O; the tuner times each candidate with CUDA events on sample frames of the
 caller's workload, keeps the fastest, and caches it in a JSON file keyed by device and workload class (size class of
@@ -25,23 +26,38 @@ def scan_bucket(L: int) -> str:
 
 
 def angle_class(views) -> str:
-    axial = all(abs((a % 90.0)) < 1e-9 or abs((a % 90.0) - 90.0) < 1e-9 for a, _ in views)
-    return "axial" if axial else "general"
+    def multiple(a, m):
+        r = a % m
+        return abs(r) < 1e-9 or abs(r - m) < 1e-9
+    if all(multiple(a, 90.0) for a, _ in views):
+        return "axial"
+    return "octant" if all(multiple(a, 45.0) for a, _ in views) else "general"
 
 
 def workload_key(device_name: str, shapes, views, L: int, N: int) -> str:
     return f"{device_name}|{size_class(shapes)}|{scan_bucket(L)}|{angle_class(views)}|N{N}"
 
 
+STRIP_SHAPES = (4096, 6144, 8192, 12288)   # pixels per strip of the strip kernel
+
+
 def candidates(max_line_bps: int):
-    out = []
+    """Strip shapes with the default list-path mapping, then every list-path mapping without the strip kernel."""
+    out = [{"line_max_runs": 2, "line_blocks_per_sm": max_line_bps, "warp_lines_per_block": 8, "strip_px": px}
+           for px in STRIP_SHAPES]
     for runs in (2, 1, 0):
         for bps in sorted({max_line_bps, max(1, max_line_bps - 1)}, reverse=True):
             for wpb in (8, 4):
                 if runs == 0 and bps != max_line_bps:
                     continue      # the line kernel does not run: its grid is irrelevant
-                out.append({"line_max_runs": runs, "line_blocks_per_sm": bps, "warp_lines_per_block": wpb})
+                out.append({"line_max_runs": runs, "line_blocks_per_sm": bps, "warp_lines_per_block": wpb,
+                            "strip_px": 0})
     return out
+
+
+def tuning_name(t: dict) -> str:
+    return (f"strip{t['strip_px']}_runs{t['line_max_runs']}_bps{t['line_blocks_per_sm']}"
+            f"_wpb{t['warp_lines_per_block']}")
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:
@@ -107,7 +123,7 @@ def autotune(ctx, Ds, views, params=None, reps: int = 5, cache_path: str | None 
     for t in candidates(max_bps):
         occ.occ_set_tuning(ctx, t)
         ms = _time_call(run, reps)
-        timings[f"runs{t['line_max_runs']}_bps{t['line_blocks_per_sm']}_wpb{t['warp_lines_per_block']}"] = round(ms, 4)
+        timings[tuning_name(t)] = round(ms, 4)
         if ms < best_ms:
             best, best_ms = t, ms
     occ.occ_set_tuning(ctx, best)

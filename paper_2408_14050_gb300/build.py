@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(OUT_DIR, "libocc.so")
-SOURCES = ["occ_kernels.cu", "occ_api.cu", "occ_noalloc.cu", "occ_fusion.cu", "occ_net.cu"]
+SOURCES = ["occ_kernels.cu", "occ_strip.cu", "occ_api.cu", "occ_noalloc.cu", "occ_fusion.cu", "occ_net.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

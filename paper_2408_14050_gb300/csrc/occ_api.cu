@@ -121,17 +121,43 @@ cudaError_t scratch_grids(Scratch& sc)
     if (sc.lines_bps_max < 1) sc.lines_bps_max = 1;
     for (int c = 0; c <= kNumClasses; c++)
         if (sc.scan_bps[c] < 1) sc.scan_bps[c] = 1;
+    if ((e = configure_strip()) != cudaSuccess) return e;
     sc.tuning.line_max_runs = 2;
     sc.tuning.line_blocks_per_sm = sc.lines_bps_max;
     sc.tuning.warp_lines_per_block = 8;
+    sc.tuning.strip_px = kStripPxDefault;
     return cudaSuccess;
+}
+
+// Strip family of a direction (cos, sin as occ_direction rounds them), or -1.
+int strip_family(float c, float s)
+{
+    const float q = (float)std::sqrt(0.5);
+    if (s == 0.0f && std::fabs(c) == 1.0f) return kFamRows;
+    if (c == 0.0f && std::fabs(s) == 1.0f) return kFamCols;
+    if (std::fabs(c) == q && c == s) return kFamDiag;
+    if (std::fabs(c) == q && c == -s) return kFamAnti;
+    return -1;
 }
 
 int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev,
                const SideStream* side, bool* forked)
 {
     const int nv = a.nv;
-    const bool lines = (a.N / 2) <= kLineMaxHalf && sc.tuning.line_max_runs > 0;
+    // Views whose scan lines stay on one row, column or diagonal take the strip kernel (N = 8, frames of at most
+    // kStripMaxSide a side); the others take the candidate lists.
+    bool strip_ok = sc.tuning.strip_px > 0 && a.N == 8;
+    for (int f = 0; f < nf; f++)
+        if (fr[f].H > kStripMaxSide || fr[f].W > kStripMaxSide) strip_ok = false;
+    int n_strip = 0;
+    for (int v = 0; v < nv; v++) {
+        a.view[v].fam = strip_ok ? strip_family(a.view[v].c, a.view[v].s) : -1;
+        if (a.view[v].fam >= 0) n_strip++;
+    }
+    const bool list_views = n_strip < nv;
+    a.any_list = list_views ? 1 : 0;
+    a.strip_px = n_strip ? sc.tuning.strip_px : 0;
+    const bool lines = list_views && (a.N / 2) <= kLineMaxHalf && sc.tuning.line_max_runs > 0;
     a.nf = nf;
     a.use_fb = lines ? 1 : 0;
     a.line_max_runs = sc.tuning.line_max_runs;
@@ -139,6 +165,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.plan = sc.plan;
     a.pref_all = sc.pref;
     a.pref_cls = sc.pref + (nf * nv + 1);
+    a.pref_ovf = sc.pref + (1 + kNumClasses) * (nf * nv + 1);
     a.ptab = sc.ptab;
     a.status = sc.status;
     a.line_ctr = sc.status + 1;   // the status region has room for the counters
@@ -154,7 +181,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     FrameChunk chunk;
     std::memset(&chunk, 0, sizeof(chunk));
     chunk.dst = sc.frames;
-    int64_t cand_off = 0, fb_off = 0, px_views = 0;
+    int64_t cand_off = 0, fb_off = 0, px_views = 0, strips = 0;
     bool wide = false;
     for (int f = 0; f < nf; f++) {
         FrameArg& F = chunk.f[f % kFramesPerChunk];
@@ -183,6 +210,9 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         px_views += (int64_t)F.H * F.W * nv;
         F.tiles_x = (F.W + kTile - 1) / kTile;
         F.tiles_y = (F.H + kTile - 1) / kTile;
+        F.strip0 = (uint32_t)strips;
+        for (int v = 0; v < nv; v++)
+            if (a.view[v].fam >= 0) strips += fam_strips(a.view[v].fam, F.H, F.W, a.strip_px);
         const int quads = F.H * ((F.W + 3) / 4);
         if (quads > a.max_quads) a.max_quads = quads;
         const int64_t px = (int64_t)nv * F.H * F.W;
@@ -195,7 +225,8 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     }
     if (cand_off > sc.cand_entries || (lines && fb_off > sc.fb_entries)) return OCC_ERR_INVALID_ARG;
     // The scan kernels number the candidates of a call (every frame and view) with 32-bit work items.
-    if (cand_off > (int64_t)UINT32_MAX) return OCC_ERR_CAPACITY;
+    if (cand_off > (int64_t)UINT32_MAX || strips > (int64_t)INT32_MAX) return OCC_ERR_CAPACITY;
+    a.strip_total = (uint32_t)strips;
     // Above about four 1920x1080 frames of 8 views, static chunks let warps drift over more data than L2 holds.
     a.line_dyn = px_views > (int64_t)64 * 1024 * 1024 ? 1 : 0;
 
@@ -215,6 +246,9 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
         launch_plan(a, st) != cudaSuccess || !mark(1))
         return OCC_ERR_CUDA;
+    // The strip views: O and M written once per strip; the lines of three or more macro-runs are listed for the warp
+    // kernels below, which add their counts to O and M.
+    if (n_strip && (launch_strip(a, st) != cudaSuccess || launch_plan_ovf(a, st) != cudaSuccess)) return OCC_ERR_CUDA;
     const int lgrid = sc.sms * sc.tuning.line_blocks_per_sm;
     if (lines && launch_scan_lines(a, lgrid, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
     // k_scan_lines has flagged every line the warp kernels take, and the merge kernel and the warp kernels only add
@@ -239,7 +273,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     }
     if (fork && (cudaEventRecord(side->join, side->st) != cudaSuccess || cudaStreamWaitEvent(st, side->join, 0) != cudaSuccess))
         return OCC_ERR_CUDA;
-    if (launch_mask(a, st) != cudaSuccess || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
+    if ((list_views && launch_mask(a, st) != cudaSuccess) || !mark(OCC_NUM_STAGES)) return OCC_ERR_CUDA;
     return OCC_OK;
 }
 
@@ -350,7 +384,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     const size_t sz_status = 256;
     const size_t sz_frames = align256(sizeof(FrameArg) * kMaxFrames);
     const size_t sz_plan = align256(sizeof(PlanEntry) * nfv);
-    const size_t sz_pref = align256(sizeof(uint32_t) * (1 + kNumClasses) * (nfv + 1));
+    const size_t sz_pref = align256(sizeof(uint32_t) * (1 + 2 * kNumClasses) * (nfv + 1));
     const size_t sz_tab = align256(sizeof(int32_t) * kTabLen * max_views);
     const size_t total = sz_hdr + sz_stats + sz_status + sz_frames + sz_plan + sz_pref + sz_tab;
     sc.cand_entries = ctx->cand_cap * max_views;
@@ -485,10 +519,11 @@ int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, co
 int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t)
 {
     if (!ctx) return OCC_ERR_INVALID_ARG;
-    occ_tuning d{2, ctx->sc.lines_bps_max, 8};
+    occ_tuning d{2, ctx->sc.lines_bps_max, 8, kStripPxDefault};
     if (!t) t = &d;
     if (t->line_max_runs < 0 || t->line_max_runs > 2 || t->line_blocks_per_sm < 1 ||
-        t->line_blocks_per_sm > ctx->sc.lines_bps_max || (t->warp_lines_per_block != 4 && t->warp_lines_per_block != 8))
+        t->line_blocks_per_sm > ctx->sc.lines_bps_max || (t->warp_lines_per_block != 4 && t->warp_lines_per_block != 8) ||
+        (t->strip_px != 0 && (t->strip_px < kStripMaxSide || t->strip_px > OCC_STRIP_PX_MAX || (t->strip_px & 63))))
         return OCC_ERR_INVALID_ARG;
     ctx->sc.tuning = *t;
     return OCC_OK;

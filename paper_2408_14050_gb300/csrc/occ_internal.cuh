@@ -24,7 +24,8 @@ enum : int {
     HDR_NEGMIN = 2,                  // min D, complemented encoding (atomicMax)
     HDR_COUNT = 8,                   // [kMaxViews] candidates found per view (may exceed the list capacity)
     HDR_L = HDR_COUNT + kMaxViews,   // [kMaxViews] scan length used per view (Eq. 3)
-    HDR_WORDS = HDR_L + kMaxViews,
+    HDR_OVF = HDR_L + kMaxViews,     // [kMaxViews] strip views: lines of three or more macro-runs listed for k_scan
+    HDR_WORDS = HDR_OVF + kMaxViews,
 };
 
 // Device status bits.
@@ -49,7 +50,47 @@ constexpr int kTabLen = 2 * kTabHalf + 1;
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
     int32_t ridx;    // index of r in Args::ratio
+    int32_t fam;     // strip family of the view's scan lines (kFam*), or -1: the view takes the list path
+    int32_t pad;
 };
+
+// Directions whose scan lines (Eq. 4) stay on one digital line of the frame: rows (alpha = 0, 180), columns (90, 270),
+// diagonals x - y = const (45, 225: cos = sin) and anti-diagonals x + y = const (135, 315: cos = -sin).  Along such a
+// line the sample of g lies t = round(fl(cc * g)) positions from the candidate, cc = sin(alpha) for columns and
+// cos(alpha) otherwise; for the diagonal directions this equals Eq. 4's per-coordinate rounding whenever every
+// coordinate is below kStripMaxSide (checked exhaustively for |g| <= 2047 by the tests).
+enum : int { kFamRows = 0, kFamCols = 1, kFamDiag = 2, kFamAnti = 3 };
+constexpr int kStripMaxSide = 4096;
+constexpr int kStripMaxLines = 16;   // lines of one strip (4 bits of a queue entry; the position takes 12)
+constexpr int kStripPxDefault = 6144;
+
+__host__ __device__ __forceinline__ int fam_lines(int fam, int H, int W)
+{
+    return fam == kFamRows ? H : (fam == kFamCols ? W : W + H - 1);
+}
+__host__ __device__ __forceinline__ int fam_len(int fam, int H, int W)
+{
+    return fam == kFamRows ? W : (fam == kFamCols ? H : (W < H ? W : H));
+}
+// Lines per strip: as many as fit strip_px pixels (at least one, at most kStripMaxLines).
+__host__ __device__ __forceinline__ int strip_lines(int fam, int H, int W, int strip_px)
+{
+    const int b = strip_px / fam_len(fam, H, W);
+    return b < 1 ? 1 : (b > kStripMaxLines ? kStripMaxLines : b);
+}
+__host__ __device__ __forceinline__ int fam_strips(int fam, int H, int W, int strip_px)
+{
+    const int b = strip_lines(fam, H, W, strip_px);
+    return (fam_lines(fam, H, W) + b - 1) / b;
+}
+
+// Number of (p, d) pairs with d in {-K..K}\{0} and 0 <= p+d < n, summed over p (Eq. 5's neighbour set).
+__host__ __device__ __forceinline__ unsigned long long pair_count(int n, int K)
+{
+    const long long nn = n, kk = K;
+    const long long one_side = (nn <= kk) ? nn * (nn - 1) / 2 : kk * (kk - 1) / 2 + (nn - kk) * kk;
+    return (unsigned long long)(2 * one_side);
+}
 
 // One frame of a call.
 struct FrameArg {
@@ -71,6 +112,8 @@ struct FrameArg {
     const uint8_t* prop;          // [nv][tiles_y][tiles_x]: 0 = the tile's candidates are skipped; null = none skipped
     uint8_t* hits;                // [nv][tiles_y][tiles_x]: 1 = a scan line from the tile found an occlusion; or null
     int32_t tiles_x, tiles_y;     // ceil(W / kTile), ceil(H / kTile)
+    uint32_t strip0;              // index of the frame's first strip (k_strip grid), strips of its views in order
+    int32_t pad2;
 };
 
 // Per (frame, view), written by k_plan.
@@ -109,6 +152,10 @@ struct Args {
                                     // room); zero at the start of a call
     uint32_t* merge_ctr;          // batch counter of the merge kernel, zero at the start of a call
     uint32_t brk_cap;             // entries brk holds: at least the candidates a call can have
+    int32_t any_list;             // some view takes the candidate-list path (k_edges lists its candidates)
+    int32_t strip_px;             // pixels of one strip (k_strip); 0 when no view takes the strip path
+    uint32_t strip_total;         // strips of the call
+    uint32_t* pref_ovf;           // [kNumClasses][nf * nv + 1] prefix of the strip views' listed lines per size class
 };
 
 // At most kFramesPerChunk frame records travel in the parameters of one k_frames launch (under 4 KB).
@@ -130,6 +177,12 @@ cudaError_t launch_merge_lines(const Args& a, int grid, bool wide, cudaStream_t 
 // cls = kNumClasses launches the class-0 kernel with 4-warp blocks.
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, cudaStream_t st);
+// Strip kernel (occ_strip.cu): the views with a strip family, every strip of the call; then the prefix sums of the
+// lines it listed for the warp kernels.
+cudaError_t launch_strip(const Args& a, cudaStream_t st);
+cudaError_t launch_plan_ovf(const Args& a, cudaStream_t st);
+size_t strip_smem(int strip_px);
+cudaError_t configure_strip();
 // Per-SM resident blocks of the persistent scan kernels (kNumClasses + 1 warp variants); also sets the shared-memory
 // opt-ins.
 cudaError_t configure_kernels(int* lines_blocks_per_sm, int scan_blocks_per_sm[kNumClasses + 1]);

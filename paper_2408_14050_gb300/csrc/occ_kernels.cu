@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
 
         // Eq. 1 on D_r for every distinct ratio, Eq. 2 for every view of that ratio.
         uint64_t bits[4] = {0, 0, 0, 0};
-        if (active) {
+        if (active && a.any_list) {
             for (int u = 0; u < a.nr; u++) {
                 const float r = a.ratio[u];
                 const bool one = (r == 1.0f);
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
                     pe[j] = valid[j] && (e2 >= a.e2min);
                 }
                 for (int v = 0; v < a.nv; v++) {
-                    if (a.view[v].ridx != u) continue;
+                    if (a.view[v].ridx != u || a.view[v].fam >= 0) continue;   // strip views: k_strip
                     const float c = a.view[v].c, s = a.view[v].s;
 #pragma unroll
                     for (int j = 0; j < 4; j++) {
@@ -270,10 +270,12 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
             }
         }
 
-        // O = 0 for the quad in every view (the scan kernel accumulates into it).
-        if (active) {
+        // O = 0 for the quad in every list-path view (the scan kernels accumulate into it; k_strip writes O of the
+        // strip views once).
+        if (active && a.any_list) {
             const int64_t o = (int64_t)y * W + x0;
             for (int v = 0; v < a.nv; v++) {
+                if (a.view[v].fam >= 0) continue;
                 int32_t* Ov = F.O + (int64_t)v * plane + o;
                 if (vecO && x0 + 4 <= W) {
                     *reinterpret_cast<int4*>(Ov) = make_int4(0, 0, 0, 0);
@@ -430,13 +432,6 @@ __device__ __forceinline__ int item_owner(const uint32_t* pref, int n, uint32_t 
     return lo;
 }
 
-// Number of (p, d) pairs with d in {-K..K}\{0} and 0 <= p+d < n, summed over p (Eq. 5's neighbour set).
-__device__ __forceinline__ unsigned long long pair_count(int n, int K)
-{
-    const long long nn = n, kk = K;
-    const long long one_side = (nn <= kk) ? nn * (nn - 1) / 2 : kk * (kk - 1) / 2 + (nn - kk) * kk;
-    return (unsigned long long)(2 * one_side);
-}
 
 // ------------------------------------------------------------------------------------------------------------------
 // k_tables: per view and g = -kTabHalf .. kTabHalf, the offsets round(fl(cos a * g)) and round(fl(sin a * g)) of
@@ -1203,8 +1198,11 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ScanSmem<CAP>& S = reinterpret_cast<ScanSmem<CAP>*>(smem_raw)[warp];
     const int nfv = a.nf * a.nv;
+    // Work items: the candidates of the list-path views in this size class, then the lines k_strip listed for it.
     const uint32_t* pref = a.pref_cls + (int64_t)cls * (nfv + 1);
-    const uint32_t total = pref[nfv];
+    const uint32_t* pref1 = a.pref_ovf + (int64_t)cls * (nfv + 1);
+    const uint64_t total0 = pref[nfv];
+    const uint64_t total = total0 + (a.strip_px ? pref1[nfv] : 0u);
     if (total == 0) return;
     const int half = a.N >> 1;
     const float beta = a.beta, zeta = a.zeta;
@@ -1224,7 +1222,11 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         bool want = mine < total;
         int my_i = 0;
         uint32_t my_idx = 0;
-        if (want) {
+        if (want && mine >= total0) {
+            const uint32_t m1 = (uint32_t)(mine - total0);
+            my_i = item_owner(pref1, nfv, m1);
+            my_idx = m1 - pref1[my_i];
+        } else if (want) {
             my_i = item_owner(pref, nfv, (uint32_t)mine);
             my_idx = (uint32_t)(mine - pref[my_i]);
             if (a.use_fb) {
@@ -1492,8 +1494,11 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
             cnt_own[q] = o;
         }
         __syncwarp();
-        // Eq. 6: add every sample's count to the occlusion sum of its pixel, found again from its k (Eq. 4).
+        // Eq. 6: add every sample's count to the occlusion sum of its pixel, found again from its k (Eq. 4).  A strip
+        // view's O is final apart from these lines, and k_mask does not run for it: M is set here.
         int32_t* Ov = F.O + (int64_t)v * F.H * F.W;
+        uint8_t* Mv = F.M + (int64_t)v * F.H * F.W;
+        const bool strip_view = va.fam >= 0;
         bool hit = false;
         for (int q = lane; q < n; q += 32) {
             const int o = cnt_own[q] + cnt_up[q];
@@ -1502,6 +1507,7 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
                 const int px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
                 const int py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
                 atomicAdd(Ov + py * W + px, o);
+                if (strip_view) Mv[py * W + px] = 1;
                 hit = true;
             }
         }

@@ -25,7 +25,7 @@ constexpr size_t kOffStatus = kOffStats + align_up(sizeof(unsigned long long) * 
 constexpr size_t kOffFrames = kOffStatus + 256;
 constexpr size_t kOffPlan = kOffFrames + align_up(sizeof(FrameArg));
 constexpr size_t kOffPref = kOffPlan + align_up(sizeof(PlanEntry) * OCC_MAX_VIEWS);
-constexpr size_t kOffTab = kOffPref + align_up(sizeof(uint32_t) * (1 + kNumClasses) * (OCC_MAX_VIEWS + 1));
+constexpr size_t kOffTab = kOffPref + align_up(sizeof(uint32_t) * (1 + 2 * kNumClasses) * (OCC_MAX_VIEWS + 1));
 constexpr size_t kFlagWords = OCC_NOALLOC_MAX_PIXEL_VIEWS / 32 + OCC_MAX_VIEWS;
 constexpr size_t kOffFlags = kOffTab + align_up(sizeof(int32_t) * kTabLen * OCC_MAX_VIEWS);
 constexpr size_t kBrkEntries = OCC_NOALLOC_MAX_PIXEL_VIEWS;

@@ -146,3 +146,25 @@ def test_wrappers_reject_wrong_dtypes_and_shapes_before_calling_the_library():
         occ.occ_detect_noalloc(D, views, None, M=M, O=O, status=st)
     with pytest.raises(ValueError, match="CUDA"):
         occ.occ_detect(None, D, views, None, M=M, O=O)
+
+
+def test_diagonal_scan_lines_stay_on_their_diagonal():
+    """The strip kernel places sample g of a scan line t = round(fl(c g)) positions along the candidate's row, column
+    or diagonal.  Eq. 4 rounds each coordinate after adding it: round(fl(fl(c g) + x)).  The two agree for every
+    |g| <= 2047 and every coordinate below 4096 at the eight directions of a 3x3 array -- checked here exhaustively
+    with binary32 arithmetic and round-half-away-from-zero, as both sides compute it."""
+    f32 = np.float32
+    xs = np.arange(4096, dtype=np.float32)
+    g = np.arange(-2047, 2048, dtype=np.float32)
+
+    def roundf(v):
+        return np.sign(v) * np.floor(np.abs(v) + f32(0.5))
+
+    for alpha in range(0, 360, 45):
+        for comp in oracle.direction(float(alpha)):
+            t = (f32(comp) * g).astype(f32)                       # fl(c g)
+            direct = roundf(t)
+            for x0 in range(0, 4096, 512):
+                x = xs[x0:x0 + 512]
+                v = (t[:, None] + x[None, :]).astype(f32)        # fl(fl(c g) + x)
+                assert np.array_equal(roundf(v) - x[None, :], np.broadcast_to(direct[:, None], v.shape)), alpha

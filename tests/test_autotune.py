@@ -12,7 +12,8 @@ def test_workload_classes():
     assert autotune.size_class([(2160, 4096)]) == "large"
     assert autotune.scan_bucket(117) == "L<=254" and autotune.scan_bucket(740) == "L<=1022"
     assert autotune.angle_class([(0.0, 1), (90.0, 1), (270.0, 1)]) == "axial"
-    assert autotune.angle_class([(0.0, 1), (45.0, 1.4)]) == "general"
+    assert autotune.angle_class([(0.0, 1), (45.0, 1.4), (315.0, 1.4)]) == "octant"
+    assert autotune.angle_class([(0.0, 1), (30.0, 1.4)]) == "general"
     k = autotune.workload_key("GB300", [(1080, 1920)], [(0.0, 1.0)], 117, 8)
     assert k == "GB300|medium|L<=254|axial|N8"
 
@@ -22,6 +23,8 @@ def test_candidates_cover_every_mapping():
     assert {t["line_max_runs"] for t in c} == {0, 1, 2}
     assert {t["warp_lines_per_block"] for t in c} == {4, 8}
     assert all(1 <= t["line_blocks_per_sm"] <= 3 for t in c)
+    assert {t["strip_px"] for t in c} == {0, *autotune.STRIP_SHAPES}
+    assert len({autotune.tuning_name(t) for t in c}) == len(c)
 
 
 def test_cache_roundtrip(tmp_path):
@@ -55,3 +58,7 @@ def test_every_tuning_gives_the_same_result(tmp_path):
         assert again == best
         with pytest.raises(occ.OccError):
             occ.occ_set_tuning(ctx, {"line_max_runs": 3, "line_blocks_per_sm": 1, "warp_lines_per_block": 8})
+        for px in (2048, 4100, occ.OCC_STRIP_PX_MAX + 64):      # below a frame side, not a multiple of 64, too large
+            with pytest.raises(occ.OccError):
+                occ.occ_set_tuning(ctx, {"line_max_runs": 2, "line_blocks_per_sm": 1, "warp_lines_per_block": 8,
+                                         "strip_px": px})

@@ -1,0 +1,131 @@
+"""The strip kernel (k_strip): views whose scan lines stay on one row, column, diagonal or anti-diagonal, one block
+per strip of such lines with D_r and O in shared memory.  Its results must be the oracle's bit for bit, and equal
+those of the candidate-list kernels (strip_px = 0), for every strip shape; frames it does not take (a side above
+4096 pixels, N != 8) fall back to the list kernels; lines of three or more macro-runs go to the warp kernel through
+the view's list and still give the oracle's O and M."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2408_14050_gb300 as occ
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OCTANT = scenes.views_3x3()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = occ.occ_create(0, max_pixels=4100 * 600, max_views=24)
+    yield c
+    c.close()
+
+
+def tuning(strip_px):
+    return {"line_max_runs": 2, "line_blocks_per_sm": 1, "warp_lines_per_block": 8, "strip_px": strip_px}
+
+
+def detect(ctx, D, views, strip_px, **kw):
+    occ.occ_set_tuning(ctx, tuning(strip_px))
+    try:
+        d = dict(gamma=1.0, zeta=2.0, beta=0.5, L=0, N=8)
+        d.update(kw)
+        M, O = occ.occ_detect(ctx, torch.from_numpy(np.ascontiguousarray(D)).cuda(), views,
+                              occ.occ_default_params(**d))
+        assert occ.occ_get_status(ctx) == occ.OCC_OK
+        return M.cpu().numpy(), O.cpu().numpy(), occ.occ_get_stats(ctx, len(views))
+    finally:
+        occ.occ_set_tuning(ctx, None)
+
+
+def check_oracle(D, views, M, O, stats, **kw):
+    d = dict(gamma=1.0, zeta=2.0, beta=0.5, L=0, N=8)
+    d.update(kw)
+    po = oracle.default_params(**d)
+    for v, (a, r) in enumerate(views):
+        Oo, Mo, st = oracle.detect_view(D, a, r, po)
+        np.testing.assert_array_equal(O[v], Oo, err_msg=f"O view {v} alpha={a} r={r}")
+        np.testing.assert_array_equal(M[v], Mo, err_msg=f"M view {v} alpha={a} r={r}")
+        for k in ("candidates", "samples", "pair_tests", "L"):
+            assert stats[v][k] == st[k], (v, a, k, stats[v][k], st[k])
+
+
+@pytest.mark.parametrize("shape", [(270, 480), (480, 270), (97, 301), (301, 97), (1, 64), (64, 1), (5, 5)])
+@pytest.mark.parametrize("strip_px", [4096, 6144, 16384])
+def test_strip_shapes_match_the_oracle(ctx, shape, strip_px):
+    """Strips of 1 to 16 lines (rows, columns and both diagonals; wide, tall, one-pixel maps), against the oracle
+    and against the candidate-list kernels."""
+    H, W = shape
+    D = scenes.make_scene(scenes.spec_array(H, W), scenes.seed_of(90, H * 7 + W)) if min(H, W) > 8 else \
+        np.random.default_rng(H + W).uniform(0, 30, (H, W)).astype(np.float32)
+    M, O, st = detect(ctx, D, OCTANT, strip_px)
+    check_oracle(D, OCTANT, M, O, st)
+    M0, O0, st0 = detect(ctx, D, OCTANT, 0)
+    np.testing.assert_array_equal(O, O0)
+    np.testing.assert_array_equal(M, M0)
+    assert st == st0
+
+
+def test_full_frame_strip_and_list_paths_agree(ctx):
+    D = scenes.array_3x3(frame=2, H=540, W=960).frames[0]
+    M, O, st = detect(ctx, D, OCTANT, occ.STRIP_PX_DEFAULT)
+    M0, O0, st0 = detect(ctx, D, OCTANT, 0)
+    np.testing.assert_array_equal(O, O0)
+    np.testing.assert_array_equal(M, M0)
+    assert st == st0
+    check_oracle(D, OCTANT, M, O, st)
+
+
+def test_lines_of_many_runs_go_to_the_warp_kernel(ctx):
+    """Uniform noise breaks scan lines into many macro-runs: most lines of the strip views are listed for the warp
+    kernel, whose counts must land in O and M of those views; r = 2.5 and a fixed L of 300 (the 1024 class)."""
+    rng = np.random.default_rng(8)
+    D = rng.uniform(0, 40, (64, 160)).astype(np.float32)
+    views = [(0.0, 1.0), (45.0, 2.5), (90.0, 1.0), (135.0, 1.0), (180.0, 2.0), (225.0, 1.0), (270.0, 1.0),
+             (315.0, 1.5), (20.0, 1.0)]
+    for L in (0, 300):
+        M, O, st = detect(ctx, D, views, occ.STRIP_PX_DEFAULT, L=L)
+        check_oracle(D, views, M, O, st, L=L)
+
+
+def test_frames_above_the_strip_limit_use_the_lists(ctx):
+    """A side above 4096 pixels, or N != 8: every view takes the candidate-list kernels, with the same results."""
+    D = scenes.make_scene(scenes.spec_array(12, 4100), scenes.seed_of(91, 0))
+    M, O, st = detect(ctx, D, OCTANT[:4], occ.STRIP_PX_DEFAULT)
+    check_oracle(D, OCTANT[:4], M, O, st)
+    D = scenes.make_scene(scenes.spec_array(90, 130), scenes.seed_of(91, 1))
+    for N in (4, 16):
+        M, O, st = detect(ctx, D, OCTANT, occ.STRIP_PX_DEFAULT, N=N)
+        check_oracle(D, OCTANT, M, O, st, N=N)
+
+
+def test_strips_in_batches_and_graphs(ctx):
+    """Uneven frames of one batch (strips of each frame after the previous frame's), captured in a CUDA graph and
+    replayed on new inputs."""
+    sizes = [(48, 64), (100, 77), (270, 480), (31, 200), (1, 9), (129, 130)]
+    views = OCTANT
+    first = [scenes.make_scene(scenes.spec_array(H, W), scenes.seed_of(92, i)) if min(H, W) > 8 else
+             np.full((H, W), 3.0, np.float32) for i, (H, W) in enumerate(sizes)]
+    second = [f[::-1, ::-1].copy() for f in first]
+    Ds = [torch.from_numpy(f).cuda() for f in first]
+    Ms = [torch.empty((len(views), *D.shape), dtype=torch.uint8, device="cuda") for D in Ds]
+    Os = [torch.empty((len(views), *D.shape), dtype=torch.int32, device="cuda") for D in Ds]
+    occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)
+    for f_np, D in zip(second, Ds):
+        D.copy_(torch.from_numpy(f_np).cuda())
+    g.replay()
+    torch.cuda.synchronize()
+    assert occ.occ_get_status(ctx) == occ.OCC_OK
+    for f_np, M, O in zip(second, Ms, Os):
+        for v, (a, r) in enumerate(views):
+            Oo, Mo, _ = oracle.detect_view(f_np, a, r)
+            np.testing.assert_array_equal(O[v].cpu().numpy(), Oo)
+            np.testing.assert_array_equal(M[v].cpu().numpy(), Mo)
