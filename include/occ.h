@@ -99,7 +99,8 @@ void occ_default_params(occ_params* p);
 void occ_direction(double alpha_deg, float* c, float* s);
 
 /* Creates a context on CUDA device `device` and allocates its scratch: the candidate lists (max_candidates entries
- * per view; <= 0 means max_pixels, which never overflows), the status word and the per-view counters.
+ * per view; <= 0 means max_pixels, which never overflows), the status word and the per-view counters.  A view that
+ * takes the strip kernel (see occ_tuning) lists only its scan lines of three or more macro-runs there.
  * max_pixels >= 1 bounds H*W of later calls; 1 <= max_views <= OCC_MAX_VIEWS.  On success *out receives the
  * context; on failure *out is NULL and the return is OCC_ERR_INVALID_ARG or OCC_ERR_CUDA. */
 int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views, int64_t max_candidates);

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_warp[kStripWarps];
-    __shared__ uint32_t s_n1, s_n2, s_b1, s_b2, s_cand;
+    __shared__ uint32_t s_n1, s_n2, s_b1, s_cand;
     __shared__ unsigned long long s_n, s_p;
 
     const int tid = threadIdx.x, lane = tid & 31;
@@ -505,10 +505,7 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
         if (nraw == 0) break;
 
         // 3. Macro-runs of every candidate's scan line.
-        if (tid == 0) {
-            s_n1 = s_n2 = 0;
-            s_b1 = s_b2 = 0;
-        }
+        if (tid == 0) s_n1 = s_n2 = s_b1 = 0;
         __syncthreads();
         for (uint32_t e = tid; e < nraw; e += kStripThreads) {
             const uint32_t ent = sRaw[e];
@@ -535,18 +532,19 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
         }
         __syncthreads();
 
-        // 4. Counts: one-run lines, then two-run lines, 32 lines per warp and batch.
+        // 4. Counts: batches of 32 lines per warp from one counter, the one-run lines' batches first, then the
+        //    two-run lines'; every batch holds lines of one kind, so the lanes of a warp run the same loop.
         const uint32_t n1 = s_n1, n2 = s_n2;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; pass++) {
-            const uint32_t nq = pass == 0 ? n1 : n2;
-            uint32_t* ctr = pass == 0 ? &s_b1 : &s_b2;
-            for (;;) {
-                uint32_t bi = 0;
-                if (lane == 0) bi = atomicAdd(ctr, 1u);
-                bi = __shfl_sync(kFullMask, bi, 0);
-                if (bi * 32 >= nq) break;
-                const uint32_t e = bi * 32 + lane;
+        const uint32_t nb1 = (n1 + 31) / 32, nbt = nb1 + (n2 + 31) / 32;
+        for (;;) {
+            uint32_t bi = 0;
+            if (lane == 0) bi = atomicAdd(&s_b1, 1u);
+            bi = __shfl_sync(kFullMask, bi, 0);
+            if (bi >= nbt) break;
+            {
+                const int pass = bi < nb1 ? 0 : 1;
+                const uint32_t e = (pass == 0 ? bi : bi - nb1) * 32 + lane;
+                const uint32_t nq = pass == 0 ? n1 : n2;
                 if (e < nq) {
                     const uint2 q = pass == 0 ? sQ[e] : sQ[kStripQueue - 1 - e];
                     const int b = (int)((q.x >> 12) & 15u), tc = (int)(q.x & 4095u);
