@@ -526,8 +526,13 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
                 int x, y;
                 line_pixel(fam, x0, y0, ay, tc, x, y);
                 const uint32_t i = atomicAdd(&F.hdr[HDR_OVF + v], 1u);
-                if ((int64_t)i < F.cap) F.cand[(int64_t)v * F.cap + i] = ((uint32_t)y << 16) | (uint32_t)x;
-                else atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
+                if ((int64_t)i < F.cap) {
+                    F.cand[(int64_t)v * F.cap + i] = ((uint32_t)y << 16) | (uint32_t)x;
+                } else {
+                    // k_plan has already gathered the frames' status words into the call's: set both.
+                    atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
+                    atomicOr(a.status, ST_CAND_OVERFLOW);
+                }
             }
         }
         __syncthreads();
