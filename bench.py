@@ -66,10 +66,13 @@ def parse():
                     help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")
     ap.add_argument("--dry-run", action="store_true",
                     help="launch and reduce over ranks (gloo) without a GPU; prints the JSON line of that run")
-    ap.add_argument("--probe", choices=["fusion", "proposer"], default=None,
-                    help="run a few launches of the median fusion and backward warp (fusion) or of the learned "
-                         "proposer's forward and training step (proposer) on bench-sized inputs, then exit "
-                         "(for profiling with ncu -k)")
+    ap.add_argument("--probe", choices=["fusion", "proposer", "detect"], default=None,
+                    help="run a few launches of the median fusion and backward warp (fusion), of the learned "
+                         "proposer's forward and training step (proposer), or three occ_detect calls on the "
+                         "1920x1080 3x3-array frame (detect) on bench-sized inputs, then exit (for profiling with "
+                         "ncu -k)")
+    ap.add_argument("--strip-px", type=int, default=None,
+                    help="with --probe detect: occ_tuning.strip_px of the calls (0: list kernels only)")
     return ap.parse_args()
 
 
@@ -754,7 +757,20 @@ def run_probe(args):
 
     import paper_2408_14050_gb300 as occ
     views = scenes.views_3x3()
-    if args.probe == "fusion":
+    if args.probe == "detect":
+        f = scenes.array_3x3(frame=0).frames[0]
+        H, W = f.shape
+        D = torch.from_numpy(f).cuda()
+        with occ.occ_create(0, max_pixels=H * W, max_views=8) as ctx:
+            if args.strip_px is not None:
+                t = occ.occ_get_tuning(ctx)[0]
+                t["strip_px"] = args.strip_px
+                occ.occ_set_tuning(ctx, t)
+            for _ in range(3):
+                occ.occ_detect(ctx, D, views)
+            if occ.occ_get_status(ctx) != occ.OCC_OK:
+                raise RuntimeError("detect failed")
+    elif args.probe == "fusion":
         f = scenes.array_3x3(frame=0).frames[0]
         H, W = f.shape
         maps = [torch.from_numpy(m).cuda() for m in scenes.stereo_maps(f, 8, seed=3)]
