@@ -150,9 +150,22 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     for (int f = 0; f < nf; f++)
         if (fr[f].H > kStripMaxSide || fr[f].W > kStripMaxSide) strip_ok = false;
     int n_strip = 0;
+    a.ngroups = 0;
     for (int v = 0; v < nv; v++) {
-        a.view[v].fam = strip_ok ? strip_family(a.view[v].c, a.view[v].s) : -1;
-        if (a.view[v].fam >= 0) n_strip++;
+        const int fam = strip_ok ? strip_family(a.view[v].c, a.view[v].s) : -1;
+        a.view[v].fam = fam;
+        if (fam < 0) continue;
+        n_strip++;
+        // Pair the view with an earlier one of the same family and ratio that is still alone.
+        int g = 0;
+        while (g < a.ngroups && !(a.group[g].fam == fam && a.group[g].vb < 0 && a.view[a.group[g].va].r == a.view[v].r))
+            g++;
+        if (g < a.ngroups) {
+            a.group[g].vb = v;
+        } else {
+            a.group[a.ngroups] = StripGroup{fam, v, -1, 0};
+            a.ngroups++;
+        }
     }
     const bool list_views = n_strip < nv;
     a.any_list = list_views ? 1 : 0;
@@ -211,8 +224,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         F.tiles_x = (F.W + kTile - 1) / kTile;
         F.tiles_y = (F.H + kTile - 1) / kTile;
         F.strip0 = (uint32_t)strips;
-        for (int v = 0; v < nv; v++)
-            if (a.view[v].fam >= 0) strips += fam_strips(a.view[v].fam, F.H, F.W, a.strip_px);
+        for (int g = 0; g < a.ngroups; g++) strips += fam_strips(a.group[g].fam, F.H, F.W, a.strip_px);
         const int quads = F.H * ((F.W + 3) / 4);
         if (quads > a.max_quads) a.max_quads = quads;
         const int64_t px = (int64_t)nv * F.H * F.W;

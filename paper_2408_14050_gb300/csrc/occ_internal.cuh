@@ -116,6 +116,14 @@ struct FrameArg {
     int32_t pad2;
 };
 
+// Views that share the strips of k_strip: the same strip family and ratio (hence the same D_r, candidates test
+// inputs and scan length), at most two (a direction and its opposite, in a camera array).
+struct StripGroup {
+    int32_t fam;
+    int32_t va, vb;   // vb = -1: one view
+    int32_t pad;
+};
+
 // Per (frame, view), written by k_plan.
 struct PlanEntry {
     int32_t h;       // half scan length h = ceil(L / 2); -1: view skipped (non-finite input or L too long)
@@ -155,6 +163,8 @@ struct Args {
     int32_t any_list;             // some view takes the candidate-list path (k_edges lists its candidates)
     int32_t strip_px;             // pixels of one strip (k_strip); 0 when no view takes the strip path
     uint32_t strip_total;         // strips of the call
+    int32_t ngroups;              // strip groups (each frame has the strips of every group, in group order)
+    StripGroup group[kMaxViews];
     uint32_t* pref_ovf;           // [kNumClasses][nf * nv + 1] prefix of the strip views' listed lines per size class
 };
 

@@ -43,6 +43,14 @@ __device__ __forceinline__ float ord2f(uint32_t o)
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
 }
 
+// O[p] += o as a reduction (no return value) predicated on o != 0 inside the asm: the count of a sample leaving the
+// window goes to O without a divergent branch around the atomic.
+__device__ __forceinline__ void o_red(int32_t* addr, int o)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.add.s32 [%0], %1;\n\t}" ::"l"(addr), "r"(o)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------------------------------------------------------
 // k_edges: Eq. 1, Eq. 2 (predicate + compaction), Eq. 3 (min/max), E/A, O = 0.
 //
@@ -644,10 +652,8 @@ __device__ __forceinline__ void rot_push(RotWindow& R, const LineSample& e, floa
         eo += (close && eb < R.v[i]) ? 1 : 0;
         R.o[i] += (close && R.b[i] < e.v) ? 1 : 0;
     }
-    if (R.o[J]) {
-        atomicAdd(Ov + R.p[J], sgn * R.o[J]);
-        if (kHits) hit = 1;
-    }
+    o_red(Ov + R.p[J], sgn * R.o[J]);
+    if (kHits) hit |= R.o[J];
     R.w[J] = e.w;
     R.v[J] = e.v;
     R.b[J] = eb;
@@ -658,11 +664,10 @@ __device__ __forceinline__ void rot_push(RotWindow& R, const LineSample& e, floa
 __device__ __forceinline__ bool rot_flush(const RotWindow& R, int32_t* Ov, int hit)
 {
 #pragma unroll
-    for (int i = 0; i < 4; i++)
-        if (R.o[i]) {
-            atomicAdd(Ov + R.p[i], R.o[i]);
-            hit = 1;
-        }
+    for (int i = 0; i < 4; i++) {
+        o_red(Ov + R.p[i], R.o[i]);
+        hit |= R.o[i];
+    }
     return hit != 0;
 }
 

@@ -32,8 +32,9 @@ namespace {
 constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kStripThreads = 128;
 constexpr int kStripWarps = kStripThreads / 32;
-constexpr int kStripQueue = 1024;          // queue entries of one round
-constexpr int kStripTab = 4096;            // offsets of samples k = 0 .. 2h (h <= 2047)
+constexpr int kStripQueue = 512;           // queue entries of one round
+constexpr int kStripTab = 4104;            // offsets of samples k = 0 .. 2h (h <= 2047), then 0 for k = 2h + 1 .. 2h + 4
+                                           // (reads one or two samples ahead need no bound check)
 
 // First pixel (x0, y0), step (ax, ay) per position and length n of line l of a family.
 __device__ __forceinline__ void line_geom(int fam, int H, int W, int l, int& x0, int& y0, int& ay, int& n)
@@ -63,16 +64,15 @@ __device__ __forceinline__ void line_pixel(int fam, int x0, int y0, int ay, int 
     y = y0 + ay * t;
 }
 
-// O of a strip pixel: 16-bit halves of 32-bit shared words.
-__device__ __forceinline__ void o_add(uint32_t* sO, int p, int o)
+// O of a strip pixel: one 32-bit shared word per pixel holds the sums of the strip's two views, view A in the low
+// and view B in the high 16 bits (sh = 0 or 16); added with a shared-memory reduction (no return value) predicated
+// on o != 0 inside the asm, so that the count of a sample leaving the window goes to O without a branch.
+__device__ __forceinline__ void o_add(uint32_t* sO, int p, int o, int sh)
 {
-    atomicAdd(sO + (p >> 1), (uint32_t)o << ((p & 1) << 4));
+    const uint32_t addr = (uint32_t)__cvta_generic_to_shared(sO + p);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.add.u32 [%0], %1;\n\t}"
+                 ::"r"(addr), "r"((uint32_t)o << sh), "r"((uint32_t)o) : "memory");
 }
-__device__ __forceinline__ uint32_t o_get(const uint32_t* sO, int p)
-{
-    return (sO[p >> 1] >> ((p & 1) << 4)) & 0xFFFFu;
-}
-
 // Eq. 5 / Eq. 6 over an emitted (sorted) stream: the last N/2 = 4 samples, the i-th emitted sample in slot i mod 4,
 // which held sample i - 4 (final once tested against the new one).  Empty slots hold W = +inf, close to nothing.
 struct Win {
@@ -92,7 +92,7 @@ __device__ __forceinline__ void win_init(Win& R)
 
 template <int J>
 __device__ __forceinline__ void win_push(Win& R, float ew, float ev, int ep, float zeta, float beta, uint32_t* sO,
-                                         int& hit)
+                                         int sh, int& hit)
 {
     const float eb = __fadd_rn(ev, beta);
     int eo = 0;
@@ -102,10 +102,8 @@ __device__ __forceinline__ void win_push(Win& R, float ew, float ev, int ep, flo
         eo += (close && eb < R.v[i]) ? 1 : 0;
         R.o[i] += (close && R.b[i] < ev) ? 1 : 0;
     }
-    if (R.o[J]) {
-        o_add(sO, R.p[J], R.o[J]);
-        hit = 1;
-    }
+    o_add(sO, R.p[J], R.o[J], sh);
+    hit |= R.o[J];
     R.w[J] = ew;
     R.v[J] = ev;
     R.b[J] = eb;
@@ -113,22 +111,23 @@ __device__ __forceinline__ void win_push(Win& R, float ew, float ev, int ep, flo
     R.o[J] = eo;
 }
 
-__device__ __forceinline__ void win_flush(const Win& R, uint32_t* sO, int& hit)
+__device__ __forceinline__ void win_flush(const Win& R, uint32_t* sO, int sh, int& hit)
 {
 #pragma unroll
-    for (int i = 0; i < 4; i++)
-        if (R.o[i]) {
-            o_add(sO, R.p[i], R.o[i]);
-            hit = 1;
-        }
+    for (int i = 0; i < 4; i++) {
+        o_add(sO, R.p[i], R.o[i], sh);
+        hit |= R.o[i];
+    }
 }
 
-// The samples of one scan line: k = 0 .. 2h at position tc + tab[k] of line row lb (its first shared index).
+// The samples of one scan line: k = 0 .. 2h at position tc + tab[k] of line row lb (its first shared index), its
+// view's half of the O words (sh).
 struct LineRef {
     const float* sV;
     const int16_t* tab;
     int base;   // lb + tc
     int h;
+    int sh;
 };
 
 __device__ __forceinline__ void sample(const LineRef& L, int k, float& w, float& v, int& p)
@@ -149,61 +148,63 @@ __device__ __forceinline__ int detect_runs(const LineRef& L, int k0, int k1, int
     float lastw = kNegInf;
     int runs = 1;
     ks = -1;
-    int tn = L.tab[min(k0 + 1, k1)];
-    for (int k = k0 + 1; k <= k1; k++) {
-        const float v = L.sV[L.base + tn];
-        tn = L.tab[min(k + 1, k1)];
-        g = __fadd_rn(g, 1.0f);
-        const float w = __fsub_rn(g, v);
-        const bool sb = w < bufw;
-        if (sb && w < lastw) {
-            if (runs == 2) return 3;
-            runs = 2;
-            ks = k;
-            bufw = w;
-            lastw = kNegInf;
-        } else {
-            lastw = sb ? w : bufw;
-            bufw = sb ? bufw : w;
-        }
+    int k = k0 + 1;
+    int tn = L.tab[k];   // k <= 2h + 1: the table's padding keeps the read in bounds
+#define OCC_DSTEP                                                                    \
+    {                                                                                \
+        const float v = L.sV[L.base + tn];                                           \
+        tn = L.tab[k + 1];                                                           \
+        g = __fadd_rn(g, 1.0f);                                                      \
+        const float w = __fsub_rn(g, v);                                             \
+        const bool sb = w < bufw;                                                    \
+        if (sb && w < lastw) {                                                       \
+            if (runs == 2) return 3;                                                 \
+            runs = 2;                                                                \
+            ks = k;                                                                  \
+            bufw = w;                                                                \
+            lastw = kNegInf;                                                         \
+        } else {                                                                     \
+            lastw = sb ? w : bufw;                                                   \
+            bufw = sb ? bufw : w;                                                    \
+        }                                                                            \
+        k++;                                                                         \
     }
+    for (; k + 3 <= k1;) {
+        OCC_DSTEP OCC_DSTEP OCC_DSTEP OCC_DSTEP
+    }
+    for (; k <= k1;) OCC_DSTEP
+#undef OCC_DSTEP
     return runs;
 }
 
-// One macro-run k0 .. k1 through the one-slot buffer: every emitted sample tested against the four before it.
+// One macro-run k0 .. k1 through the one-slot buffer: every emitted sample tested against the four before it.  The
+// n - 1 samples after the first go in four at a time (the window slot of a step is its index mod 4), then the rest, then
+// the buffered sample is emitted last.
 __device__ __forceinline__ void count_stream(const LineRef& L, int k0, int k1, float zeta, float beta, uint32_t* sO,
                                              int& hit)
 {
-    const float kInf = __int_as_float(0x7f800000);
     Win R;
     win_init(R);
     float bw, bv;
     int bp;
     sample(L, k0, bw, bv, bp);
     float g = (float)(k0 - L.h);
-    // The sample in flight (k) and the offset of the one after it.
+    // The sample in flight (k) and the table offset of the one after it.
     int k = k0 + 1;
-    int pn = L.base + L.tab[min(k, k1)];
+    int pn = L.base + L.tab[k];   // k + 2 <= 2h + 3 below: the table's padding keeps the reads in bounds
     float vn = L.sV[pn];
-    int tn = L.tab[min(k + 1, k1)];
-    int left = k1 - k0 + 1;   // pushes: every sample once; the last step pushes in a sample of W = +inf
-#define OCC_SSTEP(J)                                                                 \
+    int tn = L.tab[k + 1];
+    int rem = k1 - k0;
+#define OCC_RSTEP(J)                                                                 \
     {                                                                                \
-        float sw, sv;                                                                \
-        int sp;                                                                      \
-        if (k <= k1) {                                                               \
-            g = __fadd_rn(g, 1.0f);                                                  \
-            sv = vn;                                                                 \
-            sp = pn;                                                                 \
-            sw = __fsub_rn(g, sv);                                                   \
-            pn = L.base + tn;                                                        \
-            vn = L.sV[pn];                                                           \
-            tn = L.tab[min(k + 2, k1)];                                              \
-        } else {                                                                     \
-            sw = kInf;                                                               \
-            sv = 0.0f;                                                               \
-            sp = 0;                                                                  \
-        }                                                                            \
+        g = __fadd_rn(g, 1.0f);                                                      \
+        const float sv = vn;                                                         \
+        const int sp = pn;                                                           \
+        const float sw = __fsub_rn(g, sv);                                           \
+        pn = L.base + tn;                                                            \
+        vn = L.sV[pn];                                                               \
+        tn = L.tab[k + 2];                                                           \
+        k++;                                                                         \
         const bool sb = sw < bw;                                                     \
         const float ew = sb ? sw : bw, ev = sb ? sv : bv;                            \
         const int ep = sb ? sp : bp;                                                 \
@@ -212,18 +213,24 @@ __device__ __forceinline__ void count_stream(const LineRef& L, int k0, int k1, f
             bv = sv;                                                                 \
             bp = sp;                                                                 \
         }                                                                            \
-        win_push<J>(R, ew, ev, ep, zeta, beta, sO, hit);                             \
-        k++;                                                                         \
-        if (--left == 0) break;                                                      \
+        win_push<J>(R, ew, ev, ep, zeta, beta, sO, L.sh, hit);                             \
     }
-    for (;;) {
-        OCC_SSTEP(0)
-        OCC_SSTEP(1)
-        OCC_SSTEP(2)
-        OCC_SSTEP(3)
+#define OCC_FSTEP(J) win_push<J>(R, bw, bv, bp, zeta, beta, sO, L.sh, hit);
+    for (; rem >= 4; rem -= 4) {
+        OCC_RSTEP(0)
+        OCC_RSTEP(1)
+        OCC_RSTEP(2)
+        OCC_RSTEP(3)
     }
-#undef OCC_SSTEP
-    win_flush(R, sO, hit);
+    switch (rem) {
+    case 0: OCC_FSTEP(0) break;
+    case 1: OCC_RSTEP(0) OCC_FSTEP(1) break;
+    case 2: OCC_RSTEP(0) OCC_RSTEP(1) OCC_FSTEP(2) break;
+    default: OCC_RSTEP(0) OCC_RSTEP(1) OCC_RSTEP(2) OCC_FSTEP(3) break;
+    }
+#undef OCC_RSTEP
+#undef OCC_FSTEP
+    win_flush(R, sO, L.sh, hit);
 }
 
 // Two macro-runs [k0, ks - 1] and [ks, k1], each through its own one-slot buffer, merged by (W, k): a head of the
@@ -289,7 +296,7 @@ __device__ __forceinline__ void count_merge2(const LineRef& L, int k0, int k1, i
             knb = kn; hbb = hbuf; bbw = bw; bbv = bv; bbp = bp;                      \
             hbw = nw; hbv = nv; hbp = np; has_b = has;                               \
         }                                                                            \
-        win_push<J>(R, ew, ev, ep, zeta, beta, sO, hit);                             \
+        win_push<J>(R, ew, ev, ep, zeta, beta, sO, L.sh, hit);                             \
     }
     for (;;) {
         OCC_MSTEP(0)
@@ -298,7 +305,7 @@ __device__ __forceinline__ void count_merge2(const LineRef& L, int k0, int k1, i
         OCC_MSTEP(3)
     }
 #undef OCC_MSTEP
-    win_flush(R, sO, hit);
+    win_flush(R, sO, L.sh, hit);
 }
 
 // First and last k of a scan line inside its digital line of n positions: tab is monotone, so the samples inside
@@ -319,6 +326,12 @@ __device__ __forceinline__ void strip_range(const int16_t* tab, int h, int tc, i
         if (inside(m)) lo = m; else hi = m - 1;
     }
     k1 = lo;
+}
+
+// The 16 bytes before D_r: a sample read ahead of a line's end (never used) may land there.
+__device__ __forceinline__ void smem_guard_init(unsigned char* smem)
+{
+    reinterpret_cast<uint4*>(smem)[0] = make_uint4(0, 0, 0, 0);
 }
 
 // Block-wide inclusive scan of one value per thread (kStripThreads threads); *total gets the sum.
@@ -345,15 +358,15 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t* s_warp, uin
 }
 
 template <bool kHits>
-__global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__ Args a)
+__global__ void __launch_bounds__(kStripThreads, 4) k_strip(const __grid_constant__ Args a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_warp[kStripWarps];
-    __shared__ uint32_t s_n1, s_n2, s_b1, s_cand;
-    __shared__ unsigned long long s_n, s_p;
+    __shared__ uint32_t s_n1, s_n2, s_b1, s_cand[2];
+    __shared__ unsigned long long s_st[2][2];
 
     const int tid = threadIdx.x, lane = tid & 31;
-    // The strip of this CTA: frame (last with strip0 <= block), then the views' strips in view order.
+    // The strip of this CTA: frame (last with strip0 <= block), then the groups' strips in group order.
     const uint32_t sid = blockIdx.x;
     int f = 0;
     {
@@ -366,113 +379,165 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
     }
     const FrameArg& F = a.frames[f];
     const int H = F.H, W = F.W;
+    // Fields used in the pixel loops, held in registers (a global record might alias the stores as far as the
+    // compiler can tell, and would be read again after each one).
+    const float* const Dp = F.D;
+    const int64_t pitch = F.pitch;
+    const uint8_t* const prop = F.prop;
+    const int tiles_x = F.tiles_x;
     uint32_t rem = sid - F.strip0;
-    int v = -1, fam = 0;
-    for (int u = 0; u < a.nv; u++) {
-        const int fm = a.view[u].fam;
-        if (fm < 0) continue;
-        const uint32_t ns = (uint32_t)fam_strips(fm, H, W, a.strip_px);
+    int gi = -1;
+    for (int u = 0; u < a.ngroups; u++) {
+        const uint32_t ns = (uint32_t)fam_strips(a.group[u].fam, H, W, a.strip_px);
         if (rem < ns) {
-            v = u;
-            fam = fm;
+            gi = u;
             break;
         }
         rem -= ns;
     }
-    if (v < 0) return;
-    const int h = a.plan[f * a.nv + v].h;
-    if (h < 0) return;   // the view was not run (non-finite input or L too long): M and O unspecified
-    const ViewArg va = a.view[v];
+    if (gi < 0) return;
+    const StripGroup grp = a.group[gi];
+    const int fam = grp.fam;
+    const int nvw = grp.vb >= 0 ? 2 : 1;               // views of the group (same family, same ratio)
+    const int vw0 = grp.va, vw1 = grp.vb >= 0 ? grp.vb : grp.va;
+    const int h = a.plan[f * a.nv + vw0].h;             // equal for both: same ratio, same L (Eq. 3)
+    if (h < 0) return;   // the views were not run (non-finite input or L too long): M and O unspecified
+    const ViewArg va = a.view[vw0], vb = a.view[vw1];
     const int len = fam_len(fam, H, W);
     const int B = strip_lines(fam, H, W, a.strip_px);
     const int l0 = (int)rem * B;
     const int nb = min(B, fam_lines(fam, H, W) - l0);
     const float r = va.r;
-    const float cc = fam == kFamCols ? va.s : va.c;
     const float zeta = a.zeta, beta = a.beta;
     const int64_t plane = (int64_t)H * W;
 
-    float* sV = reinterpret_cast<float*>(smem);                                   // [nb][len] D_r
-    uint32_t* sO = reinterpret_cast<uint32_t*>(smem + (size_t)a.strip_px * 4);    // [nb][len] O, 16 bits each
-    uint32_t* sBits = sO + a.strip_px / 2;                                        // [nb][len] candidate bits
-    int16_t* sTab = reinterpret_cast<int16_t*>(sBits + a.strip_px / 32);          // [2h + 1] positions
-    uint2* sQ = reinterpret_cast<uint2*>(sTab + kStripTab);                       // one-run lines from the front,
-                                                                                  // two-run lines from the back
-    uint16_t* sRaw = reinterpret_cast<uint16_t*>(sQ + kStripQueue);               // candidates of the round
+    // Shared memory: a guard word (a sample read one step ahead of a line's end may fall one position before its
+    // first), D_r of the lines, the O words, the candidate bits of each view, each view's table of sample offsets,
+    // the line queue and the round's candidates.
+    float* sV = reinterpret_cast<float*>(smem + 16);                                        // [nb][len]
+    uint32_t* sO = reinterpret_cast<uint32_t*>(smem + 16 + (size_t)a.strip_px * 4);         // [nb][len]
+    uint32_t* sBits = sO + a.strip_px;                                                      // [2][strip_px / 32]
+    int16_t* sTab = reinterpret_cast<int16_t*>(sBits + 2 * (a.strip_px / 32));              // [2][kStripTab]
+    uint2* sQ = reinterpret_cast<uint2*>(sTab + 2 * kStripTab);                             // [kStripQueue]
+    uint32_t* sRaw = reinterpret_cast<uint32_t*>(sQ + kStripQueue);                         // [kStripQueue]
 
-    const int npx = nb * len;
+    const int npx = nb * len;   // shared positions of the strip (lines shorter than len leave some unused)
     const int nwords = (npx + 31) >> 5;
-    for (int i = tid; i < (npx + 1) / 2; i += kStripThreads) sO[i] = 0;
-    for (int i = tid; i < nwords; i += kStripThreads) sBits[i] = 0;
-    for (int k = tid; k <= 2 * h; k += kStripThreads)
-        sTab[k] = (int16_t)(int)roundf(__fmul_rn(cc, (float)(k - h)));
-    if (tid == 0) {
-        s_cand = 0;
-        s_n = s_p = 0;
+    for (int i = tid; i < npx; i += kStripThreads) sO[i] = 0;
+    for (int i = tid; i < 2 * nwords; i += kStripThreads) sBits[(i < nwords ? 0 : a.strip_px / 32 - nwords) + i] = 0;
+    for (int w = 0; w < nvw; w++) {
+        const ViewArg& vv = w ? vb : va;
+        const float cc = fam == kFamCols ? vv.s : vv.c;
+        for (int k = tid; k <= 2 * h + 4; k += kStripThreads)
+            sTab[w * kStripTab + k] = k <= 2 * h ? (int16_t)(int)roundf(__fmul_rn(cc, (float)(k - h))) : (int16_t)0;
     }
+    if (tid < 2) {
+        s_cand[tid] = 0;
+        s_st[tid][0] = s_st[tid][1] = 0;
+    }
+    if (tid == 0) smem_guard_init(smem);
     __syncthreads();
 
-    // 1. Stage D_r and evaluate Eq. 1-2 (on D_r) for every pixel of the strip; threads walk the strip so that
-    //    neighbouring threads read neighbouring pixels of a row.
-    const int span = fam == kFamRows ? W : H;    // positions of the outer loop: x along rows, y otherwise
-    const int iters = nb * span;
+    // Thread layout of the two pixel passes (staging, output), without divisions per pixel: along rows every thread
+    // walks x of each line in turn (coalesced); for the other families the nb lines of the strip lie side by side in
+    // a row of the frame, so groups of nb neighbouring threads take one row each, the whole group walking y.
+    const int tb = fam == kFamRows ? 0 : tid % nb;
+    const int ty = fam == kFamRows ? tid : tid / nb;
+    const int ystep = kStripThreads / nb;
+    const bool in_grp = fam == kFamRows || ty < ystep;
+    int bx0, by0, bay, bn;
+    line_geom(fam, H, W, l0 + tb, bx0, by0, bay, bn);
+    const int dl = fam == kFamDiag ? (l0 + tb) - (H - 1) : l0 + tb;   // x - y of a diagonal, x + y of an anti-diagonal
+
+    // 1. Stage D_r and evaluate Eq. 1-2 (on D_r, shared by the group's views) for every pixel of the strip, four
+    //    pixels of a thread at a time with their twelve loads (D, right and lower neighbours) issued first.
     const int tpv = F.tiles_x * F.tiles_y;
-    uint32_t my_cand = 0;
-    for (int i = tid; i < iters; i += kStripThreads) {
-        int b, x, y, t;
+    uint32_t my_cand[2] = {0, 0};
+    {
+        const bool one = (r == 1.0f);
+        auto stage4 = [&](const int (&bq)[4], const int (&xq)[4], const int (&yq)[4], const int (&tq)[4],
+                          const bool (&ok)[4]) {
+            float d[4], dx[4], dy[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                d[u] = dx[u] = dy[u] = 0.0f;
+                if (ok[u]) {
+                    const float* row = Dp + (int64_t)yq[u] * pitch + xq[u];
+                    d[u] = __ldg(row);
+                    if (xq[u] + 1 < W) dx[u] = __ldg(row + 1);
+                    if (yq[u] + 1 < H) dy[u] = __ldg(row + pitch);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                if (!ok[u]) continue;
+                const float dr = one ? d[u] : __fmul_rn(r, d[u]);
+                const int q = bq[u] * len + tq[u];
+                sV[q] = dr;
+                const float ex = (xq[u] + 1 < W) ? __fsub_rn(one ? dx[u] : __fmul_rn(r, dx[u]), dr) : 0.0f;
+                const float ey = (yq[u] + 1 < H) ? __fsub_rn(one ? dy[u] : __fmul_rn(r, dy[u]), dr) : 0.0f;
+                const float e2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+                if (!(e2 >= a.e2min)) continue;
+                const int tile = (yq[u] / kTile) * tiles_x + xq[u] / kTile;
+#pragma unroll
+                for (int w = 0; w < 2; w++) {
+                    if (w >= nvw) break;
+                    const ViewArg& vv = w ? vb : va;
+                    bool cand = __fadd_rn(__fmul_rn(ex, vv.c), __fmul_rn(ey, vv.s)) > 0.0f;
+                    if (cand && prop) cand = prop[(int64_t)(w ? vw1 : vw0) * tpv + tile] != 0;
+                    if (cand) {
+                        atomicOr(sBits + w * (a.strip_px / 32) + (q >> 5), 1u << (q & 31));
+                        my_cand[w]++;
+                    }
+                }
+            }
+        };
+        int bq[4], xq[4], yq[4], tq[4];
+        bool ok[4];
         if (fam == kFamRows) {
-            b = i / W;
-            x = i - b * W;
-            y = l0 + b;
-            t = x;
-        } else {
-            y = i / nb;
-            b = i - y * nb;
-            const int l = l0 + b;
-            if (fam == kFamCols) {
-                x = l;
-                t = y;
-            } else {
-                int x0, y0, ay, n;
-                line_geom(fam, H, W, l, x0, y0, ay, n);
-                x = fam == kFamDiag ? y + (l - (H - 1)) : l - y;
-                if (x < 0 || x >= W) continue;
-                t = x - x0;
+            for (int b = 0; b < nb; b++)
+                for (int x0 = tid; x0 < W; x0 += 4 * kStripThreads) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        bq[u] = b;
+                        xq[u] = x0 + u * kStripThreads;
+                        yq[u] = l0 + b;
+                        tq[u] = xq[u];
+                        ok[u] = xq[u] < W;
+                    }
+                    stage4(bq, xq, yq, tq, ok);
+                }
+        } else if (in_grp) {
+            for (int y0 = ty; y0 < H; y0 += 4 * ystep) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int y = y0 + u * ystep;
+                    const int x = fam == kFamCols ? dl : (fam == kFamDiag ? y + dl : dl - y);
+                    bq[u] = tb;
+                    xq[u] = x;
+                    yq[u] = y;
+                    tq[u] = fam == kFamCols ? y : (fam == kFamDiag ? y - by0 : x - bx0);
+                    ok[u] = y < H && (unsigned)x < (unsigned)W;
+                }
+                stage4(bq, xq, yq, tq, ok);
             }
         }
-        const float* row = F.D + (int64_t)y * F.pitch;
-        const float d = __ldg(row + x);
-        const float dr = (r == 1.0f) ? d : __fmul_rn(r, d);
-        sV[b * len + t] = dr;
-        float ex = 0.0f, ey = 0.0f;
-        if (x + 1 < W) {
-            const float d1 = __ldg(row + x + 1);
-            ex = __fsub_rn((r == 1.0f) ? d1 : __fmul_rn(r, d1), dr);
-        }
-        if (y + 1 < H) {
-            const float d1 = __ldg(row + F.pitch + x);
-            ey = __fsub_rn((r == 1.0f) ? d1 : __fmul_rn(r, d1), dr);
-        }
-        const float e2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
-        bool cand = e2 >= a.e2min && __fadd_rn(__fmul_rn(ex, va.c), __fmul_rn(ey, va.s)) > 0.0f;
-        if (cand && F.prop) cand = F.prop[(int64_t)v * tpv + (y / kTile) * F.tiles_x + x / kTile] != 0;
-        if (cand) {
-            const int q = b * len + t;
-            atomicOr(sBits + (q >> 5), 1u << (q & 31));
-            my_cand++;
-        }
     }
-    atomicAdd(&s_cand, my_cand);
+    atomicAdd(&s_cand[0], my_cand[0]);
+    if (nvw > 1) atomicAdd(&s_cand[1], my_cand[1]);
     __syncthreads();
 
-    unsigned long long acc_n = 0, acc_p = 0;
-    // 2-4. Rounds: up to kStripQueue candidates each, in pixel order of the strip.
-    for (int wc = 0; wc < nwords;) {
+    unsigned long long acc_n0 = 0, acc_p0 = 0, acc_n1 = 0, acc_p1 = 0;
+    // 2-4. Rounds: up to kStripQueue candidates each, the first view's in pixel order, then the second view's.
+    const int nw_all = nvw * nwords;
+    for (int wc = 0; wc < nw_all;) {
         // Compaction: words wc, wc + 1, ... while the queue has room (a word that does not fit starts the next round).
         uint32_t nraw = 0;
-        while (wc < nwords) {
+        while (wc < nw_all) {
             const int wi = wc + tid;
-            const uint32_t word = wi < nwords ? sBits[wi] : 0u;
+            const int w = wi >= nwords ? 1 : 0;
+            const int wl = wi - w * nwords;
+            const uint32_t word = wi < nw_all ? sBits[w * (a.strip_px / 32) + wl] : 0u;
             const uint32_t c = __popc(word);
             uint32_t total;
             const uint32_t incl = block_scan(c, s_warp, &total);
@@ -483,13 +548,13 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
                 while (m) {
                     const int j = __ffs(m) - 1;
                     m &= m - 1;
-                    const int q = wi * 32 + j;
+                    const int q = wl * 32 + j;
                     const int b = q / len;
-                    sRaw[pos++] = (uint16_t)((b << 12) | (q - b * len));
+                    sRaw[pos++] = ((uint32_t)w << 16) | ((uint32_t)b << 12) | (uint32_t)(q - b * len);
                 }
             }
             // Words that fit: a prefix of the sweep (incl is non-decreasing).
-            const uint32_t nfit = __syncthreads_count(fits && wi < nwords);
+            const uint32_t nfit = __syncthreads_count(fits && wi < nw_all);
             uint32_t added = 0;
             if (nfit > 0) {
                 // The sum of c over the fitting words is the inclusive count of the last fitting thread.
@@ -509,14 +574,15 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
         __syncthreads();
         for (uint32_t e = tid; e < nraw; e += kStripThreads) {
             const uint32_t ent = sRaw[e];
-            const int b = (int)(ent >> 12), tc = (int)(ent & 4095u);
+            const int w = (int)(ent >> 16), b = (int)((ent >> 12) & 15u), tc = (int)(ent & 4095u);
             int x0, y0, ay, n;
             line_geom(fam, H, W, l0 + b, x0, y0, ay, n);
+            const int16_t* tab = sTab + w * kStripTab;
             int k0, k1, ks;
-            strip_range(sTab, h, tc, n, k0, k1);
-            const LineRef L{sV, sTab, b * len + tc, h};
+            strip_range(tab, h, tc, n, k0, k1);
+            const LineRef L{sV, tab, b * len + tc, h, w << 4};
             const int runs = detect_runs(L, k0, k1, ks);
-            const uint32_t w0 = ent | ((uint32_t)k0 << 16);
+            const uint32_t w0 = (ent & 0xFFFFu) | ((uint32_t)k0 << 16) | ((uint32_t)w << 28);
             if (runs == 1) {
                 sQ[atomicAdd(&s_n1, 1u)] = make_uint2(w0, (uint32_t)k1);
             } else if (runs == 2) {
@@ -525,7 +591,8 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
                 // Three or more macro-runs: listed for the warp kernel (k_scan), which adds its counts to O and M.
                 int x, y;
                 line_pixel(fam, x0, y0, ay, tc, x, y);
-                const uint32_t i = atomicAdd(&F.hdr[HDR_OVF + v], 1u);
+                const int v = w ? vw1 : vw0;
+                const uint32_t i = atomicAdd(&F.hdr[HDR_OVF + v], 1u);   // (rare)
                 if ((int64_t)i < F.cap) {
                     F.cand[(int64_t)v * F.cap + i] = ((uint32_t)y << 16) | (uint32_t)x;
                 } else {
@@ -546,70 +613,75 @@ __global__ void __launch_bounds__(kStripThreads) k_strip(const __grid_constant__
             if (lane == 0) bi = atomicAdd(&s_b1, 1u);
             bi = __shfl_sync(kFullMask, bi, 0);
             if (bi >= nbt) break;
-            {
-                const int pass = bi < nb1 ? 0 : 1;
-                const uint32_t e = (pass == 0 ? bi : bi - nb1) * 32 + lane;
-                const uint32_t nq = pass == 0 ? n1 : n2;
-                if (e < nq) {
-                    const uint2 q = pass == 0 ? sQ[e] : sQ[kStripQueue - 1 - e];
-                    const int b = (int)((q.x >> 12) & 15u), tc = (int)(q.x & 4095u);
-                    const int k0 = (int)(q.x >> 16), k1 = (int)(q.y & 0xFFFFu);
-                    const LineRef L{sV, sTab, b * len + tc, h};
-                    int hit = 0;
-                    if (pass == 0) count_stream(L, k0, k1, zeta, beta, sO, hit);
-                    else count_merge2(L, k0, k1, (int)(q.y >> 16), zeta, beta, sO, hit);
-                    const int n = k1 - k0 + 1;
-                    acc_n += (unsigned long long)n;
-                    acc_p += pair_count(n, 4);
-                    if (kHits && hit && F.hits) {
-                        int x0, y0, ay, nl, x, y;
-                        line_geom(fam, H, W, l0 + b, x0, y0, ay, nl);
-                        line_pixel(fam, x0, y0, ay, tc, x, y);
-                        F.hits[(int64_t)v * tpv + (y / kTile) * F.tiles_x + x / kTile] = 1;
-                    }
+            const int pass = bi < nb1 ? 0 : 1;
+            const uint32_t e = (pass == 0 ? bi : bi - nb1) * 32 + lane;
+            const uint32_t nq = pass == 0 ? n1 : n2;
+            if (e < nq) {
+                const uint2 q = pass == 0 ? sQ[e] : sQ[kStripQueue - 1 - e];
+                const int w = (int)(q.x >> 28);
+                const int b = (int)((q.x >> 12) & 15u), tc = (int)(q.x & 4095u);
+                const int k0 = (int)((q.x >> 16) & 4095u), k1 = (int)(q.y & 0xFFFFu);
+                const LineRef L{sV, sTab + w * kStripTab, b * len + tc, h, w << 4};
+                int hit = 0;
+                if (pass == 0) count_stream(L, k0, k1, zeta, beta, sO, hit);
+                else count_merge2(L, k0, k1, (int)(q.y >> 16), zeta, beta, sO, hit);
+                const int n = k1 - k0 + 1;
+                const unsigned long long pc = pair_count(n, 4);
+                if (w) {
+                    acc_n1 += (unsigned long long)n;
+                    acc_p1 += pc;
+                } else {
+                    acc_n0 += (unsigned long long)n;
+                    acc_p0 += pc;
+                }
+                if (kHits && hit && F.hits) {
+                    int x0, y0, ay, nl, x, y;
+                    line_geom(fam, H, W, l0 + b, x0, y0, ay, nl);
+                    line_pixel(fam, x0, y0, ay, tc, x, y);
+                    F.hits[(int64_t)(w ? vw1 : vw0) * tpv + (y / kTile) * tiles_x + x / kTile] = 1;
                 }
             }
         }
         __syncthreads();
     }
 
-    // 5. O and M of the strip, once; statistics and the candidate count of the view.
-    int32_t* Ov = F.O + (int64_t)v * plane;
-    uint8_t* Mv = F.M + (int64_t)v * plane;
-    for (int i = tid; i < iters; i += kStripThreads) {
-        int b, x, y, t;
-        if (fam == kFamRows) {
-            b = i / W;
-            x = i - b * W;
-            y = l0 + b;
-            t = x;
-        } else {
-            y = i / nb;
-            b = i - y * nb;
-            const int l = l0 + b;
-            if (fam == kFamCols) {
-                x = l;
-                t = y;
-            } else {
-                int x0, y0, ay, n;
-                line_geom(fam, H, W, l, x0, y0, ay, n);
-                x = fam == kFamDiag ? y + (l - (H - 1)) : l - y;
-                if (x < 0 || x >= W) continue;
-                t = x - x0;
-            }
-        }
-        const uint32_t o = o_get(sO, b * len + t);
+    // 5. O and M of the strip's views, once; statistics and the candidate counts of the views.
+    int32_t* OA = F.O + (int64_t)vw0 * plane;
+    uint8_t* MA = F.M + (int64_t)vw0 * plane;
+    int32_t* OB = F.O + (int64_t)vw1 * plane;
+    uint8_t* MB = F.M + (int64_t)vw1 * plane;
+    auto out1 = [&](int b, int x, int y, int t) {
+        const uint32_t o = sO[b * len + t];
         const int64_t g = (int64_t)y * W + x;
-        Ov[g] = (int32_t)o;
-        Mv[g] = o ? 1 : 0;
+        OA[g] = (int32_t)(o & 0xFFFFu);
+        MA[g] = (o & 0xFFFFu) ? 1 : 0;
+        if (nvw > 1) {
+            OB[g] = (int32_t)(o >> 16);
+            MB[g] = (o >> 16) ? 1 : 0;
+        }
+    };
+    if (fam == kFamRows) {
+        for (int b = 0; b < nb; b++)
+            for (int x = tid; x < W; x += kStripThreads) out1(b, x, l0 + b, x);
+    } else if (in_grp) {
+        for (int y = ty; y < H; y += ystep) {
+            const int x = fam == kFamCols ? dl : (fam == kFamDiag ? y + dl : dl - y);
+            if ((unsigned)x >= (unsigned)W) continue;
+            out1(tb, x, y, fam == kFamCols ? y : (fam == kFamDiag ? y - by0 : x - bx0));
+        }
     }
-    atomicAdd(&s_n, acc_n);
-    atomicAdd(&s_p, acc_p);
+    atomicAdd(&s_st[0][0], acc_n0);
+    atomicAdd(&s_st[0][1], acc_p0);
+    if (nvw > 1) {
+        atomicAdd(&s_st[1][0], acc_n1);
+        atomicAdd(&s_st[1][1], acc_p1);
+    }
     __syncthreads();
-    if (tid == 0) {
-        if (s_n) atomicAdd(&F.stats[2 * v], s_n);
-        if (s_p) atomicAdd(&F.stats[2 * v + 1], s_p);
-        if (s_cand) atomicAdd(&F.hdr[HDR_COUNT + v], s_cand);
+    if (tid < nvw) {
+        const int v = tid ? vw1 : vw0;
+        if (s_st[tid][0]) atomicAdd(&F.stats[2 * v], s_st[tid][0]);
+        if (s_st[tid][1]) atomicAdd(&F.stats[2 * v + 1], s_st[tid][1]);
+        if (s_cand[tid]) atomicAdd(&F.hdr[HDR_COUNT + v], s_cand[tid]);
     }
 }
 
@@ -676,8 +748,8 @@ __global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_const
 
 size_t strip_smem(int strip_px)
 {
-    return (size_t)strip_px * 4 + (size_t)strip_px * 2 + (size_t)strip_px / 8 + sizeof(int16_t) * kStripTab +
-           sizeof(uint2) * kStripQueue + sizeof(uint16_t) * kStripQueue;
+    return 16 + (size_t)strip_px * 4 + (size_t)strip_px * 4 + (size_t)strip_px / 4 + sizeof(int16_t) * 2 * kStripTab +
+           sizeof(uint2) * kStripQueue + sizeof(uint32_t) * kStripQueue;
 }
 
 cudaError_t configure_strip()
