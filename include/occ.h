@@ -190,8 +190,8 @@ int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
  *                        (alpha a multiple of 45 degrees) when N = 8 and no side of a frame exceeds 4096 pixels:
  *                        one block owns a strip of adjacent such lines of about strip_px pixels, holds D_r and O of
  *                        it in shared memory and writes O and M once.  0 turns it off (every view takes the
- *                        candidate-list kernels above); otherwise 4096 .. OCC_STRIP_PX_MAX, a multiple of 64
- *                        (default 6144). */
+ *                        candidate-list kernels above); otherwise 1024 .. OCC_STRIP_PX_MAX, a multiple of 64,
+ *                        raised for a call to its longest row, column or diagonal (default 4096). */
 #define OCC_STRIP_PX_MAX 16384
 typedef struct {
     int32_t line_max_runs;

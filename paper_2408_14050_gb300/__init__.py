@@ -32,7 +32,7 @@ STAGES = ["candidates", "scan_lines", "scan_256", "scan_1024", "scan_4096", "mas
 
 OCC_NOALLOC_MAX_PIXEL_VIEWS = 16777216
 OCC_STRIP_PX_MAX = 16384
-STRIP_PX_DEFAULT = 6144      # default occ_tuning.strip_px
+STRIP_PX_DEFAULT = 4096      # default occ_tuning.strip_px
 
 OCC_MAX_FRAMES = 1024
 
@@ -70,7 +70,7 @@ class occ_view_stats(ctypes.Structure):
 
 class occ_tuning(ctypes.Structure):
     """Mapping of the scan work: line_max_runs (0, 1, 2), line_blocks_per_sm, warp_lines_per_block (4, 8), strip_px
-    (0 = no strip kernel, else 4096 .. OCC_STRIP_PX_MAX pixels per strip, a multiple of 64)."""
+    (0 = no strip kernel, else 1024 .. OCC_STRIP_PX_MAX pixels per strip, a multiple of 64)."""
     _fields_ = [("line_max_runs", ctypes.c_int32), ("line_blocks_per_sm", ctypes.c_int32),
                 ("warp_lines_per_block", ctypes.c_int32), ("strip_px", ctypes.c_int32)]
 

@@ -38,7 +38,7 @@ def workload_key(device_name: str, shapes, views, L: int, N: int) -> str:
     return f"{device_name}|{size_class(shapes)}|{scan_bucket(L)}|{angle_class(views)}|N{N}"
 
 
-STRIP_SHAPES = (4096, 6144, 8192, 12288)   # pixels per strip of the strip kernel
+STRIP_SHAPES = (2048, 3072, 4096, 6144)   # pixels per strip of the strip kernel
 
 
 def candidates(max_line_bps: int):

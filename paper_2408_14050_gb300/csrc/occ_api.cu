@@ -1,6 +1,7 @@
 // occ_api.cu -- host side of the C ABI declared in include/occ.h: argument validation, the binary32 direction of each
 // view, the context and its scratch, the launch sequence shared by every entry point (run_frames), status and
 // statistics.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdlib>
@@ -169,7 +170,16 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     }
     const bool list_views = n_strip < nv;
     a.any_list = list_views ? 1 : 0;
-    a.strip_px = n_strip ? sc.tuning.strip_px : 0;
+    // Pixels per strip: the tuning's, raised to the longest line of the call's strip families (a strip holds at least
+    // one whole line), rounded up to a multiple of 64.
+    int strip_px = 0;
+    if (n_strip) {
+        strip_px = sc.tuning.strip_px;
+        for (int f = 0; f < nf; f++)
+            for (int g = 0; g < a.ngroups; g++) strip_px = std::max(strip_px, fam_len(a.group[g].fam, fr[f].H, fr[f].W));
+        strip_px = (strip_px + 63) & ~63;
+    }
+    a.strip_px = strip_px;
     const bool lines = list_views && (a.N / 2) <= kLineMaxHalf && sc.tuning.line_max_runs > 0;
     a.nf = nf;
     a.use_fb = lines ? 1 : 0;
@@ -180,6 +190,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.pref_cls = sc.pref + (nf * nv + 1);
     a.pref_ovf = sc.pref + (1 + kNumClasses) * (nf * nv + 1);
     a.ptab = sc.ptab;
+    a.stab = sc.stab;
     a.status = sc.status;
     a.line_ctr = sc.status + 1;   // the status region has room for the counters
     a.brk = sc.brk;
@@ -255,7 +266,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
         for (int k = 0; k < kNumClasses; k++) run_cls[k] = (k == c);
     }
-    if (!mark(0) || (lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
+    if (!mark(0) || ((lines || n_strip) && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
         launch_plan(a, st) != cudaSuccess || !mark(1))
         return OCC_ERR_CUDA;
     // The strip views: O and M written once per strip; the lines of three or more macro-runs are listed for the warp
@@ -397,7 +408,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     const size_t sz_frames = align256(sizeof(FrameArg) * kMaxFrames);
     const size_t sz_plan = align256(sizeof(PlanEntry) * nfv);
     const size_t sz_pref = align256(sizeof(uint32_t) * (1 + 2 * kNumClasses) * (nfv + 1));
-    const size_t sz_tab = align256(sizeof(int32_t) * kTabLen * max_views);
+    const size_t sz_tab = align256(sizeof(int32_t) * kTabLen * max_views) + align256(sizeof(int16_t) * kSTabLen * max_views);
     const size_t total = sz_hdr + sz_stats + sz_status + sz_frames + sz_plan + sz_pref + sz_tab;
     sc.cand_entries = ctx->cand_cap * max_views;
     sc.fb_entries = (ctx->cand_cap / 32 + kMaxFrames + 1) * (int64_t)max_views;
@@ -424,6 +435,7 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     sc.plan = reinterpret_cast<PlanEntry*>(p); p += sz_plan;
     sc.pref = reinterpret_cast<uint32_t*>(p); p += sz_pref;
     sc.ptab = reinterpret_cast<int32_t*>(p);
+    sc.stab = reinterpret_cast<int16_t*>(p + align256(sizeof(int32_t) * kTabLen * max_views));
     sc.cand = ctx->d_cand;
     sc.fb = ctx->d_fb;
     sc.brk = ctx->d_brk;
@@ -535,7 +547,7 @@ int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t)
     if (!t) t = &d;
     if (t->line_max_runs < 0 || t->line_max_runs > 2 || t->line_blocks_per_sm < 1 ||
         t->line_blocks_per_sm > ctx->sc.lines_bps_max || (t->warp_lines_per_block != 4 && t->warp_lines_per_block != 8) ||
-        (t->strip_px != 0 && (t->strip_px < kStripMaxSide || t->strip_px > OCC_STRIP_PX_MAX || (t->strip_px & 63))))
+        (t->strip_px != 0 && (t->strip_px < 1024 || t->strip_px > OCC_STRIP_PX_MAX || (t->strip_px & 63))))
         return OCC_ERR_INVALID_ARG;
     ctx->sc.tuning = *t;
     return OCC_OK;

@@ -46,6 +46,9 @@ constexpr int kLineMaxHalf = 4;
 // Position tables: per view, for g = -kTabHalf .. kTabHalf, round(fl(cos a * g)) and round(fl(sin a * g)).
 constexpr int kTabHalf = (OCC_MAX_SCAN + 1) / 2;
 constexpr int kTabLen = 2 * kTabHalf + 1;
+// Per view, for g = -kTabHalf .. kTabHalf + 8: the strip kernel's offset round(fl(cc * g)) of sample g along its line
+// (the entries past kTabHalf keep reads a step or two ahead of a line's end in bounds).
+constexpr int kSTabLen = kTabLen + 8;
 
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
@@ -62,7 +65,7 @@ struct ViewArg {
 enum : int { kFamRows = 0, kFamCols = 1, kFamDiag = 2, kFamAnti = 3 };
 constexpr int kStripMaxSide = 4096;
 constexpr int kStripMaxLines = 16;   // lines of one strip (4 bits of a queue entry; the position takes 12)
-constexpr int kStripPxDefault = 6144;
+constexpr int kStripPxDefault = 4096;
 
 __host__ __device__ __forceinline__ int fam_lines(int fam, int H, int W)
 {
@@ -151,6 +154,7 @@ struct Args {
     uint32_t* pref_all;           // [nf * nv + 1] prefix of the candidate counts of every (frame, view)
     uint32_t* pref_cls;           // [kNumClasses][nf * nv + 1] the same restricted to each size class
     int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact
+    int16_t* stab;                // [nv][kSTabLen] strip offsets (see kSTabLen)
     uint32_t* status;             // OR of every frame's status bits
     uint32_t* line_ctr;           // work counter of the line kernel, zero at the start of a call
     uint32_t* brk;                // lists of the merge kernel: from the front, the work items of the lines of more than
@@ -210,6 +214,7 @@ struct Scratch {
     PlanEntry* plan;               // [max_frames * max_views]
     uint32_t* pref;                // [(1 + kNumClasses) * (max_frames * max_views + 1)]
     int32_t* ptab;                 // [max_views][kTabLen]
+    int16_t* stab;                 // [max_views][kSTabLen]
     uint32_t* cand;                // candidate list pool
     int64_t cand_entries;
     uint32_t* fb;                  // line-flag pool (words)

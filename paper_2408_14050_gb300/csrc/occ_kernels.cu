@@ -452,15 +452,20 @@ constexpr int32_t kTabExact = (int32_t)0x80008000;
 
 __global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Args a)
 {
-    const int64_t total = (int64_t)a.nv * kTabLen;
+    const int64_t total = (int64_t)a.nv * kSTabLen;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < total; i += (int64_t)gridDim.x * 256) {
-        const int v = (int)(i / kTabLen);
-        const float g = (float)((int)(i - (int64_t)v * kTabLen) - kTabHalf);
+        const int v = (int)(i / kSTabLen);
+        const int j = (int)(i - (int64_t)v * kSTabLen);
+        const float g = (float)(j - kTabHalf);
         const float tx = __fmul_rn(a.view[v].c, g), ty = __fmul_rn(a.view[v].s, g);
+        // Strip views: the sample's offset along its row, column or diagonal (rounded like Eq. 4, which it equals
+        // there; see kStripMaxSide).
+        a.stab[i] = (int16_t)(int)roundf(a.view[v].fam == kFamCols ? ty : tx);
+        if (j >= kTabLen) continue;
         const float fx = tx - floorf(tx), fy = ty - floorf(ty);   // exact: the fraction of a binary32 value
         const bool risky = fabsf(fx - 0.5f) <= 0.00390625f || fabsf(fy - 0.5f) <= 0.00390625f;
         const int dx = (int)roundf(tx), dy = (int)roundf(ty);
-        a.ptab[i] = risky ? kTabExact : (int32_t)((uint32_t)(dx & 0xFFFF) | ((uint32_t)dy << 16));
+        a.ptab[(int64_t)v * kTabLen + j] = risky ? kTabExact : (int32_t)((uint32_t)(dx & 0xFFFF) | ((uint32_t)dy << 16));
     }
 }
 
@@ -1618,7 +1623,7 @@ cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st)
 
 cudaError_t launch_tables(const Args& a, cudaStream_t st)
 {
-    const int64_t total = (int64_t)a.nv * kTabLen;
+    const int64_t total = (int64_t)a.nv * kSTabLen;
     k_tables<<<(int)((total + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }

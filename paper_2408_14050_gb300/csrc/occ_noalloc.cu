@@ -27,7 +27,8 @@ constexpr size_t kOffPlan = kOffFrames + align_up(sizeof(FrameArg));
 constexpr size_t kOffPref = kOffPlan + align_up(sizeof(PlanEntry) * OCC_MAX_VIEWS);
 constexpr size_t kOffTab = kOffPref + align_up(sizeof(uint32_t) * (1 + 2 * kNumClasses) * (OCC_MAX_VIEWS + 1));
 constexpr size_t kFlagWords = OCC_NOALLOC_MAX_PIXEL_VIEWS / 32 + OCC_MAX_VIEWS;
-constexpr size_t kOffFlags = kOffTab + align_up(sizeof(int32_t) * kTabLen * OCC_MAX_VIEWS);
+constexpr size_t kOffSTab = kOffTab + align_up(sizeof(int32_t) * kTabLen * OCC_MAX_VIEWS);
+constexpr size_t kOffFlags = kOffSTab + align_up(sizeof(int16_t) * kSTabLen * OCC_MAX_VIEWS);
 constexpr size_t kBrkEntries = OCC_NOALLOC_MAX_PIXEL_VIEWS;
 constexpr size_t kOffBrk = kOffFlags + align_up(sizeof(uint32_t) * kFlagWords);
 constexpr size_t kOffCand = kOffBrk + align_up(sizeof(uint32_t) * kBrkEntries);
@@ -65,6 +66,7 @@ cudaError_t setup_device(DeviceSetup& s)
     sc.plan = reinterpret_cast<PlanEntry*>(p + kOffPlan);
     sc.pref = reinterpret_cast<uint32_t*>(p + kOffPref);
     sc.ptab = reinterpret_cast<int32_t*>(p + kOffTab);
+    sc.stab = reinterpret_cast<int16_t*>(p + kOffSTab);
     sc.fb = reinterpret_cast<uint32_t*>(p + kOffFlags);
     sc.fb_entries = (int64_t)kFlagWords;
     sc.brk = reinterpret_cast<uint32_t*>(p + kOffBrk);

@@ -33,8 +33,6 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kStripThreads = 128;
 constexpr int kStripWarps = kStripThreads / 32;
 constexpr int kStripQueue = 512;           // queue entries of one round
-constexpr int kStripTab = 4104;            // offsets of samples k = 0 .. 2h (h <= 2047), then 0 for k = 2h + 1 .. 2h + 4
-                                           // (reads one or two samples ahead need no bound check)
 
 // First pixel (x0, y0), step (ax, ay) per position and length n of line l of a family.
 __device__ __forceinline__ void line_geom(int fam, int H, int W, int l, int& x0, int& y0, int& ay, int& n)
@@ -132,7 +130,7 @@ struct LineRef {
 
 __device__ __forceinline__ void sample(const LineRef& L, int k, float& w, float& v, int& p)
 {
-    p = L.base + L.tab[k];
+    p = L.base + __ldg(L.tab + k);
     v = L.sV[p];
     w = __fsub_rn((float)(k - L.h), v);
 }
@@ -144,16 +142,16 @@ __device__ __forceinline__ int detect_runs(const LineRef& L, int k0, int k1, int
 {
     const float kNegInf = __int_as_float(0xff800000);
     float g = (float)(k0 - L.h);
-    float bufw = __fsub_rn(g, L.sV[L.base + L.tab[k0]]);
+    float bufw = __fsub_rn(g, L.sV[L.base + __ldg(L.tab + k0)]);
     float lastw = kNegInf;
     int runs = 1;
     ks = -1;
     int k = k0 + 1;
-    int tn = L.tab[k];   // k <= 2h + 1: the table's padding keeps the read in bounds
+    int tn = __ldg(L.tab + k);   // k <= 2h + 1: the view's table runs past g = h (kSTabLen)
 #define OCC_DSTEP                                                                    \
     {                                                                                \
         const float v = L.sV[L.base + tn];                                           \
-        tn = L.tab[k + 1];                                                           \
+        tn = __ldg(L.tab + k + 1);                                                   \
         g = __fadd_rn(g, 1.0f);                                                      \
         const float w = __fsub_rn(g, v);                                             \
         const bool sb = w < bufw;                                                    \
@@ -191,9 +189,9 @@ __device__ __forceinline__ void count_stream(const LineRef& L, int k0, int k1, f
     float g = (float)(k0 - L.h);
     // The sample in flight (k) and the table offset of the one after it.
     int k = k0 + 1;
-    int pn = L.base + L.tab[k];   // k + 2 <= 2h + 3 below: the table's padding keeps the reads in bounds
+    int pn = L.base + __ldg(L.tab + k);   // k + 2 <= 2h + 2 below: the view's table runs past g = h (kSTabLen)
     float vn = L.sV[pn];
-    int tn = L.tab[k + 1];
+    int tn = __ldg(L.tab + k + 1);
     int rem = k1 - k0;
 #define OCC_RSTEP(J)                                                                 \
     {                                                                                \
@@ -203,7 +201,7 @@ __device__ __forceinline__ void count_stream(const LineRef& L, int k0, int k1, f
         const float sw = __fsub_rn(g, sv);                                           \
         pn = L.base + tn;                                                            \
         vn = L.sV[pn];                                                               \
-        tn = L.tab[k + 2];                                                           \
+        tn = __ldg(L.tab + k + 2);                                                   \
         k++;                                                                         \
         const bool sb = sw < bw;                                                     \
         const float ew = sb ? sw : bw, ev = sb ? sv : bv;                            \
@@ -312,7 +310,7 @@ __device__ __forceinline__ void count_merge2(const LineRef& L, int k0, int k1, i
 // form one interval of k around k = h (the candidate itself).
 __device__ __forceinline__ void strip_range(const int16_t* tab, int h, int tc, int n, int& k0, int& k1)
 {
-    auto inside = [&](int k) { return (unsigned)(tc + tab[k]) < (unsigned)n; };
+    auto inside = [&](int k) { return (unsigned)(tc + __ldg(tab + k)) < (unsigned)n; };
     int lo = 0, hi = h;
     while (lo < hi) {
         const int m = (lo + hi) >> 1;
@@ -412,25 +410,20 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_strip(const __grid_constan
     const int64_t plane = (int64_t)H * W;
 
     // Shared memory: a guard word (a sample read one step ahead of a line's end may fall one position before its
-    // first), D_r of the lines, the O words, the candidate bits of each view, each view's table of sample offsets,
-    // the line queue and the round's candidates.
+    // first), D_r of the lines, the O words, the candidate bits of each view, the line queue and the round's
+    // candidates.  Each view's sample offsets (k = 0 .. 2h + 4) come from its table in global memory (L1).
     float* sV = reinterpret_cast<float*>(smem + 16);                                        // [nb][len]
     uint32_t* sO = reinterpret_cast<uint32_t*>(smem + 16 + (size_t)a.strip_px * 4);         // [nb][len]
     uint32_t* sBits = sO + a.strip_px;                                                      // [2][strip_px / 32]
-    int16_t* sTab = reinterpret_cast<int16_t*>(sBits + 2 * (a.strip_px / 32));              // [2][kStripTab]
-    uint2* sQ = reinterpret_cast<uint2*>(sTab + 2 * kStripTab);                             // [kStripQueue]
+    uint2* sQ = reinterpret_cast<uint2*>(sBits + 2 * (a.strip_px / 32));                    // [kStripQueue]
     uint32_t* sRaw = reinterpret_cast<uint32_t*>(sQ + kStripQueue);                         // [kStripQueue]
+    const int16_t* tabs[2] = {a.stab + (int64_t)vw0 * kSTabLen + (kTabHalf - h),
+                              a.stab + (int64_t)vw1 * kSTabLen + (kTabHalf - h)};
 
     const int npx = nb * len;   // shared positions of the strip (lines shorter than len leave some unused)
     const int nwords = (npx + 31) >> 5;
     for (int i = tid; i < npx; i += kStripThreads) sO[i] = 0;
     for (int i = tid; i < 2 * nwords; i += kStripThreads) sBits[(i < nwords ? 0 : a.strip_px / 32 - nwords) + i] = 0;
-    for (int w = 0; w < nvw; w++) {
-        const ViewArg& vv = w ? vb : va;
-        const float cc = fam == kFamCols ? vv.s : vv.c;
-        for (int k = tid; k <= 2 * h + 4; k += kStripThreads)
-            sTab[w * kStripTab + k] = k <= 2 * h ? (int16_t)(int)roundf(__fmul_rn(cc, (float)(k - h))) : (int16_t)0;
-    }
     if (tid < 2) {
         s_cand[tid] = 0;
         s_st[tid][0] = s_st[tid][1] = 0;
@@ -577,7 +570,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_strip(const __grid_constan
             const int w = (int)(ent >> 16), b = (int)((ent >> 12) & 15u), tc = (int)(ent & 4095u);
             int x0, y0, ay, n;
             line_geom(fam, H, W, l0 + b, x0, y0, ay, n);
-            const int16_t* tab = sTab + w * kStripTab;
+            const int16_t* tab = w ? tabs[1] : tabs[0];
             int k0, k1, ks;
             strip_range(tab, h, tc, n, k0, k1);
             const LineRef L{sV, tab, b * len + tc, h, w << 4};
@@ -621,7 +614,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_strip(const __grid_constan
                 const int w = (int)(q.x >> 28);
                 const int b = (int)((q.x >> 12) & 15u), tc = (int)(q.x & 4095u);
                 const int k0 = (int)((q.x >> 16) & 4095u), k1 = (int)(q.y & 0xFFFFu);
-                const LineRef L{sV, sTab + w * kStripTab, b * len + tc, h, w << 4};
+                const LineRef L{sV, w ? tabs[1] : tabs[0], b * len + tc, h, w << 4};
                 int hit = 0;
                 if (pass == 0) count_stream(L, k0, k1, zeta, beta, sO, hit);
                 else count_merge2(L, k0, k1, (int)(q.y >> 16), zeta, beta, sO, hit);
@@ -748,8 +741,8 @@ __global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_const
 
 size_t strip_smem(int strip_px)
 {
-    return 16 + (size_t)strip_px * 4 + (size_t)strip_px * 4 + (size_t)strip_px / 4 + sizeof(int16_t) * 2 * kStripTab +
-           sizeof(uint2) * kStripQueue + sizeof(uint32_t) * kStripQueue;
+    return 16 + (size_t)strip_px * 4 + (size_t)strip_px * 4 + (size_t)strip_px / 4 + sizeof(uint2) * kStripQueue +
+           sizeof(uint32_t) * kStripQueue;
 }
 
 cudaError_t configure_strip()

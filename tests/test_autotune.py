@@ -58,7 +58,7 @@ def test_every_tuning_gives_the_same_result(tmp_path):
         assert again == best
         with pytest.raises(occ.OccError):
             occ.occ_set_tuning(ctx, {"line_max_runs": 3, "line_blocks_per_sm": 1, "warp_lines_per_block": 8})
-        for px in (2048, 4100, occ.OCC_STRIP_PX_MAX + 64):      # below a frame side, not a multiple of 64, too large
+        for px in (512, 4100, occ.OCC_STRIP_PX_MAX + 64):       # too small, not a multiple of 64, too large
             with pytest.raises(occ.OccError):
                 occ.occ_set_tuning(ctx, {"line_max_runs": 2, "line_blocks_per_sm": 1, "warp_lines_per_block": 8,
                                          "strip_px": px})
