@@ -150,9 +150,21 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------------------------
 # Our arm
 
-# Kernels one occ_detect queues: frame table, position tables, candidates, plan, line-per-thread scan, merge of the
-# lines it lists, the three warp scan classes, mask.
-LAUNCHES_PER_DETECT = 10
+
+
+def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -> int:
+    """Kernels one occ_detect queues.  Views whose scan lines stay on a row, column or diagonal (alpha a multiple of
+    45 degrees) take the strip kernel when N = 8 and the tuning enables it: frame table, position tables, edges
+    (min/max), plan, strips, prefix sums of the listed long lines, the three warp scan classes.  Any other view adds
+    the candidate-list kernels: line-per-thread scan and its merge (when line_max_runs > 0) and the mask."""
+    strip_ok = tuning.get("strip_px", 0) > 0 and N == 8 and max_side <= 4096
+    strip = [strip_ok and abs((a % 45.0)) < 1e-9 for a, _ in views]
+    n = 3 + 1 + 3          # frames, tables, edges; plan; three warp classes
+    if any(strip):
+        n += 2
+    if not all(strip):
+        n += 1 + (2 if tuning.get("line_max_runs", 2) > 0 and N <= 8 else 0)
+    return n
 
 # DRAM bytes (read + write) per detect call of the scan stage (all its launches) from the ncu capture summarised in
 # profiles/, valid only for the kernel code it was taken on (sha256 prefix of csrc/occ_kernels.cu without comments
@@ -172,9 +184,12 @@ def code_sha(src: str) -> str:
 
 
 def kernels_sha() -> str:
-    path = os.path.join(ROOT, "paper_2408_14050_gb300", "csrc", "occ_kernels.cu")
-    with open(path, encoding="utf-8") as f:
-        return code_sha(f.read())
+    """Code hash of the scan kernels (the list kernels' and the strip kernel's sources, concatenated)."""
+    src = ""
+    for name in ("occ_kernels.cu", "occ_strip.cu"):
+        with open(os.path.join(ROOT, "paper_2408_14050_gb300", "csrc", name), encoding="utf-8") as f:
+            src += f.read()
+    return code_sha(src)
 
 
 def measured_traffic(kernel: str):
@@ -294,7 +309,9 @@ def run_ours(args):
         achieved = ops / (scan_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(alu_peak / 1e9, 1), "unit": "Gop/s",
                 "frac": round(achieved / (alu_peak / 1e9), 4), "traffic": measured_traffic("scan"),
-                "kernel": "scan stage: k_scan_lines + k_merge_lines + k_scan<256|1024|4096> (Eq. 4-6)",
+                "kernel": ("scan stage: k_strip + k_plan_ovf + k_scan<256|1024|4096> (Eq. 1-6 on strips of rows, "
+                           "columns and diagonals)" if tuning.get("strip_px", 0) else
+                           "scan stage: k_scan_lines + k_merge_lines + k_scan<256|1024|4096> (Eq. 4-6)"),
                 "launch_ms": round(scan_ms, 4),
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz", "ops_per_launch": ops}
     else:
@@ -376,7 +393,7 @@ def run_ours(args):
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": args.steps * LAUNCHES_PER_DETECT,
+            "gpu_launches": args.steps * launches_per_detect(views, tuning, 8, max(H, W)),
             "clocks": clk,
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
             "stage_ms_source": f"{PROFILED_STEPS} calls with per-stage events, after the timed steps",
@@ -558,6 +575,57 @@ def run_fusion(args, dev, frame, views):
 NET_FWD_FLOP_PER_PX = 2 * 9 * (1 * 16 + 16 * 16 + 16 * 32 + 32 * 16)
 
 
+def ideal_proposal_sweep(dev, views, sigmas=(0.0, 0.1, 0.25), per_size: int = 4, reps: int = 5):
+    """Upper bound of what any tile proposer can gain: the plain method run with the ideal proposal (exactly the tiles
+    whose scan lines find an occlusion, taken from the plain run's own tile hit flags), which gives the plain masks
+    (it only drops scan lines that add nothing), against the plain method on the same batch; for noise levels sigma
+    of the mixed-resolution recipe.  A learned proposer can only do worse: it also pays for its network."""
+    import dataclasses
+
+    import torch
+
+    import paper_2408_14050_gb300 as occ
+    out = []
+    for sigma in sigmas:
+        frames = []
+        for i, (H, W) in enumerate(scenes.MIXED_SIZES * per_size):
+            spec = dataclasses.replace(scenes.spec_array(H, W), sigma=float(sigma))
+            frames.append(torch.from_numpy(scenes.make_scene(spec, scenes.seed_of(34, i))).to(dev))
+        px = sum(int(f.numel()) for f in frames)
+        V = len(views)
+        ctx = occ.occ_create(dev.index, max_pixels=px, max_views=V)
+        Ms = [torch.empty((V, *f.shape), dtype=torch.uint8, device=dev) for f in frames]
+        Os = [torch.empty((V, *f.shape), dtype=torch.int32, device=dev) for f in frames]
+        hits = [torch.empty((V, *occ.tiles_of(*f.shape)), dtype=torch.uint8, device=dev) for f in frames]
+        occ.occ_detect_batched(ctx, frames, views, Ms=Ms, Os=Os, hits=hits)
+        M_plain = [m.clone() for m in Ms]
+        props = [h.clone() for h in hits]
+
+        def timed(fn):
+            for _ in range(2):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        ms_plain = timed(lambda: occ.occ_detect_batched(ctx, frames, views, Ms=Ms, Os=Os))
+        ms_ideal = timed(lambda: occ.occ_detect_batched(ctx, frames, views, Ms=Ms, Os=Os, proposals=props))
+        same = all(torch.equal(a, b) for a, b in zip(Ms, M_plain))
+        if occ.occ_get_status(ctx) != occ.OCC_OK or not same:
+            raise RuntimeError("ideal proposal run differs from the plain masks")
+        tiles = sum(int(h.numel()) for h in hits)
+        kept = sum(int(h.sum().item()) for h in hits)
+        ctx.close()
+        out.append({"sigma": sigma, "frames": len(frames), "ms_plain": round(ms_plain, 3),
+                    "ms_ideal_proposal": round(ms_ideal, 3), "speedup_bound": round(ms_plain / ms_ideal, 4),
+                    "tiles_skipped": round(1 - kept / tiles, 4)})
+    return out
+
+
 def run_learned(args, dev, views):
     """The learned tile proposer (trained here on the GPU with the library's own kernels on labels of the plain
     method) against the plain method on the mixed-size batch: pixel recall and precision of the masks, tiles skipped,
@@ -593,6 +661,8 @@ def run_learned(args, dev, views):
     cctx.close()
     del cal_frames
 
+    sweep = ideal_proposal_sweep(dev, views)
+
     wl = scenes.mixed_batch(n_frames=args.learned_eval_frames, workers=workers)
     frames = [torch.from_numpy(f).to(dev) for f in wl.frames]
     px = sum(int(f.numel()) for f in frames)
@@ -622,6 +692,7 @@ def run_learned(args, dev, views):
         "roofline": {"bound": "tensor", "kernel": "k_conv_tma / k_conv (network forward, all layers)",
                      "achieved": round(tflops, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(tflops / peak, 4),
                      "flop_per_px": NET_FWD_FLOP_PER_PX, "peak_source": src},
+        "ideal_proposal_sweep": sweep,
         "eval": f"{len(frames)} mixed frames ({', '.join(sorted({f'{f.shape[1]}x{f.shape[0]}' for f in frames}))}),"
                 " 8 views; masks of the proposed run are a subset of the plain masks by construction",
     }
