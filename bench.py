@@ -510,6 +510,28 @@ def run_stress(args, dev, rank, world):
     if occ.occ_get_status(ctx) != occ.OCC_OK:
         raise RuntimeError("stress detect failed")
     ctx.close()
+    # The batched form on the same workload: two 4096x2160 maps of the recipe (frames 0 and 1) in one
+    # occ_detect_batched call, with the tuning the single-frame call used.
+    D2 = [D, torch.from_numpy(scenes.stress_5x5(frame=1).frames[0]).to(dev)]
+    bctx = occ.occ_create(dev.index, max_pixels=2 * H * W, max_views=V)
+    occ.occ_set_tuning(bctx, tuning)
+    Ms2 = [M, torch.empty_like(M)]
+    Os2 = [O, torch.empty_like(O)]
+    occ.occ_detect_batched(bctx, D2, wl.views, p, Ms=Ms2, Os=Os2)
+    bsteps = 3
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(bsteps):
+        occ.occ_detect_batched(bctx, D2, wl.views, p, Ms=Ms2, Os=Os2)
+    e1.record()
+    torch.cuda.synchronize()
+    tb = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+    if occ.occ_get_status(bctx) != occ.OCC_OK:
+        raise RuntimeError("stress batched detect failed")
+    bctx.close()
+    batched = {"value": round(bsteps * world * 2 * H * W * V / tb / 1e6, 1), "unit": UNIT,
+               "ms_per_step": round(tb / bsteps * 1e3, 3), "frames": 2, "steps": bsteps,
+               "api": "occ_detect_batched, two 4096x2160 maps, 24 views"}
     ms = t / steps * 1e3
     ops = 8 * samples + 3 * pairs
     scan_ms = ms - stage["candidates"] - stage["mask"]
@@ -520,7 +542,7 @@ def run_stress(args, dev, rank, world):
             "samples_per_s": round(samples / (ms / 1e3)),
             "scan_alu_frac": round(ops / (scan_ms / 1e3) / alu_peak, 4),
             "stage_ms": {k: round(v, 3) for k, v in stage.items()}, "steps": steps, "tuning": tuning,
-            "l2": "inputs and outputs larger than L2", "clocks": clk}
+            "l2": "inputs and outputs larger than L2", "clocks": clk, "batched": batched}
 
 
 def run_fusion(args, dev, frame, views):
