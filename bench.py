@@ -166,11 +166,12 @@ def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -
         n += 1 + (2 if tuning.get("line_max_runs", 2) > 0 and N <= 8 else 0)
     return n
 
-# DRAM bytes (read + write) per detect call of the scan stage (all its launches) from the ncu capture summarised in
-# profiles/, valid only for the kernel code it was taken on (sha256 prefix of csrc/occ_kernels.cu without comments
-# and blank space); reported as null otherwise.
+# DRAM bytes (read + write) per detect call of the scan stage (all its launches: the strip kernel, the prefix sums of
+# its listed lines and the warp kernels) from the ncu launch list summarised in profiles/, valid only for the kernel
+# code it was taken on (sha256 prefix of csrc/occ_kernels.cu + csrc/occ_strip.cu without comments and blank space);
+# reported as null otherwise.
 PROFILED_STEPS = 20   # occ_detect calls with per-stage events after the timed region (stage_ms)
-MEASURED_TRAFFIC = {"scan": {"bytes": 115355989, "kernels_sha": "64c6ffc13a48d26d"}}
+MEASURED_TRAFFIC = {"scan": {"bytes": 48391040, "kernels_sha": "4ef7ed40da43bbea"}}
 
 
 def code_sha(src: str) -> str:
