@@ -153,25 +153,25 @@ class ClockSampler:
 
 
 def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -> int:
-    """Kernels one occ_detect queues.  Views whose scan lines stay on a row, column or diagonal (alpha a multiple of
-    45 degrees) take the strip kernel when N = 8 and the tuning enables it: frame table, position tables, edges
-    (min/max), plan, strips, prefix sums of the listed long lines, the three warp scan classes.  Any other view adds
-    the candidate-list kernels: line-per-thread scan and its merge (when line_max_runs > 0) and the mask."""
+    """Kernels one occ_detect queues (no E, A or tile outputs).  Views whose scan lines stay on a row, column or
+    diagonal (alpha a multiple of 45 degrees) take the strip kernel when N = 8 and the tuning enables it.  All views
+    on strips: frame table, min/max with the position tables, plan, strips, prefix sums of the listed long lines, the
+    three warp scan classes.  Otherwise: frame table, position tables (when some kernel uses them), edges and
+    candidates, plan, the strips and their prefix sums (if any view takes them), the line-per-thread scan and its
+    merge (when line_max_runs > 0), the three warp scan classes, the mask."""
     strip_ok = tuning.get("strip_px", 0) > 0 and N == 8 and max_side <= 4096
     strip = [strip_ok and abs((a % 45.0)) < 1e-9 for a, _ in views]
-    n = 3 + 1 + 3          # frames, tables, edges; plan; three warp classes
+    lines = tuning.get("line_max_runs", 2) > 0 and N <= 8
+    if all(strip):
+        return 8
+    n = 1 + 1 + 1 + 3 + 1          # frames, edges, plan, three warp classes, mask
     if any(strip):
         n += 2
-    if not all(strip):
-        n += 1 + (2 if tuning.get("line_max_runs", 2) > 0 and N <= 8 else 0)
+    if lines:
+        n += 2
+    if lines or any(strip):
+        n += 1                     # tables
     return n
-
-# DRAM bytes (read + write) per detect call of the scan stage (all its launches: the strip kernel, the prefix sums of
-# its listed lines and the warp kernels) from the ncu launch list summarised in profiles/, valid only for the kernel
-# code it was taken on (sha256 prefix of csrc/occ_kernels.cu + csrc/occ_strip.cu without comments and blank space);
-# reported as null otherwise.
-PROFILED_STEPS = 20   # occ_detect calls with per-stage events after the timed region (stage_ms)
-MEASURED_TRAFFIC = {"scan": {"bytes": 48391040, "kernels_sha": "4ef7ed40da43bbea"}}
 
 
 def code_sha(src: str) -> str:

@@ -266,9 +266,18 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
         for (int k = 0; k < kNumClasses; k++) run_cls[k] = (k == c);
     }
-    if (!mark(0) || ((lines || n_strip) && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
-        launch_plan(a, st) != cudaSuccess || !mark(1))
+    // Every view on strips and no E, A or hit flags asked for: one read of D for Eq. 3 (with the tables in the same
+    // launch) is all the candidate pass has to do.
+    bool extras = a.hits != 0;
+    for (int f = 0; f < nf; f++) extras = extras || fr[f].E || fr[f].A;
+    const bool minmax_only = !list_views && !extras;
+    if (!mark(0)) return OCC_ERR_CUDA;
+    if (minmax_only) {
+        if (launch_minmax(a, st) != cudaSuccess) return OCC_ERR_CUDA;
+    } else if (((lines || n_strip) && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess) {
         return OCC_ERR_CUDA;
+    }
+    if (launch_plan(a, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
     // The strip views: O and M written once per strip; the lines of three or more macro-runs are listed for the warp
     // kernels below, which add their counts to O and M.
     if (n_strip && (launch_strip(a, st) != cudaSuccess || launch_plan_ovf(a, st) != cudaSuccess)) return OCC_ERR_CUDA;

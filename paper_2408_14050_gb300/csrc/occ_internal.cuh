@@ -184,6 +184,9 @@ struct FrameChunk {
 cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st);
 cudaError_t launch_tables(const Args& a, cudaStream_t st);
 cudaError_t launch_edges(const Args& a, cudaStream_t st);
+// k_edges' min/max and non-finite check alone, with the position tables (k_tables) in the same launch: for calls with
+// no candidate-list view and no E, A or tile hit outputs.
+cudaError_t launch_minmax(const Args& a, cudaStream_t st);
 cudaError_t launch_plan(const Args& a, cudaStream_t st);
 // The line-per-thread scan over every view; wide = true when some frame's offsets need 64 bits.
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);

@@ -323,6 +323,100 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------------------------------------------------------
+// k_minmax: what k_edges does when no view takes the candidate lists and neither E, A nor tile hit flags are asked
+// for -- the min/max of D (Eq. 3) and the non-finite check, one read of D, four pixels per thread and step -- and, in
+// the blocks of grid row nf, the position tables (as k_tables).
+
+constexpr int kMinMaxThreads = 256;
+
+// Marks a position-table entry whose nearest pixel must be computed exactly (see k_tables).
+constexpr int32_t kTabExact = (int32_t)0x80008000;
+
+// Entry i of the position tables (view i / kSTabLen, g = i % kSTabLen - kTabHalf): the strip kernel's offset along the
+// view's row, column or diagonal (rounded like Eq. 4, which it equals there; see kStripMaxSide), and for g <= kTabHalf
+// the list kernels' packed pixel offsets.
+__device__ __forceinline__ void tables_entry(const Args& a, int64_t i)
+{
+    const int v = (int)(i / kSTabLen);
+    const int j = (int)(i - (int64_t)v * kSTabLen);
+    const float g = (float)(j - kTabHalf);
+    const float tx = __fmul_rn(a.view[v].c, g), ty = __fmul_rn(a.view[v].s, g);
+    a.stab[i] = (int16_t)(int)roundf(a.view[v].fam == kFamCols ? ty : tx);
+    if (j >= kTabLen) return;
+    const float fx = tx - floorf(tx), fy = ty - floorf(ty);
+    const bool risky = fabsf(fx - 0.5f) <= 0.00390625f || fabsf(fy - 0.5f) <= 0.00390625f;
+    const int dx = (int)roundf(tx), dy = (int)roundf(ty);
+    a.ptab[(int64_t)v * kTabLen + j] = risky ? kTabExact : (int32_t)((uint32_t)(dx & 0xFFFF) | ((uint32_t)dy << 16));
+}
+
+__global__ void __launch_bounds__(kMinMaxThreads) k_minmax(const __grid_constant__ Args a)
+{
+    if ((int)blockIdx.y == a.nf) {
+        const int64_t total = (int64_t)a.nv * kSTabLen;
+        for (int64_t i = (int64_t)blockIdx.x * kMinMaxThreads + threadIdx.x; i < total;
+             i += (int64_t)gridDim.x * kMinMaxThreads)
+            tables_entry(a, i);
+        return;
+    }
+    __shared__ float s_lo[kMinMaxThreads / 32], s_hi[kMinMaxThreads / 32];
+    __shared__ int s_bad;
+    const FrameArg& F = a.frames[blockIdx.y];
+    const int W = F.W, H = F.H;
+    const float* const Dp = F.D;
+    const int64_t pitch = F.pitch;
+    const int QW = (W + 3) >> 2;
+    const int64_t nq = (int64_t)H * QW;
+    const bool vec = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(Dp) & 15) == 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_bad = 0;
+    float lo = INFINITY, hi = -INFINITY;
+    bool bad = false;
+    for (int64_t q = (int64_t)blockIdx.x * kMinMaxThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kMinMaxThreads) {
+        const int y = (int)(q / QW);
+        const int x0 = (int)(q - (int64_t)y * QW) * 4;
+        const float* row = Dp + (int64_t)y * pitch;
+        float d[4];
+        if (vec && x0 + 4 <= W) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(row + x0));
+            d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) d[j] = (x0 + j < W) ? __ldg(row + x0 + j) : d[0];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            lo = fminf(lo, d[j]);
+            hi = fmaxf(hi, d[j]);
+            bad |= !isfinite(d[j]);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(kFull, lo, off));
+        hi = fmaxf(hi, __shfl_xor_sync(kFull, hi, off));
+    }
+    __syncthreads();
+    if (__any_sync(kFull, bad) && lane == 0) s_bad = 1;
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float blo = INFINITY, bhi = -INFINITY;
+        for (int w = 0; w < kMinMaxThreads / 32; w++) {
+            blo = fminf(blo, s_lo[w]);
+            bhi = fmaxf(bhi, s_hi[w]);
+        }
+        if (blo <= bhi) {
+            atomicMax(&F.hdr[HDR_MAX], f2ord(bhi));
+            atomicMax(&F.hdr[HDR_NEGMIN], ~f2ord(blo));
+        }
+        if (s_bad) atomicOr(&F.hdr[HDR_STATUS], ST_NONFINITE);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------------------------
 // k_frames: copies a chunk of frame records from the launch parameters into the device frame table.
 
 __global__ void k_frames(const __grid_constant__ FrameChunk c)
@@ -448,25 +542,12 @@ __device__ __forceinline__ int item_owner(const uint32_t* pref, int n, uint32_t 
 // that ulp is at most 2^-7 for the coordinates this library accepts (x < 2^16, |g| <= 2047), so entries whose
 // fraction lies within 2^-8 of 0.5 are marked kTabExact and computed without the table.
 
-constexpr int32_t kTabExact = (int32_t)0x80008000;
 
 __global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Args a)
 {
     const int64_t total = (int64_t)a.nv * kSTabLen;
-    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < total; i += (int64_t)gridDim.x * 256) {
-        const int v = (int)(i / kSTabLen);
-        const int j = (int)(i - (int64_t)v * kSTabLen);
-        const float g = (float)(j - kTabHalf);
-        const float tx = __fmul_rn(a.view[v].c, g), ty = __fmul_rn(a.view[v].s, g);
-        // Strip views: the sample's offset along its row, column or diagonal (rounded like Eq. 4, which it equals
-        // there; see kStripMaxSide).
-        a.stab[i] = (int16_t)(int)roundf(a.view[v].fam == kFamCols ? ty : tx);
-        if (j >= kTabLen) continue;
-        const float fx = tx - floorf(tx), fy = ty - floorf(ty);   // exact: the fraction of a binary32 value
-        const bool risky = fabsf(fx - 0.5f) <= 0.00390625f || fabsf(fy - 0.5f) <= 0.00390625f;
-        const int dx = (int)roundf(tx), dy = (int)roundf(ty);
-        a.ptab[(int64_t)v * kTabLen + j] = risky ? kTabExact : (int32_t)((uint32_t)(dx & 0xFFFF) | ((uint32_t)dy << 16));
-    }
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < total; i += (int64_t)gridDim.x * 256)
+        tables_entry(a, i);
 }
 
 // ------------------------------------------------------------------------------------------------------------------
@@ -1634,6 +1715,15 @@ cudaError_t launch_edges(const Args& a, cudaStream_t st)
     if (bx > 2048) bx = 2048;
     if (bx < 1) bx = 1;
     k_edges<<<dim3(bx, a.nf), kEdgeThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minmax(const Args& a, cudaStream_t st)
+{
+    int bx = (a.max_quads + kMinMaxThreads - 1) / kMinMaxThreads;
+    if (bx > 1024) bx = 1024;
+    if (bx < 8) bx = 8;
+    k_minmax<<<dim3(bx, a.nf + 1), kMinMaxThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
