@@ -356,7 +356,7 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t* s_warp, uin
 }
 
 template <bool kHits>
-__global__ void __launch_bounds__(kStripThreads, 4) k_strip(const __grid_constant__ Args a)
+__global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constant__ Args a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_warp[kStripWarps];
