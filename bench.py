@@ -174,6 +174,14 @@ def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -
     return n
 
 
+# DRAM bytes (read + write) per detect call of the scan stage (all its launches: the strip kernel, the prefix sums of
+# its listed lines and the warp kernels) from the ncu launch list summarised in profiles/, valid only for the kernel
+# code it was taken on (sha256 prefix of csrc/occ_kernels.cu + csrc/occ_strip.cu without comments and blank space);
+# reported as null otherwise.
+PROFILED_STEPS = 20   # occ_detect calls with per-stage events after the timed region (stage_ms)
+MEASURED_TRAFFIC = {"scan": {"bytes": 48391040, "kernels_sha": "4ef7ed40da43bbea"}}
+
+
 def code_sha(src: str) -> str:
     """sha256 prefix of a CUDA source with its comments and blank space removed: comment edits do not change it."""
     import hashlib
