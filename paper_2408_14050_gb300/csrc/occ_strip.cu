@@ -442,64 +442,33 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
     line_geom(fam, H, W, l0 + tb, bx0, by0, bay, bn);
     const int dl = fam == kFamDiag ? (l0 + tb) - (H - 1) : l0 + tb;   // x - y of a diagonal, x + y of an anti-diagonal
 
-    // 1. Stage D_r of the strip, then evaluate Eq. 1-2 (on D_r, shared by the group's views) for every pixel: the
-    //    right and lower neighbours come from the strip's own lines where they lie on one (for a diagonal strip the
-    //    lines on either side, one position along or not), from D otherwise (the strip's first or last line).  Each
-    //    pass takes four pixels of a thread at a time, their loads issued first.
+    // 1. Stage D_r and evaluate Eq. 1-2 (on D_r, shared by the group's views) for every pixel of the strip, four
+    //    pixels of a thread at a time with their twelve loads (D, right and lower neighbours) issued first.
     const int tpv = F.tiles_x * F.tiles_y;
     uint32_t my_cand[2] = {0, 0};
     {
         const bool one = (r == 1.0f);
-        int bq[4], xq[4], yq[4], tq[4];
-        bool ok[4];
-        // Shared index of a neighbour of pixel (b, t) on line b + db at position t + dt, or -1 when that line is not
-        // in the strip (the value then comes from D).
-        auto nb_index = [&](int b, int t, int db, int dt) { return (b + db >= 0 && b + db < nb) ? (b + db) * len + t + dt : -1; };
-        auto right_of = [&](int b, int t) {
-            if (fam == kFamRows) return b * len + t + 1;
-            if (fam == kFamCols) return nb_index(b, t, 1, 0);
-            if (fam == kFamDiag) return nb_index(b, t, 1, (l0 + b) - (H - 1) >= 0 ? 0 : 1);
-            return nb_index(b, t, 1, (l0 + b) >= H - 1 ? 0 : 1);
-        };
-        auto below_of = [&](int b, int t) {
-            if (fam == kFamRows) return nb_index(b, t, 1, 0);
-            if (fam == kFamCols) return b * len + t + 1;
-            if (fam == kFamDiag) return nb_index(b, t, -1, (l0 + b) - (H - 1) >= 1 ? 1 : 0);
-            return nb_index(b, t, 1, (l0 + b) >= H - 1 ? -1 : 0);
-        };
-        auto stage4 = [&]() {
-            float d[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) d[u] = ok[u] ? __ldg(Dp + (int64_t)yq[u] * pitch + xq[u]) : 0.0f;
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                if (ok[u]) sV[bq[u] * len + tq[u]] = one ? d[u] : __fmul_rn(r, d[u]);
-        };
-        auto test4 = [&]() {
-            float dx[4], dy[4];
-            int ix[4], iy[4];
+        auto stage4 = [&](const int (&bq)[4], const int (&xq)[4], const int (&yq)[4], const int (&tq)[4],
+                          const bool (&ok)[4]) {
+            float d[4], dx[4], dy[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                ix[u] = iy[u] = -1;
-                dx[u] = dy[u] = 0.0f;
-                if (!ok[u]) continue;
-                if (xq[u] + 1 < W) {
-                    ix[u] = right_of(bq[u], tq[u]);
-                    if (ix[u] < 0) dx[u] = __ldg(Dp + (int64_t)yq[u] * pitch + xq[u] + 1);
-                }
-                if (yq[u] + 1 < H) {
-                    iy[u] = below_of(bq[u], tq[u]);
-                    if (iy[u] < 0) dy[u] = __ldg(Dp + (int64_t)(yq[u] + 1) * pitch + xq[u]);
+                d[u] = dx[u] = dy[u] = 0.0f;
+                if (ok[u]) {
+                    const float* row = Dp + (int64_t)yq[u] * pitch + xq[u];
+                    d[u] = __ldg(row);
+                    if (xq[u] + 1 < W) dx[u] = __ldg(row + 1);
+                    if (yq[u] + 1 < H) dy[u] = __ldg(row + pitch);
                 }
             }
 #pragma unroll
             for (int u = 0; u < 4; u++) {
                 if (!ok[u]) continue;
+                const float dr = one ? d[u] : __fmul_rn(r, d[u]);
                 const int q = bq[u] * len + tq[u];
-                const float dr = sV[q];
-                float ex = 0.0f, ey = 0.0f;
-                if (xq[u] + 1 < W) ex = __fsub_rn(ix[u] >= 0 ? sV[ix[u]] : (one ? dx[u] : __fmul_rn(r, dx[u])), dr);
-                if (yq[u] + 1 < H) ey = __fsub_rn(iy[u] >= 0 ? sV[iy[u]] : (one ? dy[u] : __fmul_rn(r, dy[u])), dr);
+                sV[q] = dr;
+                const float ex = (xq[u] + 1 < W) ? __fsub_rn(one ? dx[u] : __fmul_rn(r, dx[u]), dr) : 0.0f;
+                const float ey = (yq[u] + 1 < H) ? __fsub_rn(one ? dy[u] : __fmul_rn(r, dy[u]), dr) : 0.0f;
                 const float e2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
                 if (!(e2 >= a.e2min)) continue;
                 const int tile = (yq[u] / kTile) * tiles_x + xq[u] / kTile;
@@ -516,36 +485,35 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
                 }
             }
         };
-        for (int pass = 0; pass < 2; pass++) {
-            if (fam == kFamRows) {
-                for (int b = 0; b < nb; b++)
-                    for (int x0 = tid; x0 < W; x0 += 4 * kStripThreads) {
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            bq[u] = b;
-                            xq[u] = x0 + u * kStripThreads;
-                            yq[u] = l0 + b;
-                            tq[u] = xq[u];
-                            ok[u] = xq[u] < W;
-                        }
-                        if (pass == 0) stage4(); else test4();
-                    }
-            } else if (in_grp) {
-                for (int y0 = ty; y0 < H; y0 += 4 * ystep) {
+        int bq[4], xq[4], yq[4], tq[4];
+        bool ok[4];
+        if (fam == kFamRows) {
+            for (int b = 0; b < nb; b++)
+                for (int x0 = tid; x0 < W; x0 += 4 * kStripThreads) {
 #pragma unroll
                     for (int u = 0; u < 4; u++) {
-                        const int y = y0 + u * ystep;
-                        const int x = fam == kFamCols ? dl : (fam == kFamDiag ? y + dl : dl - y);
-                        bq[u] = tb;
-                        xq[u] = x;
-                        yq[u] = y;
-                        tq[u] = fam == kFamCols ? y : (fam == kFamDiag ? y - by0 : x - bx0);
-                        ok[u] = y < H && (unsigned)x < (unsigned)W;
+                        bq[u] = b;
+                        xq[u] = x0 + u * kStripThreads;
+                        yq[u] = l0 + b;
+                        tq[u] = xq[u];
+                        ok[u] = xq[u] < W;
                     }
-                    if (pass == 0) stage4(); else test4();
+                    stage4(bq, xq, yq, tq, ok);
                 }
+        } else if (in_grp) {
+            for (int y0 = ty; y0 < H; y0 += 4 * ystep) {
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int y = y0 + u * ystep;
+                    const int x = fam == kFamCols ? dl : (fam == kFamDiag ? y + dl : dl - y);
+                    bq[u] = tb;
+                    xq[u] = x;
+                    yq[u] = y;
+                    tq[u] = fam == kFamCols ? y : (fam == kFamDiag ? y - by0 : x - bx0);
+                    ok[u] = y < H && (unsigned)x < (unsigned)W;
+                }
+                stage4(bq, xq, yq, tq, ok);
             }
-            if (pass == 0) __syncthreads();
         }
     }
     atomicAdd(&s_cand[0], my_cand[0]);
