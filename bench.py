@@ -179,7 +179,7 @@ def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -
 # code it was taken on (sha256 prefix of csrc/occ_kernels.cu + csrc/occ_strip.cu without comments and blank space);
 # reported as null otherwise.
 PROFILED_STEPS = 20   # occ_detect calls with per-stage events after the timed region (stage_ms)
-MEASURED_TRAFFIC = {"scan": {"bytes": 48391040, "kernels_sha": "4ef7ed40da43bbea"}}
+MEASURED_TRAFFIC = {"scan": {"bytes": 62190464, "kernels_sha": "2f0039b2af74c896"}}
 
 
 def code_sha(src: str) -> str:
