@@ -152,16 +152,29 @@ class ClockSampler:
 
 
 
+def strip_views(views, tuning: dict, N: int = 8, max_side: int = 1920):
+    """Which views take the strip kernel: alpha a multiple of 45 degrees, N = 8, no side above 4096, strips on."""
+    strip_ok = tuning.get("strip_px", 0) > 0 and N == 8 and max_side <= 4096
+    return [strip_ok and abs((a % 45.0)) < 1e-9 for a, _ in views]
+
+
+def fused_call(views, tuning: dict, N: int = 8, max_side: int = 1920) -> bool:
+    """An occ_detect without E, A or tile outputs runs as the one fused launch: every view on strips, fused on (and
+    room in the context's scratch, which the bench's contexts have)."""
+    return all(strip_views(views, tuning, N, max_side)) and bool(tuning.get("fused", 1))
+
+
 def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -> int:
     """Kernels one occ_detect queues (no E, A or tile outputs).  Views whose scan lines stay on a row, column or
     diagonal (alpha a multiple of 45 degrees) take the strip kernel when N = 8 and the tuning enables it.  All views
-    on strips: frame table, min/max with the position tables, plan, strips, prefix sums of the listed long lines, the
-    three warp scan classes.  Otherwise: frame table, position tables (when some kernel uses them), edges and
-    candidates, plan, the strips and their prefix sums (if any view takes them), the line-per-thread scan and its
-    merge (when line_max_runs > 0), the three warp scan classes, the mask."""
-    strip_ok = tuning.get("strip_px", 0) > 0 and N == 8 and max_side <= 4096
-    strip = [strip_ok and abs((a % 45.0)) < 1e-9 for a, _ in views]
+    on strips: one fused launch, or (fused off) frame table, min/max with the position tables, plan, strips, prefix
+    sums of the listed long lines, the three warp scan classes.  Otherwise: frame table, position tables (when some
+    kernel uses them), edges and candidates, plan, the strips and their prefix sums (if any view takes them), the
+    line-per-thread scan and its merge (when line_max_runs > 0), the three warp scan classes, the mask."""
+    strip = strip_views(views, tuning, N, max_side)
     lines = tuning.get("line_max_runs", 2) > 0 and N <= 8
+    if fused_call(views, tuning, N, max_side):
+        return 1
     if all(strip):
         return 8
     n = 1 + 1 + 1 + 3 + 1          # frames, edges, plan, three warp classes, mask
@@ -193,9 +206,10 @@ def code_sha(src: str) -> str:
 
 
 def kernels_sha() -> str:
-    """Code hash of the scan kernels (the list kernels' and the strip kernel's sources, concatenated)."""
+    """Code hash of the scan kernels (the list kernels', the strip and fused kernels' sources and their shared device
+    headers, concatenated)."""
     src = ""
-    for name in ("occ_kernels.cu", "occ_strip.cu"):
+    for name in ("occ_kernels.cu", "occ_strip.cu", "occ_common.cuh", "occ_scanline.cuh"):
         with open(os.path.join(ROOT, "paper_2408_14050_gb300", "csrc", name), encoding="utf-8") as f:
             src += f.read()
     return code_sha(src)
@@ -318,7 +332,10 @@ def run_ours(args):
         achieved = ops / (scan_ms / 1e3) / 1e9
         roof = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(alu_peak / 1e9, 1), "unit": "Gop/s",
                 "frac": round(achieved / (alu_peak / 1e9), 4), "traffic": measured_traffic("scan"),
-                "kernel": ("scan stage: k_strip + k_plan_ovf + k_scan<256|1024|4096> (Eq. 1-6 on strips of rows, "
+                "kernel": ("k_fused: the whole call in one launch (min/max of Eq. 3, plan, Eq. 1-6 on strips of rows, "
+                           "columns and diagonals, lines of three or more macro-runs)"
+                           if fused_call(views, tuning, 8, max(H, W)) else
+                           "scan stage: k_strip + k_plan_ovf + k_scan<256|1024|4096> (Eq. 1-6 on strips of rows, "
                            "columns and diagonals)" if tuning.get("strip_px", 0) else
                            "scan stage: k_scan_lines + k_merge_lines + k_scan<256|1024|4096> (Eq. 4-6)"),
                 "launch_ms": round(scan_ms, 4),

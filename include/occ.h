@@ -191,13 +191,19 @@ int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
  *                        one block owns a strip of adjacent such lines of about strip_px pixels, holds D_r and O of
  *                        it in shared memory and writes O and M once.  0 turns it off (every view takes the
  *                        candidate-list kernels above); otherwise 1024 .. OCC_STRIP_PX_MAX, a multiple of 64,
- *                        raised for a call to its longest row, column or diagonal (default 4096). */
+ *                        raised for a call to its longest row, column or diagonal (default 4096).
+ *   fused                1 (default): a call whose views all take the strip kernel and that asks for no E, A or
+ *                        tile hits runs as one kernel launch (the min/max of Eq. 3, the plan, the strips and the
+ *                        lines of three or more macro-runs, with bounded waits between them; see
+ *                        occ_set_wait_limit), when the context's scratch has room for its work lists; 0: the same
+ *                        work in separate launches. */
 #define OCC_STRIP_PX_MAX 16384
 typedef struct {
     int32_t line_max_runs;
     int32_t line_blocks_per_sm;
     int32_t warp_lines_per_block;
     int32_t strip_px;
+    int32_t fused;
 } occ_tuning;
 
 /* Sets the tuning of later calls (NULL: the defaults).  OCC_ERR_INVALID_ARG for out-of-range fields. */
@@ -205,6 +211,13 @@ int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t);
 
 /* The tuning in effect, with the occupancy limit of line_blocks_per_sm in *max_line_blocks_per_sm (may be NULL). */
 int occ_get_tuning(occ_ctx* ctx, occ_tuning* t, int32_t* max_line_blocks_per_sm);
+
+/* The bound of every wait of the fused launch (occ_tuning.fused) between its stages: wait_us microseconds (0: the
+ * default of 2 s; at most 60 s).  A wait that reaches it makes every block of the launch stop and the call's status
+ * OCC_ERR_TIMEOUT (occ_get_status), with O and M unspecified; the context stays usable.  hold != 0 is a test hook:
+ * the fused launches of later calls never release the frames' plans, so that their strips' waits reach the bound.
+ * OCC_ERR_INVALID_ARG for a negative or too large wait_us. */
+int occ_set_wait_limit(occ_ctx* ctx, int64_t wait_us, int32_t hold);
 
 /* Stages of one occ_detect call, in launch order: candidates (Eq. 1-2 and the min/max of Eq. 3), the
  * line-per-thread scan (Eq. 4-6 for the scan lines whose sort is a set of adjacent swaps, or two such stretches;

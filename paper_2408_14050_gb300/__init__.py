@@ -37,7 +37,7 @@ STRIP_PX_DEFAULT = 4096      # default occ_tuning.strip_px
 OCC_MAX_FRAMES = 1024
 
 EXPORTED = ["occ_default_params", "occ_direction", "occ_create", "occ_destroy", "occ_detect", "occ_detect_host",
-            "occ_detect_host_async", "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning",
+            "occ_detect_host_async", "occ_detect_batched", "occ_get_status", "occ_get_stats", "occ_set_tuning", "occ_get_tuning", "occ_set_wait_limit",
             "occ_set_profiling", "occ_get_timings", "occ_detect_noalloc", "occ_fuse_median", "occ_warp_views",
             "occ_detect_batched_tiles", "occ_net_create", "occ_net_destroy", "occ_net_set_params",
             "occ_net_get_params", "occ_net_forward", "occ_net_loss_grad", "occ_net_adam", "occ_net_propose",
@@ -70,9 +70,10 @@ class occ_view_stats(ctypes.Structure):
 
 class occ_tuning(ctypes.Structure):
     """Mapping of the scan work: line_max_runs (0, 1, 2), line_blocks_per_sm, warp_lines_per_block (4, 8), strip_px
-    (0 = no strip kernel, else 1024 .. OCC_STRIP_PX_MAX pixels per strip, a multiple of 64)."""
+    (0 = no strip kernel, else 1024 .. OCC_STRIP_PX_MAX pixels per strip, a multiple of 64), fused (1 = one launch
+    for calls whose views all take the strip kernel, 0 = separate launches)."""
     _fields_ = [("line_max_runs", ctypes.c_int32), ("line_blocks_per_sm", ctypes.c_int32),
-                ("warp_lines_per_block", ctypes.c_int32), ("strip_px", ctypes.c_int32)]
+                ("warp_lines_per_block", ctypes.c_int32), ("strip_px", ctypes.c_int32), ("fused", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -134,6 +135,8 @@ def load(build_if_missing: bool = True):
         L.occ_set_tuning.restype = ctypes.c_int
         L.occ_get_tuning.argtypes = [vp, ctypes.POINTER(occ_tuning), ctypes.POINTER(i32)]
         L.occ_get_tuning.restype = ctypes.c_int
+        L.occ_set_wait_limit.argtypes = [vp, i64, i32]
+        L.occ_set_wait_limit.restype = ctypes.c_int
         L.occ_set_profiling.argtypes = [vp, ctypes.c_int]
         L.occ_set_profiling.restype = ctypes.c_int
         L.occ_get_timings.argtypes = [vp, ctypes.POINTER(ctypes.c_float), i32]
@@ -488,10 +491,19 @@ def occ_set_tuning(ctx: Context, tuning: dict | None = None):
     t = None
     if tuning is not None:
         t = occ_tuning(int(tuning["line_max_runs"]), int(tuning["line_blocks_per_sm"]),
-                       int(tuning["warp_lines_per_block"]), int(tuning.get("strip_px", STRIP_PX_DEFAULT)))
+                       int(tuning["warp_lines_per_block"]), int(tuning.get("strip_px", STRIP_PX_DEFAULT)),
+                       int(tuning.get("fused", 1)))
     rc = load().occ_set_tuning(ctx.handle, ctypes.byref(t) if t is not None else None)
     if rc != OCC_OK:
         raise OccError(rc, "occ_set_tuning")
+
+
+def occ_set_wait_limit(ctx: Context, wait_us: int = 0, hold: bool = False):
+    """Bound of the fused launch's waits in microseconds (0: 2 s); hold=True is the test hook that withholds the
+    frames' plans so that the waits reach the bound (status OCC_ERR_TIMEOUT)."""
+    rc = load().occ_set_wait_limit(ctx.handle, int(wait_us), 1 if hold else 0)
+    if rc != OCC_OK:
+        raise OccError(rc, "occ_set_wait_limit")
 
 
 def occ_get_tuning(ctx: Context):

@@ -1,6 +1,7 @@
 """Autotuner of the mapping of the scan work (occ_tuning): the strip kernel's tile shape (pixels per strip, hence
-lines per strip and blocks per multiprocessor; or no strip kernel), how many macro-runs the line-per-thread kernel
-takes (0, 1, 2), its resident blocks per multiprocessor, and the warps per block of the one-warp-per-line kernel.
+lines per strip and blocks per multiprocessor; or no strip kernel), whether an all-strip call runs as one fused launch
+or as separate launches, how many macro-runs the line-per-thread kernel takes (0, 1, 2), its resident blocks per
+multiprocessor, and the warps per block of the one-warp-per-line kernel.
 
 Every choice gives bit-identical M and O; the tuner times each candidate with CUDA events on sample frames of the
 caller's workload, keeps the fastest, and caches it in a JSON file keyed by device and workload class (size class of
@@ -42,22 +43,23 @@ STRIP_SHAPES = (2048, 3072, 4096, 6144)   # pixels per strip of the strip kernel
 
 
 def candidates(max_line_bps: int):
-    """Strip shapes with the default list-path mapping, then every list-path mapping without the strip kernel."""
-    out = [{"line_max_runs": 2, "line_blocks_per_sm": max_line_bps, "warp_lines_per_block": 8, "strip_px": px}
-           for px in STRIP_SHAPES]
+    """Strip shapes, fused and not, with the default list-path mapping; then every list-path mapping without the strip
+    kernel."""
+    out = [{"line_max_runs": 2, "line_blocks_per_sm": max_line_bps, "warp_lines_per_block": 8, "strip_px": px,
+            "fused": fused} for px in STRIP_SHAPES for fused in (1, 0)]
     for runs in (2, 1, 0):
         for bps in sorted({max_line_bps, max(1, max_line_bps - 1)}, reverse=True):
             for wpb in (8, 4):
                 if runs == 0 and bps != max_line_bps:
                     continue      # the line kernel does not run: its grid is irrelevant
                 out.append({"line_max_runs": runs, "line_blocks_per_sm": bps, "warp_lines_per_block": wpb,
-                            "strip_px": 0})
+                            "strip_px": 0, "fused": 1})
     return out
 
 
 def tuning_name(t: dict) -> str:
-    return (f"strip{t['strip_px']}_runs{t['line_max_runs']}_bps{t['line_blocks_per_sm']}"
-            f"_wpb{t['warp_lines_per_block']}")
+    return (f"strip{t['strip_px']}{'f' if t.get('fused', 1) else ''}_runs{t['line_max_runs']}"
+            f"_bps{t['line_blocks_per_sm']}_wpb{t['warp_lines_per_block']}")
 
 
 def load_cache(path: str = DEFAULT_CACHE) -> dict:

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "occ_internal.cuh"
@@ -127,7 +128,32 @@ cudaError_t scratch_grids(Scratch& sc)
     sc.tuning.line_blocks_per_sm = sc.lines_bps_max;
     sc.tuning.warp_lines_per_block = 8;
     sc.tuning.strip_px = kStripPxDefault;
+    sc.tuning.fused = 1;
     return cudaSuccess;
+}
+
+cudaError_t write_strip_tables(int16_t* stab)
+{
+    // cc = 1, -1, fl(sqrt(1/2)), -fl(sqrt(1/2)): cos and sin of the strip directions as occ_direction rounds them.
+    float q = 0.0f, qs = 0.0f;
+    occ_direction(45.0, &q, &qs);
+    const float cc[kNumSTabs] = {1.0f, -1.0f, q, -q};
+    static int16_t host[kNumSTabs][kSTabLen];
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (int t = 0; t < kNumSTabs; t++)
+        for (int j = 0; j < kSTabLen; j++) {
+            const float prod = cc[t] * (float)(j - kTabHalf);   // one binary32 multiply, as fl(cc * g) on the device
+            host[t][j] = (int16_t)(int)std::round(prod);        // nearest, halves away from zero (roundf)
+        }
+    return cudaMemcpy(stab, host, sizeof(host), cudaMemcpyHostToDevice);
+}
+
+// Which strip offset table a strip view uses (see kNumSTabs): cc = sin for columns, cos otherwise.
+int strip_table(int fam, float c, float s)
+{
+    const float cc = fam == kFamCols ? s : c;
+    return cc == 1.0f ? 0 : (cc == -1.0f ? 1 : (cc > 0.0f ? 2 : 3));
 }
 
 // Strip family of a direction (cos, sin as occ_direction rounds them), or -1.
@@ -139,6 +165,51 @@ int strip_family(float c, float s)
     if (std::fabs(c) == q && c == s) return kFamDiag;
     if (std::fabs(c) == q && c == -s) return kFamAnti;
     return -1;
+}
+
+// The fused launch of a call: its tickets, grid, and the completion records, published-line pool and per-block warp
+// buffers it keeps in the merge kernel's list pool (which an all-strip call does not use).
+struct FusedLayout {
+    FusedPlan plan;
+    int grid;
+    uint32_t mm0[kFusedMaxFrames + 1];
+    FrameArg frames[kFusedMaxFrames];
+};
+
+bool fused_layout(const Scratch& sc, const FrameIn* fr, int nf, const Args& a, FusedLayout& fl)
+{
+    if (nf > kFusedMaxFrames || a.strip_px <= 0) return false;
+    const int bps = fused_blocks_per_sm(a.strip_px);
+    if (bps < 1) return false;
+    std::memset(&fl.plan, 0, sizeof(fl.plan));
+    int64_t t = 0, strips = 0;
+    for (int f = 0; f < nf; f++) {
+        fl.mm0[f] = (uint32_t)t;
+        const int64_t quads = (int64_t)fr[f].H * ((fr[f].W + 3) / 4);
+        t += (quads + kFusedQuadsPerTicket - 1) / kFusedQuadsPerTicket;
+        for (int g = 0; g < a.ngroups; g++) strips += fam_strips(a.group[g].fam, fr[f].H, fr[f].W, a.strip_px);
+    }
+    fl.mm0[nf] = (uint32_t)t;
+    const int64_t work = t + strips;
+    const int64_t grid = std::min<int64_t>((int64_t)sc.sms * bps, work);
+    if (work + grid > (int64_t)INT32_MAX || strips < 1) return false;
+    // Scratch: warp buffers (one per block), then the pool of published lines.
+    const size_t slot = fused_slot_bytes();
+    char* base = reinterpret_cast<char*>(sc.brk);
+    const size_t bytes = (size_t)sc.brk_entries * sizeof(uint32_t);
+    const size_t off_pool = align256((size_t)grid * slot);
+    if (off_pool + sizeof(uint4) * 1024 > bytes) return false;
+    fl.grid = (int)grid;
+    FusedPlan& z = fl.plan;
+    z.mm_end = (uint32_t)t;
+    z.strip_end = (uint32_t)(t + strips);
+    z.end = (uint32_t)(t + strips + grid);
+    z.hold = (uint32_t)sc.hold;
+    z.wait_ns = sc.wait_ns;
+    z.slots = reinterpret_cast<unsigned char*>(base);
+    z.pool = reinterpret_cast<uint4*>(base + off_pool);
+    z.pool_cap = (uint32_t)std::min<size_t>((bytes - off_pool) / sizeof(uint4), UINT32_MAX);
+    return true;
 }
 
 int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev,
@@ -155,6 +226,7 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     for (int v = 0; v < nv; v++) {
         const int fam = strip_ok ? strip_family(a.view[v].c, a.view[v].s) : -1;
         a.view[v].fam = fam;
+        a.view[v].stab = fam >= 0 ? strip_table(fam, a.view[v].c, a.view[v].s) : 0;
         if (fam < 0) continue;
         n_strip++;
         // Pair the view with an earlier one of the same family and ratio that is still alone.
@@ -192,14 +264,23 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.ptab = sc.ptab;
     a.stab = sc.stab;
     a.status = sc.status;
-    a.line_ctr = sc.status + 1;   // the status region has room for the counters
+    a.line_ctr = sc.status + CTR_LINE;   // the status region has room for the counters
     a.brk = sc.brk;
-    a.brk_count = reinterpret_cast<unsigned long long*>(sc.status + 2);
-    a.merge_ctr = sc.status + 4;
+    a.brk_count = reinterpret_cast<unsigned long long*>(sc.status + CTR_BRK);
+    a.merge_ctr = sc.status + CTR_MERGE;
     a.brk_cap = (uint32_t)(sc.brk_entries < (int64_t)UINT32_MAX ? sc.brk_entries : (int64_t)UINT32_MAX);
     a.max_quads = 0;
     a.max_px = 0;
     a.hits = 0;
+
+    // Every view on strips and no E, A or hit flags asked for: one read of D for Eq. 3 (with the tables in the same
+    // launch) is all the candidate pass has to do; with room in the scratch, the whole call is one fused launch.
+    bool extras = false;
+    for (int f = 0; f < nf; f++) extras = extras || fr[f].E || fr[f].A || fr[f].hits;
+    const bool minmax_only = !list_views && !extras;
+    FusedLayout fl;
+    const bool fused = minmax_only && sc.tuning.fused && fused_layout(sc, fr, nf, a, fl);
+    FrameArg* fused_frames = fused ? fl.frames : nullptr;
 
     // Frame records: lists and flags laid out frame after frame in the pools.
     FrameChunk chunk;
@@ -240,7 +321,9 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         if (quads > a.max_quads) a.max_quads = quads;
         const int64_t px = (int64_t)nv * F.H * F.W;
         if (px > a.max_px) a.max_px = px;
-        if (f % kFramesPerChunk == kFramesPerChunk - 1 || f == nf - 1) {
+        if (fused_frames) {
+            fused_frames[f] = F;
+        } else if (f % kFramesPerChunk == kFramesPerChunk - 1 || f == nf - 1) {
             chunk.first = f - f % kFramesPerChunk;
             chunk.count = f % kFramesPerChunk + 1;
             if (launch_frames(chunk, st) != cudaSuccess) return OCC_ERR_CUDA;
@@ -254,9 +337,22 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     a.line_dyn = px_views > (int64_t)64 * 1024 * 1024 ? 1 : 0;
 
     auto mark = [&](int i) { return !ev || cudaEventRecord(ev[i], st) == cudaSuccess; };
+    if (fused) {
+        // One launch: its stage times all fall in the line-per-thread stage's slot.
+        if (forked) *forked = false;
+        a.fz = fl.plan;
+        if (cudaMemsetAsync(sc.hdr, 0, sizeof(uint32_t) * HDR_WORDS * nf, st) != cudaSuccess ||
+            cudaMemsetAsync(sc.stats, 0, sizeof(unsigned long long) * 2 * sc.max_views * nf, st) != cudaSuccess ||
+            cudaMemsetAsync(sc.status, 0, CTR_WORDS * sizeof(uint32_t), st) != cudaSuccess || !mark(0) || !mark(1) ||
+            launch_fused(a, fl.frames, fl.mm0, nf, fl.grid, st) != cudaSuccess)
+            return OCC_ERR_CUDA;
+        for (int i = 2; i <= OCC_NUM_STAGES; i++)
+            if (!mark(i)) return OCC_ERR_CUDA;
+        return OCC_OK;
+    }
     if (cudaMemsetAsync(sc.hdr, 0, sizeof(uint32_t) * HDR_WORDS * nf, st) != cudaSuccess ||
         cudaMemsetAsync(sc.stats, 0, sizeof(unsigned long long) * 2 * sc.max_views * nf, st) != cudaSuccess ||
-        cudaMemsetAsync(sc.status, 0, 5 * sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(sc.status, 0, CTR_WORDS * sizeof(uint32_t), st) != cudaSuccess ||
         (lines && cudaMemsetAsync(sc.fb, 0, sizeof(uint32_t) * fb_off, st) != cudaSuccess))
         return OCC_ERR_CUDA;
     // Size classes of the warp kernels that can receive work: with a fixed L only one.
@@ -266,15 +362,10 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         const int c = nk <= kClassCap[0] ? 0 : (nk <= kClassCap[1] ? 1 : 2);
         for (int k = 0; k < kNumClasses; k++) run_cls[k] = (k == c);
     }
-    // Every view on strips and no E, A or hit flags asked for: one read of D for Eq. 3 (with the tables in the same
-    // launch) is all the candidate pass has to do.
-    bool extras = a.hits != 0;
-    for (int f = 0; f < nf; f++) extras = extras || fr[f].E || fr[f].A;
-    const bool minmax_only = !list_views && !extras;
     if (!mark(0)) return OCC_ERR_CUDA;
     if (minmax_only) {
         if (launch_minmax(a, st) != cudaSuccess) return OCC_ERR_CUDA;
-    } else if (((lines || n_strip) && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess) {
+    } else if ((lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess) {
         return OCC_ERR_CUDA;
     }
     if (launch_plan(a, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
@@ -413,11 +504,11 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     const size_t nfv = (size_t)kMaxFrames * max_views;
     const size_t sz_hdr = align256(sizeof(uint32_t) * HDR_WORDS * kMaxFrames);
     const size_t sz_stats = align256(sizeof(unsigned long long) * 2 * nfv);
-    const size_t sz_status = 256;
+    const size_t sz_status = kStatusBytes;
     const size_t sz_frames = align256(sizeof(FrameArg) * kMaxFrames);
     const size_t sz_plan = align256(sizeof(PlanEntry) * nfv);
     const size_t sz_pref = align256(sizeof(uint32_t) * (1 + 2 * kNumClasses) * (nfv + 1));
-    const size_t sz_tab = align256(sizeof(int32_t) * kTabLen * max_views) + align256(sizeof(int16_t) * kSTabLen * max_views);
+    const size_t sz_tab = align256(sizeof(int32_t) * kTabLen * max_views) + align256(sizeof(int16_t) * kSTabLen * kNumSTabs);
     const size_t total = sz_hdr + sz_stats + sz_status + sz_frames + sz_plan + sz_pref + sz_tab;
     sc.cand_entries = ctx->cand_cap * max_views;
     sc.fb_entries = (ctx->cand_cap / 32 + kMaxFrames + 1) * (int64_t)max_views;
@@ -448,6 +539,11 @@ int occ_create(occ_ctx** out, int device, int64_t max_pixels, int32_t max_views,
     sc.cand = ctx->d_cand;
     sc.fb = ctx->d_fb;
     sc.brk = ctx->d_brk;
+    if (write_strip_tables(sc.stab) != cudaSuccess) {
+        cudaGetLastError();
+        occ_destroy(ctx);
+        return OCC_ERR_CUDA;
+    }
     *out = ctx;
     return OCC_OK;
 }
@@ -552,13 +648,22 @@ int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, co
 int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t)
 {
     if (!ctx) return OCC_ERR_INVALID_ARG;
-    occ_tuning d{2, ctx->sc.lines_bps_max, 8, kStripPxDefault};
+    occ_tuning d{2, ctx->sc.lines_bps_max, 8, kStripPxDefault, 1};
     if (!t) t = &d;
     if (t->line_max_runs < 0 || t->line_max_runs > 2 || t->line_blocks_per_sm < 1 ||
         t->line_blocks_per_sm > ctx->sc.lines_bps_max || (t->warp_lines_per_block != 4 && t->warp_lines_per_block != 8) ||
-        (t->strip_px != 0 && (t->strip_px < 1024 || t->strip_px > OCC_STRIP_PX_MAX || (t->strip_px & 63))))
+        (t->strip_px != 0 && (t->strip_px < 1024 || t->strip_px > OCC_STRIP_PX_MAX || (t->strip_px & 63))) ||
+        (t->fused != 0 && t->fused != 1))
         return OCC_ERR_INVALID_ARG;
     ctx->sc.tuning = *t;
+    return OCC_OK;
+}
+
+int occ_set_wait_limit(occ_ctx* ctx, int64_t wait_us, int32_t hold)
+{
+    if (!ctx || wait_us < 0 || wait_us > 60000000) return OCC_ERR_INVALID_ARG;
+    ctx->sc.wait_ns = wait_us ? (uint64_t)wait_us * 1000u : 2000000000ull;
+    ctx->sc.hold = hold ? 1 : 0;
     return OCC_OK;
 }
 

@@ -22,6 +22,8 @@ enum : int {
     HDR_STATUS = 0,                  // status bits of the frame (ST_*)
     HDR_MAX = 1,                     // max D, order-preserving encoding (atomicMax)
     HDR_NEGMIN = 2,                  // min D, complemented encoding (atomicMax)
+    HDR_MMDONE = 3,                  // fused launch: min/max tickets of the frame done
+    HDR_READY = 4,                   // fused launch: the frame's plan is written (1)
     HDR_COUNT = 8,                   // [kMaxViews] candidates found per view (may exceed the list capacity)
     HDR_L = HDR_COUNT + kMaxViews,   // [kMaxViews] scan length used per view (Eq. 3)
     HDR_OVF = HDR_L + kMaxViews,     // [kMaxViews] strip views: lines of three or more macro-runs listed for k_scan
@@ -46,15 +48,18 @@ constexpr int kLineMaxHalf = 4;
 // Position tables: per view, for g = -kTabHalf .. kTabHalf, round(fl(cos a * g)) and round(fl(sin a * g)).
 constexpr int kTabHalf = (OCC_MAX_SCAN + 1) / 2;
 constexpr int kTabLen = 2 * kTabHalf + 1;
-// Per view, for g = -kTabHalf .. kTabHalf + 8: the strip kernel's offset round(fl(cc * g)) of sample g along its line
-// (the entries past kTabHalf keep reads a step or two ahead of a line's end in bounds).
+// The strip kernel's offsets round(fl(cc * g)) of sample g along its line, for g = -kTabHalf .. kTabHalf + 8 (the
+// entries past kTabHalf keep reads a step or two ahead of a line's end in bounds): one table per value of cc, which
+// for the strip directions is cos or sin of the view rounded to binary32, +-1 or +-fl(sqrt(1/2)) (kNumSTabs tables,
+// written once when the scratch is set up).
 constexpr int kSTabLen = kTabLen + 8;
+constexpr int kNumSTabs = 4;   // cc = 1, -1, fl(sqrt(1/2)), -fl(sqrt(1/2))
 
 struct ViewArg {
     float c, s, r;   // binary32 cos(alpha), sin(alpha), ratio
     int32_t ridx;    // index of r in Args::ratio
     int32_t fam;     // strip family of the view's scan lines (kFam*), or -1: the view takes the list path
-    int32_t pad;
+    int32_t stab;    // strip views: which of the kNumSTabs offset tables (cc = sin for columns, else cos)
 };
 
 // Directions whose scan lines (Eq. 4) stay on one digital line of the frame: rows (alpha = 0, 180), columns (90, 270),
@@ -135,6 +140,50 @@ struct PlanEntry {
     uint32_t pad;
 };
 
+// Words of the call's status region (zero at the start of every call): the status word, the counters of the list
+// kernels, then those of the fused launch (k_fused).
+enum : int {
+    CTR_LINE = 1,            // work counter of the line kernel
+    CTR_BRK = 2,             // two words: entries / pairs of the merge kernel's lists
+    CTR_MERGE = 4,           // batch counter of the merge kernel
+    CTR_TICKET = 8,          // fused: next ticket
+    CTR_STRIPS = 10,         // fused: strips done
+    CTR_OVF_READY = 11,      // fused: prefix sums of the listed lines written (1)
+    CTR_OVF_CURSOR = 12,     // fused: [kNumClasses] next listed line of each size class
+    CTR_ABORT = 15,          // fused: a wait gave up; every block stops
+    CTR_POOL = 16,           // fused: entries of the published-line pool reserved
+    CTR_CLAIM = 17,          // fused: entries of the pool taken by the workers
+    CTR_EXIT = 18,           // fused: blocks that have ended
+    CTR_WORDS = 19,
+    CTR_EPOCH = 32,          // fused: launches so far (kept across calls): the tag of this launch's pool entries
+};
+constexpr size_t kStatusBytes = 256;   // bytes of the status region in every scratch layout
+static_assert(CTR_WORDS <= CTR_EPOCH && (CTR_EPOCH + 1) * sizeof(uint32_t) <= kStatusBytes,
+              "status region too small for the counters");
+
+// The fused launch (occ_strip.cu): one kernel for a call whose views all take the strip kernel and that asks for no E,
+// A or tile hits.  Blocks take tickets from one counter in this order: the min/max tiles of every frame (the last one
+// of a frame writes its plan), the strips, then worker tickets that take the published lines of three or more
+// macro-runs (and, once every strip is done, those in the views' lists).
+constexpr int kFusedQuadsPerTicket = 2048;   // 4-pixel quads of D per min/max ticket (128 threads x 16)
+constexpr int kFusedMaxFrames = 128;         // frame records in the launch parameters
+struct FusedPlan {
+    uint32_t mm_end;                         // tickets [0, mm_end): min/max tiles, frame after frame
+    uint32_t strip_end;                      // [mm_end, strip_end): strips (strip index = ticket - mm_end)
+    uint32_t end;                            // [strip_end, end): workers
+    uint32_t hold;                           // test hook: never release the frames' plans
+    uint64_t wait_ns;                        // bound of every wait
+    uint4* pool;                             // published lines: (y << 16 | x, frame << 8 | view or kPoolSkip, tag, -)
+    unsigned char* slots;                    // per block, a warp buffer of the largest size class (global memory)
+    uint32_t pool_cap;
+};
+constexpr uint32_t kPoolSkip = 0xFFFFFFFFu;  // a pool entry without a line (its reservation ran past the pool)
+template <int NF>
+struct FusedFrames {
+    uint32_t mm0[NF + 1];                    // first min/max ticket of each frame (mm0[nf] = mm_end)
+    FrameArg f[NF];
+};
+
 struct Args {
     int32_t nf, nv, nr;           // frames, views, distinct ratios
     float gamma, zeta, beta;
@@ -154,7 +203,7 @@ struct Args {
     uint32_t* pref_all;           // [nf * nv + 1] prefix of the candidate counts of every (frame, view)
     uint32_t* pref_cls;           // [kNumClasses][nf * nv + 1] the same restricted to each size class
     int32_t* ptab;                // [nv][kTabLen] packed (dx & 0xFFFF) | (dy << 16), or kTabExact
-    int16_t* stab;                // [nv][kSTabLen] strip offsets (see kSTabLen)
+    const int16_t* stab;          // [kNumSTabs][kSTabLen] strip offsets (see kSTabLen)
     uint32_t* status;             // OR of every frame's status bits
     uint32_t* line_ctr;           // work counter of the line kernel, zero at the start of a call
     uint32_t* brk;                // lists of the merge kernel: from the front, the work items of the lines of more than
@@ -170,6 +219,7 @@ struct Args {
     int32_t ngroups;              // strip groups (each frame has the strips of every group, in group order)
     StripGroup group[kMaxViews];
     uint32_t* pref_ovf;           // [kNumClasses][nf * nv + 1] prefix of the strip views' listed lines per size class
+    FusedPlan fz;                 // the fused launch (unused otherwise)
 };
 
 // At most kFramesPerChunk frame records travel in the parameters of one k_frames launch (under 4 KB).
@@ -184,8 +234,7 @@ struct FrameChunk {
 cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st);
 cudaError_t launch_tables(const Args& a, cudaStream_t st);
 cudaError_t launch_edges(const Args& a, cudaStream_t st);
-// k_edges' min/max and non-finite check alone, with the position tables (k_tables) in the same launch: for calls with
-// no candidate-list view and no E, A or tile hit outputs.
+// k_edges' min/max and non-finite check alone: for calls with no candidate-list view and no E, A or tile hit outputs.
 cudaError_t launch_minmax(const Args& a, cudaStream_t st);
 cudaError_t launch_plan(const Args& a, cudaStream_t st);
 // The line-per-thread scan over every view; wide = true when some frame's offsets need 64 bits.
@@ -200,6 +249,14 @@ cudaError_t launch_strip(const Args& a, cudaStream_t st);
 cudaError_t launch_plan_ovf(const Args& a, cudaStream_t st);
 size_t strip_smem(int strip_px);
 cudaError_t configure_strip();
+// The fused launch of an all-strip call (a.fz filled in, the status region and frame headers cleared), on `grid`
+// blocks: the nf <= kFusedMaxFrames frame records f travel in the launch parameters, with the first min/max ticket of
+// each frame (mm0[0 .. nf], mm0[nf] = a.fz.mm_end).
+cudaError_t launch_fused(const Args& a, const FrameArg* f, const uint32_t* mm0, int nf, int grid, cudaStream_t st);
+// Resident blocks per SM of the fused kernel with strips of strip_px pixels.
+int fused_blocks_per_sm(int strip_px);
+// Bytes of one block's warp buffer of the largest size class (FusedPlan::slots).
+size_t fused_slot_bytes();
 // Per-SM resident blocks of the persistent scan kernels (kNumClasses + 1 warp variants); also sets the shared-memory
 // opt-ins.
 cudaError_t configure_kernels(int* lines_blocks_per_sm, int scan_blocks_per_sm[kNumClasses + 1]);
@@ -217,7 +274,7 @@ struct Scratch {
     PlanEntry* plan;               // [max_frames * max_views]
     uint32_t* pref;                // [(1 + kNumClasses) * (max_frames * max_views + 1)]
     int32_t* ptab;                 // [max_views][kTabLen]
-    int16_t* stab;                 // [max_views][kSTabLen]
+    int16_t* stab;                 // [kNumSTabs][kSTabLen], written by write_strip_tables
     uint32_t* cand;                // candidate list pool
     int64_t cand_entries;
     uint32_t* fb;                  // line-flag pool (words)
@@ -229,6 +286,8 @@ struct Scratch {
     int32_t lines_bps_max;         // resident blocks per SM of the line kernel
     int32_t scan_bps[kNumClasses + 1];  // of the warp kernels (classes 0, 1, 2, then class 0 with 4-warp blocks)
     occ_tuning tuning;             // mapping and grid choices (occ_set_tuning)
+    uint64_t wait_ns = 2000000000ull;  // bound of the fused launch's waits (occ_set_wait_limit)
+    int32_t hold = 0;              // test hook: the fused launch never releases the frames' plans
 };
 
 // One frame of a call as the caller gives it.
@@ -261,6 +320,9 @@ struct SideStream {
 // the warp kernels ran on the side stream.  Returns OCC_OK once queued, or OCC_ERR_CUDA.
 int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream_t st, cudaEvent_t* ev,
                const SideStream* side = nullptr, bool* forked = nullptr);
+
+// Computes the kNumSTabs strip offset tables on the host and copies them to stab (synchronous).
+cudaError_t write_strip_tables(int16_t* stab);
 
 // Occupancy of the persistent scan kernels on the current device (also sets their shared-memory opt-ins) and the
 // default tuning.

@@ -25,23 +25,14 @@
 #include <cstdint>
 
 #include "occ_internal.cuh"
+#include "occ_common.cuh"
+#include "occ_scanline.cuh"
 
 namespace occ {
 
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-
-// Order-preserving map of binary32 onto uint32 (larger float -> larger code) for atomicMax-based min/max.
-__device__ __forceinline__ uint32_t f2ord(float f)
-{
-    const uint32_t b = __float_as_uint(f);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float ord2f(uint32_t o)
-{
-    return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
-}
 
 // O[p] += o as a reduction (no return value) predicated on o != 0 inside the asm: the count of a sample leaving the
 // window goes to O without a divergent branch around the atomic.
@@ -324,40 +315,12 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
 
 // ------------------------------------------------------------------------------------------------------------------
 // k_minmax: what k_edges does when no view takes the candidate lists and neither E, A nor tile hit flags are asked
-// for -- the min/max of D (Eq. 3) and the non-finite check, one read of D, four pixels per thread and step -- and, in
-// the blocks of grid row nf, the position tables (as k_tables).
+// for -- the min/max of D (Eq. 3) and the non-finite check, one read of D, four pixels per thread and step.
 
 constexpr int kMinMaxThreads = 256;
 
-// Marks a position-table entry whose nearest pixel must be computed exactly (see k_tables).
-constexpr int32_t kTabExact = (int32_t)0x80008000;
-
-// Entry i of the position tables (view i / kSTabLen, g = i % kSTabLen - kTabHalf): the strip kernel's offset along the
-// view's row, column or diagonal (rounded like Eq. 4, which it equals there; see kStripMaxSide), and for g <= kTabHalf
-// the list kernels' packed pixel offsets.
-__device__ __forceinline__ void tables_entry(const Args& a, int64_t i)
-{
-    const int v = (int)(i / kSTabLen);
-    const int j = (int)(i - (int64_t)v * kSTabLen);
-    const float g = (float)(j - kTabHalf);
-    const float tx = __fmul_rn(a.view[v].c, g), ty = __fmul_rn(a.view[v].s, g);
-    a.stab[i] = (int16_t)(int)roundf(a.view[v].fam == kFamCols ? ty : tx);
-    if (j >= kTabLen) return;
-    const float fx = tx - floorf(tx), fy = ty - floorf(ty);
-    const bool risky = fabsf(fx - 0.5f) <= 0.00390625f || fabsf(fy - 0.5f) <= 0.00390625f;
-    const int dx = (int)roundf(tx), dy = (int)roundf(ty);
-    a.ptab[(int64_t)v * kTabLen + j] = risky ? kTabExact : (int32_t)((uint32_t)(dx & 0xFFFF) | ((uint32_t)dy << 16));
-}
-
 __global__ void __launch_bounds__(kMinMaxThreads) k_minmax(const __grid_constant__ Args a)
 {
-    if ((int)blockIdx.y == a.nf) {
-        const int64_t total = (int64_t)a.nv * kSTabLen;
-        for (int64_t i = (int64_t)blockIdx.x * kMinMaxThreads + threadIdx.x; i < total;
-             i += (int64_t)gridDim.x * kMinMaxThreads)
-            tables_entry(a, i);
-        return;
-    }
     __shared__ float s_lo[kMinMaxThreads / 32], s_hi[kMinMaxThreads / 32];
     __shared__ int s_bad;
     const FrameArg& F = a.frames[blockIdx.y];
@@ -371,25 +334,8 @@ __global__ void __launch_bounds__(kMinMaxThreads) k_minmax(const __grid_constant
     if (threadIdx.x == 0) s_bad = 0;
     float lo = INFINITY, hi = -INFINITY;
     bool bad = false;
-    for (int64_t q = (int64_t)blockIdx.x * kMinMaxThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kMinMaxThreads) {
-        const int y = (int)(q / QW);
-        const int x0 = (int)(q - (int64_t)y * QW) * 4;
-        const float* row = Dp + (int64_t)y * pitch;
-        float d[4];
-        if (vec && x0 + 4 <= W) {
-            const float4 t = __ldg(reinterpret_cast<const float4*>(row + x0));
-            d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; j++) d[j] = (x0 + j < W) ? __ldg(row + x0 + j) : d[0];
-        }
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            lo = fminf(lo, d[j]);
-            hi = fmaxf(hi, d[j]);
-            bad |= !isfinite(d[j]);
-        }
-    }
+    for (int64_t q = (int64_t)blockIdx.x * kMinMaxThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kMinMaxThreads)
+        minmax_quad(Dp, pitch, W, QW, vec, q, lo, hi, bad);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         lo = fminf(lo, __shfl_xor_sync(kFull, lo, off));
@@ -449,19 +395,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_plan(const __grid_constant__ A
             const uint32_t st = F.hdr[HDR_STATUS];
             PlanEntry pe{-1, 0, 0u, 0u};
             if (!(st & ST_NONFINITE)) {
-                int L;
-                if (a.Lover > 0) {
-                    L = a.Lover;
-                } else {
-                    // Eq. 3 on D_r: max D_r = fl(r max D) and min D_r = fl(r min D) (rounding is monotone).
-                    const float mx = ord2f(F.hdr[HDR_MAX]);
-                    const float mn = ord2f(~F.hdr[HDR_NEGMIN]);
-                    const float r = a.view[v].r;
-                    const float dmx = (r == 1.0f) ? mx : __fmul_rn(r, mx);
-                    const float dmn = (r == 1.0f) ? mn : __fmul_rn(r, mn);
-                    const float t = __fmul_rn(__fsub_rn(dmx, dmn), 2.0f);
-                    L = (t <= (float)OCC_MAX_SCAN) ? (int)ceilf(t) : -1;
-                }
+                const int L = scan_length(a, F.hdr[HDR_MAX], F.hdr[HDR_NEGMIN], a.view[v].r);
                 if (L < 0) {
                     atomicOr(&F.hdr[HDR_STATUS], ST_SCAN_TOO_LONG);
                     st_all |= ST_SCAN_TOO_LONG;
@@ -545,7 +479,7 @@ __device__ __forceinline__ int item_owner(const uint32_t* pref, int n, uint32_t 
 
 __global__ void __launch_bounds__(256) k_tables(const __grid_constant__ Args a)
 {
-    const int64_t total = (int64_t)a.nv * kSTabLen;
+    const int64_t total = (int64_t)a.nv * kTabLen;
     for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < total; i += (int64_t)gridDim.x * 256)
         tables_entry(a, i);
 }
@@ -1232,54 +1166,9 @@ __global__ void __launch_bounds__(kLineThreads, 3) k_merge_lines(const __grid_co
 }
 
 // ------------------------------------------------------------------------------------------------------------------
-// k_scan: Eq. 4 - Eq. 6 with one warp per candidate, for lines of up to CAP samples; any line, any N.  When the
-// line-per-thread kernel ran first, only the candidates it flagged are processed here.
-//
-// Sort.  The valid samples split into maximal runs already ordered by (W, k) (a run ends where W drops).  A sample
-// of run a precedes, in sorted order, exactly the samples of later runs with smaller W and of earlier runs with W
-// not larger than its own; its rank is its index plus the first count minus the number of samples of earlier runs
-// with larger W.  Runs whose W range does not straddle the sample's W contribute nothing or everything, so only
-// straddling runs need a binary search, and a sample that no other run straddles keeps its index.  A line that is
-// one run is already sorted; a line with more than kMaxRuns runs goes through a counting sort by W bucket and
-// transposition passes within the buckets.
-// Occlusion test (Eq. 5).  Every pair of sorted positions (q, q+d), d <= N/2, is tested once from its lower end:
-// |fl(W_q - W_{q+d})| is symmetric, and |dW| grows with d in sorted order, so the pairs found this way are exactly
-// the ones the walk of Eq. 5 reaches from either end.  q is hit when V_q + beta < V_{q+d}, and q+d when
-// V_{q+d} + beta < V_q; hits on the upper end go to a shared counter.  Eq. 6: the counts are added to O.
-
-constexpr int kMaxRuns = 16;
-
-template <int CAP>
-struct ScanSmem {
-    float uw[CAP];      // W by k; after the sort, hit counters
-    float uv[CAP];      // V by k; after the sort, hit counters
-    float sw[CAP];      // sorted W (hit counters when the line is one run; bucket counts during the bucket sort)
-    float sv[CAP];      // sorted V (hit counters when the line is one run)
-    uint16_t sidx[CAP]; // sample index (k - k0) of each sorted position
-    int32_t runs[kMaxRuns + 2];
-    float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
-    float run_hi[kMaxRuns + 1];   // last (largest) W of each run
-    float lo_after[kMaxRuns + 2]; // min of run_lo over the runs after run b
-    float hi_before[kMaxRuns + 2];// max of run_hi over the runs before run b
-};
-
-// First index in [lo, hi) whose value is > x (upper) or >= x (lower); a[lo..hi) is non-decreasing.
-__device__ __forceinline__ int upper_bound_f(const float* a, int lo, int hi, float x)
-{
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (a[m] <= x) lo = m + 1; else hi = m;
-    }
-    return lo;
-}
-__device__ __forceinline__ int lower_bound_f(const float* a, int lo, int hi, float x)
-{
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (a[m] < x) lo = m + 1; else hi = m;
-    }
-    return lo;
-}
+// k_scan: Eq. 4 - Eq. 6 with one warp per candidate, for lines of up to CAP samples; any line, any N (the per-line
+// steps are scan_line, occ_scanline.cuh).  When the line-per-thread kernel ran first, only the candidates it flagged
+// are processed here.
 
 template <int CAP, int WPB>
 __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args a, int cls)
@@ -1295,10 +1184,6 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
     const uint64_t total0 = pref[nfv];
     const uint64_t total = total0 + (a.strip_px ? pref1[nfv] : 0u);
     if (total == 0) return;
-    const int half = a.N >> 1;
-    const float beta = a.beta, zeta = a.zeta;
-    const unsigned lt = (1u << lane) - 1u;
-
     int cur_v = -1;
     unsigned long long acc_n = 0, acc_p = 0;
 
@@ -1332,302 +1217,12 @@ __global__ void __launch_bounds__(WPB * 32) k_scan(const __grid_constant__ Args 
         todo &= todo - 1;
         const int i = __shfl_sync(kFull, my_i, jl);
         const int64_t idx = (int64_t)__shfl_sync(kFull, my_idx, jl);
-        const int f = i / a.nv, v = i - f * a.nv;
-        const FrameArg& F = a.frames[f];
-        const uint32_t cw = F.cand[(int64_t)v * F.cap + idx];
-        const ViewArg va = a.view[v];
-        const float fcx = (float)(cw & 0xFFFFu), fcy = (float)(cw >> 16);
-        const bool one = (va.r == 1.0f);
-        const int h = a.plan[i].h;
-        const int nk = 2 * h + 1;
-        const int W = F.W;
-        const float fW = (float)F.W, fH = (float)F.H;
-
-        // Eq. 4: positions, bounds, V = D_r at the nearest pixel, W = g - V.
-        int k0 = -1, kl = -1, n = 0;
-        auto record = [&](int base, bool ok) {
-            const unsigned b = __ballot_sync(kFull, ok);
-            if (b) {
-                if (k0 < 0) k0 = base + __ffs(b) - 1;
-                kl = base + 31 - __clz(b);
-                n += __popc(b);
-            }
-        };
-        if constexpr (CAP <= 256) {
-            // Every lane's gathers (at most CAP / 32) are issued before any is used.
-            constexpr int kSl = CAP / 32;
-            float dvs[kSl];
-            bool oks[kSl];
-#pragma unroll
-            for (int i = 0; i < kSl; i++) {
-                const int k = i * 32 + lane;
-                oks[i] = false;
-                dvs[i] = 0.0f;
-                if (k < nk) {
-                    const float g = (float)(k - h);
-                    const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
-                    const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
-                    oks[i] = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
-                    if (oks[i]) dvs[i] = __ldg(F.D + (int64_t)(int)ry * F.pitch + (int)rx);
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < kSl; i++) {
-                const int base = i * 32;
-                if (base >= nk) break;
-                const int k = base + lane;
-                if (oks[i]) {
-                    const float V = one ? dvs[i] : __fmul_rn(va.r, dvs[i]);
-                    S.uw[k] = __fsub_rn((float)(k - h), V);
-                    S.uv[k] = V;
-                }
-                record(base, oks[i]);
-            }
-        } else {
-            for (int base = 0; base < nk; base += 32) {
-                const int k = base + lane;
-                bool ok = false;
-                if (k < nk) {
-                    const float g = (float)(k - h);
-                    const float rx = roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
-                    const float ry = roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
-                    ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
-                    if (ok) {
-                        const float dv = __ldg(F.D + (int64_t)(int)ry * F.pitch + (int)rx);
-                        const float V = one ? dv : __fmul_rn(va.r, dv);
-                        S.uw[k] = __fsub_rn(g, V);
-                        S.uv[k] = V;
-                    }
-                }
-                record(base, ok);
-            }
-        }
-        // The samples inside the image form one interval of k (positions are monotone in g).
-        if (n == 0 || kl - k0 + 1 != n) {
-            if (lane == 0 && n != 0) atomicOr(a.status, ST_INTERNAL);
-            __syncwarp();
-            continue;
-        }
-        __syncwarp();
-        const float* uw = S.uw + k0;
-        const float* uv = S.uv + k0;
-
-        // Runs: a new run starts after every descent W[i+1] < W[i].
-        int R = 1;
-        for (int base = 0; base < n - 1; base += 32) {
-            const int i = base + lane;
-            const bool dsc = (i < n - 1) && (uw[i + 1] < uw[i]);
-            const unsigned b = __ballot_sync(kFull, dsc);
-            if (dsc) {
-                const int slot = R + __popc(b & lt);
-                if (slot <= kMaxRuns) S.runs[slot] = i + 1;
-            }
-            R += __popc(b);
-        }
-
-        const float* sw;
-        const float* sv;
-        int* cnt_own;
-        int* cnt_up;
-        if (R == 1) {
-            sw = uw; sv = uv;
-            cnt_own = reinterpret_cast<int*>(S.sv);
-            cnt_up = reinterpret_cast<int*>(S.sw);
-        } else {
-            sw = S.sw; sv = S.sv;
-            cnt_own = reinterpret_cast<int*>(S.uv);
-            cnt_up = reinterpret_cast<int*>(S.uw);
-            if (R <= kMaxRuns) {
-                if (lane == 0) {
-                    S.runs[0] = 0;
-                    S.runs[R] = n;
-                }
-                __syncwarp();
-                if (lane < R) {
-                    S.run_lo[lane] = uw[S.runs[lane]];
-                    S.run_hi[lane] = uw[S.runs[lane + 1] - 1];
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    float m = INFINITY;
-                    S.lo_after[R] = m;
-                    for (int b = R - 1; b >= 0; b--) {
-                        S.lo_after[b] = m;            // min run_lo over runs b+1 .. R-1
-                        m = fminf(m, S.run_lo[b]);
-                    }
-                    float x = -INFINITY;
-                    for (int b = 0; b < R; b++) {
-                        S.hi_before[b] = x;           // max run_hi over runs 0 .. b-1
-                        x = fmaxf(x, S.run_hi[b]);
-                    }
-                }
-                __syncwarp();
-                for (int i = lane; i < n; i += 32) {
-                    const float wi = uw[i];
-                    int ra = 0;
-                    while (ra + 1 < R && S.runs[ra + 1] <= i) ra++;
-                    int rank = i;
-                    if (S.lo_after[ra] < wi) {        // some later run has smaller W
-                        for (int b = ra + 1; b < R; b++) {
-                            if (S.run_lo[b] >= wi) continue;
-                            const int st = S.runs[b], en = S.runs[b + 1];
-                            rank += (S.run_hi[b] < wi) ? en - st : lower_bound_f(uw, st, en, wi) - st;
-                        }
-                    }
-                    if (S.hi_before[ra] > wi) {       // some earlier run has larger W
-                        for (int b = 0; b < ra; b++) {
-                            if (S.run_hi[b] <= wi) continue;
-                            const int st = S.runs[b], en = S.runs[b + 1];
-                            rank -= (S.run_lo[b] > wi) ? en - st : en - upper_bound_f(uw, st, en, wi);
-                        }
-                    }
-                    S.sw[rank] = wi;
-                    S.sv[rank] = uv[i];
-                    S.sidx[rank] = (uint16_t)i;
-                }
-            } else {
-                // Many runs: a counting sort by the bucket (int)(fl(W - W_min) * scale) -- a non-decreasing function of W,
-                // so it orders the samples of different buckets -- then odd-even transposition passes by (W, index)
-                // until none swaps, which orders the samples within a bucket.  Buckets are about one W unit wide, at
-                // most CAP of them, so most hold a sample or two.
-                float wlo = INFINITY, whi = -INFINITY;
-                for (int i = lane; i < n; i += 32) {
-                    wlo = fminf(wlo, uw[i]);
-                    whi = fmaxf(whi, uw[i]);
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    wlo = fminf(wlo, __shfl_xor_sync(kFull, wlo, o));
-                    whi = fmaxf(whi, __shfl_xor_sync(kFull, whi, o));
-                }
-                const float span = __fsub_rn(whi, wlo);
-                int B = CAP;
-                float scale = 1.0f;
-                if (span < (float)(CAP - 1)) B = (int)span + 1;
-                else scale = (float)(CAP - 1) / span;
-                auto bucket = [&](float w) { return min((int)(__fsub_rn(w, wlo) * scale), B - 1); };
-                int* cnt = reinterpret_cast<int*>(S.sw);
-                for (int b = lane; b < B; b += 32) cnt[b] = 0;
-                __syncwarp();
-                for (int i = lane; i < n; i += 32) atomicAdd(&cnt[bucket(uw[i])], 1);
-                __syncwarp();
-                // Exclusive prefix sums of the counts, 32 buckets at a time.
-                int carry = 0;
-                for (int b0 = 0; b0 < B; b0 += 32) {
-                    const int b = b0 + lane;
-                    const int c = b < B ? cnt[b] : 0;
-                    int incl = c;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(kFull, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    if (b < B) cnt[b] = carry + incl - c;
-                    carry += __shfl_sync(kFull, incl, 31);
-                }
-                __syncwarp();
-                for (int i = lane; i < n; i += 32) S.sidx[atomicAdd(&cnt[bucket(uw[i])], 1)] = (uint16_t)i;
-                __syncwarp();
-                for (;;) {
-                    bool swapped = false;
-#pragma unroll
-                    for (int par = 0; par < 2; par++) {
-                        for (int i = 2 * lane + par; i + 1 < n; i += 64) {
-                            const int ia = S.sidx[i], ib = S.sidx[i + 1];
-                            const float wa = uw[ia], wb = uw[ib];
-                            if (wa > wb || (wa == wb && ia > ib)) {
-                                S.sidx[i] = (uint16_t)ib;
-                                S.sidx[i + 1] = (uint16_t)ia;
-                                swapped = true;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                    if (!__any_sync(kFull, swapped)) break;
-                }
-                for (int q = lane; q < n; q += 32) {
-                    const int idx = S.sidx[q];
-                    S.sw[q] = uw[idx];
-                    S.sv[q] = uv[idx];
-                }
-            }
-        }
-        __syncwarp();
-
-        // Eq. 5, every pair once from its lower sorted end.
-        for (int q = lane; q < n; q += 32) cnt_up[q] = 0;
-        __syncwarp();
-        for (int q = lane; q < n; q += 32) {
-            const float wq = sw[q];
-            const float vq = sv[q];
-            const float vbq = __fadd_rn(vq, beta);
-            int o = 0;
-            if (half <= 4) {
-#pragma unroll
-                for (int d = 1; d <= 4; d++) {
-                    if (d <= half && q + d < n) {
-                        const float wd = sw[q + d];
-                        const float vd = sv[q + d];
-                        const bool close = fabsf(__fsub_rn(wq, wd)) < zeta;
-                        o += (close && vbq < vd) ? 1 : 0;
-                        if (close && __fadd_rn(vd, beta) < vq) atomicAdd(&cnt_up[q + d], 1);
-                    }
-                }
-            } else {
-                for (int d = 1; d <= half && q + d < n; d++) {
-                    const float wd = sw[q + d];
-                    if (!(fabsf(__fsub_rn(wq, wd)) < zeta)) break;
-                    const float vd = sv[q + d];
-                    o += (vbq < vd) ? 1 : 0;
-                    if (__fadd_rn(vd, beta) < vq) atomicAdd(&cnt_up[q + d], 1);
-                }
-            }
-            cnt_own[q] = o;
-        }
-        __syncwarp();
-        // Eq. 6: add every sample's count to the occlusion sum of its pixel, found again from its k (Eq. 4).  A strip
-        // view's O is final apart from these lines, and k_mask does not run for it: M is set here.
-        int32_t* Ov = F.O + (int64_t)v * F.H * F.W;
-        uint8_t* Mv = F.M + (int64_t)v * F.H * F.W;
-        const bool strip_view = va.fam >= 0;
-        bool hit = false;
-        for (int q = lane; q < n; q += 32) {
-            const int o = cnt_own[q] + cnt_up[q];
-            if (o) {
-                const float g = (float)(k0 + (R == 1 ? q : (int)S.sidx[q]) - h);
-                const int px = (int)roundf(__fadd_rn(__fmul_rn(va.c, g), fcx));
-                const int py = (int)roundf(__fadd_rn(__fmul_rn(va.s, g), fcy));
-                atomicAdd(Ov + py * W + px, o);
-                if (strip_view) Mv[py * W + px] = 1;
-                hit = true;
-            }
-        }
-        if (__any_sync(kFull, hit) && lane == 0 && F.hits) {
-            const int cx = (int)(cw & 0xFFFFu), cy = (int)(cw >> 16);
-            F.hits[(int64_t)v * F.tiles_x * F.tiles_y + (cy / kTile) * F.tiles_x + cx / kTile] = 1;
-        }
-
-        if (lane == 0) {
-            if (i != cur_v) {
-                if (cur_v >= 0) {
-                    const int cf = cur_v / a.nv, cv = cur_v - cf * a.nv;
-                    atomicAdd(&a.frames[cf].stats[2 * cv], acc_n);
-                    atomicAdd(&a.frames[cf].stats[2 * cv + 1], acc_p);
-                }
-                cur_v = i;
-                acc_n = acc_p = 0;
-            }
-            acc_n += (unsigned long long)n;
-            acc_p += pair_count(n, half);
-        }
-        __syncwarp();
+        const FrameArg& F = a.frames[i / a.nv];
+        const uint32_t cw = F.cand[(int64_t)(i % a.nv) * F.cap + idx];
+        scan_item<CAP>(a, a.frames, S, lane, i, cw, cur_v, acc_n, acc_p);
         }
     }
-    if (lane == 0 && cur_v >= 0) {
-        const int cf = cur_v / a.nv, cv = cur_v - cf * a.nv;
-        atomicAdd(&a.frames[cf].stats[2 * cv], acc_n);
-        atomicAdd(&a.frames[cf].stats[2 * cv + 1], acc_p);
-    }
+    flush_item_stats(a.frames, a.nv, lane, cur_v, acc_n, acc_p);
 }
 
 // ------------------------------------------------------------------------------------------------------------------
@@ -1704,7 +1299,7 @@ cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st)
 
 cudaError_t launch_tables(const Args& a, cudaStream_t st)
 {
-    const int64_t total = (int64_t)a.nv * kSTabLen;
+    const int64_t total = (int64_t)a.nv * kTabLen;
     k_tables<<<(int)((total + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -1722,8 +1317,8 @@ cudaError_t launch_minmax(const Args& a, cudaStream_t st)
 {
     int bx = (a.max_quads + kMinMaxThreads - 1) / kMinMaxThreads;
     if (bx > 1024) bx = 1024;
-    if (bx < 8) bx = 8;
-    k_minmax<<<dim3(bx, a.nf + 1), kMinMaxThreads, 0, st>>>(a);
+    if (bx < 1) bx = 1;
+    k_minmax<<<dim3(bx, a.nf), kMinMaxThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

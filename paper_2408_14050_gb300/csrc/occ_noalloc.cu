@@ -22,13 +22,13 @@ constexpr size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t kOffHdr = 0;
 constexpr size_t kOffStats = kOffHdr + align_up(sizeof(uint32_t) * HDR_WORDS);
 constexpr size_t kOffStatus = kOffStats + align_up(sizeof(unsigned long long) * 2 * OCC_MAX_VIEWS);
-constexpr size_t kOffFrames = kOffStatus + 256;
+constexpr size_t kOffFrames = kOffStatus + kStatusBytes;
 constexpr size_t kOffPlan = kOffFrames + align_up(sizeof(FrameArg));
 constexpr size_t kOffPref = kOffPlan + align_up(sizeof(PlanEntry) * OCC_MAX_VIEWS);
 constexpr size_t kOffTab = kOffPref + align_up(sizeof(uint32_t) * (1 + 2 * kNumClasses) * (OCC_MAX_VIEWS + 1));
 constexpr size_t kFlagWords = OCC_NOALLOC_MAX_PIXEL_VIEWS / 32 + OCC_MAX_VIEWS;
 constexpr size_t kOffSTab = kOffTab + align_up(sizeof(int32_t) * kTabLen * OCC_MAX_VIEWS);
-constexpr size_t kOffFlags = kOffSTab + align_up(sizeof(int16_t) * kSTabLen * OCC_MAX_VIEWS);
+constexpr size_t kOffFlags = kOffSTab + align_up(sizeof(int16_t) * kSTabLen * kNumSTabs);
 constexpr size_t kBrkEntries = OCC_NOALLOC_MAX_PIXEL_VIEWS;
 constexpr size_t kOffBrk = kOffFlags + align_up(sizeof(uint32_t) * kFlagWords);
 constexpr size_t kOffCand = kOffBrk + align_up(sizeof(uint32_t) * kBrkEntries);
@@ -75,7 +75,8 @@ cudaError_t setup_device(DeviceSetup& s)
     sc.cand_entries = OCC_NOALLOC_MAX_PIXEL_VIEWS;
     sc.max_frames = 1;
     sc.max_views = OCC_MAX_VIEWS;
-    return cudaSuccess;
+    if ((e = write_strip_tables(sc.stab)) != cudaSuccess) cudaGetLastError();
+    return e;
 }
 
 }  // namespace

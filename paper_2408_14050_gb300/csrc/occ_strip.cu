@@ -8,12 +8,15 @@
 //      of them, one bit per pixel;
 //   2. it compacts the candidates (ballots, block prefix sums) into a queue, round by round;
 //   3. per candidate, one pass over its scan line with the one-slot buffer finds its macro-runs (the stretches the
-//      buffer sorts): lines of one macro-run go to one queue, lines of two to another, longer lines to the frame's
-//      list for the warp kernel k_scan;
+//      buffer sorts): lines of one macro-run go to one queue, lines of two to another, longer lines to a short list
+//      of the strip (those that do not fit it, or have more than 255 samples, to the frame's list for the warp
+//      kernel k_scan);
 //   4. the lines of each queue are counted in batches of 32 per warp, every lane streaming one line: a plain stream
 //      (one run) or the merge of two one-slot buffers (two runs), the sorted samples tested against the N/2 emitted
 //      before them (Eq. 5), final counts added to the strip's occlusion sums O in shared memory (Eq. 6);
-//   5. it writes O and M = (O > 0) of its lines once, coalesced: no zero fill, no global atomics, no mask pass.
+//   5. the lines of the strip's short list, one warp each, go through the warp sort of the list path (scan_line),
+//      their counts added to the same shared sums;
+//   6. it writes O and M = (O > 0) of its lines once, coalesced: no zero fill, no global atomics, no mask pass.
 // O of one strip pixel fits 16 bits: at most 2h + 1 <= 4095 scan lines reach a pixel, each with at most two samples
 // on it (|cos| or |sin| <= 1 moves a diagonal line by at most one pixel per step) and each sample counts at most
 // N = 8 partners, so O <= 65520; two sums share a 32-bit word and are added with 32-bit shared atomics, which cannot
@@ -21,9 +24,13 @@
 //
 // Every floating-point operation that decides a candidate, an order or a count is the same round-to-nearest binary32
 // operation as in the list path (occ_kernels.cu) and the oracle, so the results are bit-identical.
+#include <atomic>
 #include <cstdint>
+#include <cstring>
 
 #include "occ_internal.cuh"
+#include "occ_common.cuh"
+#include "occ_scanline.cuh"
 
 namespace occ {
 
@@ -33,6 +40,23 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kStripThreads = 128;
 constexpr int kStripWarps = kStripThreads / 32;
 constexpr int kStripQueue = 512;           // queue entries of one round
+constexpr int kStripMany = 64;             // fused kernel: lines of three or more macro-runs a strip keeps to publish
+constexpr int kStripManyMaxH = 127;        // ... when their 2h + 1 samples fit the 256-sample warp buffers
+
+// Shared memory of a strip block: a 16-byte guard, D_r and the O words of strip_px pixels, two candidate bit maps, the
+// line queue and the round's candidates.
+__host__ __device__ __forceinline__ size_t strip_smem_bytes(int strip_px)
+{
+    return 16 + (size_t)strip_px * 4 + (size_t)strip_px * 4 + (size_t)strip_px / 4 + sizeof(uint2) * kStripQueue +
+           sizeof(uint32_t) * kStripQueue;
+}
+
+// The fused launch's tag of its published-line entries: the count of earlier launches (CTR_EPOCH, raised by the last
+// block to end, so constant while any block runs), top bit set so that it is never 0.
+__device__ __forceinline__ uint32_t fused_tag(const Args& a)
+{
+    return (*reinterpret_cast<const volatile uint32_t*>(a.status + CTR_EPOCH) & 0x7FFFFFFFu) | 0x80000000u;
+}
 
 // First pixel (x0, y0), step (ax, ay) per position and length n of line l of a family.
 __device__ __forceinline__ void line_geom(int fam, int H, int W, int l, int& x0, int& y0, int& ay, int& n)
@@ -355,27 +379,31 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t* s_warp, uin
     return x + before;
 }
 
-template <bool kHits>
-__global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constant__ Args a)
+// One strip (index sid over the call's strips) of the strip kernel, run by the whole block; frames: the call's frame
+// records.  kFused (the fused kernel): the lines of three or more macro-runs are kept in shared memory and published
+// after the strip's O is written, for the worker blocks; the rest go to the views' lists, as in k_strip.
+template <bool kHits, bool kFused>
+__device__ __forceinline__ void strip_run(const Args& a, const FrameArg* frames, uint32_t sid)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_warp[kStripWarps];
     __shared__ uint32_t s_n1, s_n2, s_b1, s_cand[2];
     __shared__ unsigned long long s_st[2][2];
+    __shared__ uint2 s_many[kStripMany];
+    __shared__ uint32_t s_n3;
 
     const int tid = threadIdx.x, lane = tid & 31;
-    // The strip of this CTA: frame (last with strip0 <= block), then the groups' strips in group order.
-    const uint32_t sid = blockIdx.x;
+    // The strip: frame (last with strip0 <= sid), then the groups' strips in group order.
     int f = 0;
     {
         int lo = 0, hi = a.nf - 1;
         while (lo < hi) {
             const int m = (lo + hi + 1) >> 1;
-            if (a.frames[m].strip0 <= sid) lo = m; else hi = m - 1;
+            if (frames[m].strip0 <= sid) lo = m; else hi = m - 1;
         }
         f = lo;
     }
-    const FrameArg& F = a.frames[f];
+    const FrameArg& F = frames[f];
     const int H = F.H, W = F.W;
     // Fields used in the pixel loops, held in registers (a global record might alias the stores as far as the
     // compiler can tell, and would be read again after each one).
@@ -417,8 +445,8 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
     uint32_t* sBits = sO + a.strip_px;                                                      // [2][strip_px / 32]
     uint2* sQ = reinterpret_cast<uint2*>(sBits + 2 * (a.strip_px / 32));                    // [kStripQueue]
     uint32_t* sRaw = reinterpret_cast<uint32_t*>(sQ + kStripQueue);                         // [kStripQueue]
-    const int16_t* tabs[2] = {a.stab + (int64_t)vw0 * kSTabLen + (kTabHalf - h),
-                              a.stab + (int64_t)vw1 * kSTabLen + (kTabHalf - h)};
+    const int16_t* tabs[2] = {a.stab + (int64_t)va.stab * kSTabLen + (kTabHalf - h),
+                              a.stab + (int64_t)vb.stab * kSTabLen + (kTabHalf - h)};
 
     const int npx = nb * len;   // shared positions of the strip (lines shorter than len leave some unused)
     const int nwords = (npx + 31) >> 5;
@@ -428,7 +456,10 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
         s_cand[tid] = 0;
         s_st[tid][0] = s_st[tid][1] = 0;
     }
-    if (tid == 0) smem_guard_init(smem);
+    if (tid == 0) {
+        smem_guard_init(smem);
+        s_n3 = 0;
+    }
     __syncthreads();
 
     // Thread layout of the two pixel passes (staging, output), without divisions per pixel: along rows every thread
@@ -581,7 +612,16 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
             } else if (runs == 2) {
                 sQ[kStripQueue - 1 - atomicAdd(&s_n2, 1u)] = make_uint2(w0, (uint32_t)k1 | ((uint32_t)ks << 16));
             } else {
-                // Three or more macro-runs: listed for the warp kernel (k_scan), which adds its counts to O and M.
+                // Three or more macro-runs: listed for the warp kernel k_scan, which adds its counts to O and M; in the
+                // fused kernel first kept in the strip's short list (published after O is written), while it has room
+                // and the line fits the warp buffers of the workers' shared memory.
+                if (kFused && h <= kStripManyMaxH) {
+                    const uint32_t i3 = atomicAdd(&s_n3, 1u);
+                    if (i3 < (uint32_t)kStripMany) {
+                        s_many[i3] = make_uint2(w0, (uint32_t)k1);
+                        continue;
+                    }
+                }
                 int x, y;
                 line_pixel(fam, x0, y0, ay, tc, x, y);
                 const int v = w ? vw1 : vw0;
@@ -676,27 +716,70 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
         if (s_st[tid][1]) atomicAdd(&F.stats[2 * v + 1], s_st[tid][1]);
         if (s_cand[tid]) atomicAdd(&F.hdr[HDR_COUNT + v], s_cand[tid]);
     }
+    if constexpr (kFused) {
+        // 6. The kept lines, published for the workers now that O and M of the strip are written: each in an entry of
+        //    the pool reserved for the strip, the launch's tag written last (after a fence).  Entries past the pool's
+        //    end go to the views' lists instead, which the workers take once every strip is done.
+        const uint32_t n3 = min(s_n3, (uint32_t)kStripMany);
+        if (n3 > 0) {
+            __shared__ uint32_t s_off;
+            if (tid == 0) s_off = atomicAdd(&a.status[CTR_POOL], n3);
+            __syncthreads();
+            const uint32_t off = s_off;
+            for (uint32_t e = tid; e < n3; e += kStripThreads) {
+                const uint2 q = s_many[e];
+                const int w = (int)(q.x >> 28);
+                const int b = (int)((q.x >> 12) & 15u), tc = (int)(q.x & 4095u);
+                int x0, y0, ay, nl, x, y;
+                line_geom(fam, H, W, l0 + b, x0, y0, ay, nl);
+                line_pixel(fam, x0, y0, ay, tc, x, y);
+                const int v = w ? vw1 : vw0;
+                const uint32_t cw = ((uint32_t)y << 16) | (uint32_t)x;
+                const uint64_t j = (uint64_t)off + e;
+                if (j < a.fz.pool_cap) {
+                    uint4* ent = a.fz.pool + j;
+                    ent->x = cw;
+                    ent->y = ((uint32_t)f << 8) | (uint32_t)v;
+                    __threadfence();
+                    *reinterpret_cast<volatile uint32_t*>(&ent->z) = fused_tag(a);
+                } else {
+                    const uint32_t i = atomicAdd(&F.hdr[HDR_OVF + v], 1u);
+                    if ((int64_t)i < F.cap) {
+                        F.cand[(int64_t)v * F.cap + i] = cw;
+                    } else {
+                        atomicOr(&F.hdr[HDR_STATUS], ST_CAND_OVERFLOW);
+                        atomicOr(a.status, ST_CAND_OVERFLOW);
+                    }
+                }
+            }
+        }
+    }
 }
 
-// k_plan_ovf: per size class, the prefix sums over (frame, view) of the lines k_strip listed (clamped to the list
-// capacity), for k_scan.  One block, one (frame, view) per thread and iteration.
-constexpr int kPlanOvfThreads = 1024;
+template <bool kHits>
+__global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constant__ Args a)
+{
+    strip_run<kHits, false>(a, a.frames, blockIdx.x);
+}
 
-__global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_constant__ Args a)
+// The prefix sums over (frame, view), per size class, of the lines the strips listed (clamped to the list capacity),
+// for the warp kernels: one block of T threads, one (frame, view) per thread and iteration.
+template <int T>
+__device__ __forceinline__ void plan_ovf_block(const Args& a, const FrameArg* frames)
 {
     __shared__ uint32_t s_carry[kNumClasses];
-    __shared__ uint32_t s_warp[kPlanOvfThreads / 32][kNumClasses];
+    __shared__ uint32_t s_warp[T / 32][kNumClasses];
     const int n = a.nf * a.nv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int stride = n + 1;
     if (threadIdx.x < kNumClasses) s_carry[threadIdx.x] = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += kPlanOvfThreads) {
+    for (int base = 0; base < n; base += T) {
         const int i = base + threadIdx.x;
         uint32_t cnt[kNumClasses] = {0, 0, 0};
         if (i < n) {
             const int f = i / a.nv, v = i - f * a.nv;
-            const FrameArg& F = a.frames[f];
+            const FrameArg& F = frames[f];
             const PlanEntry pe = a.plan[i];
             if (a.view[v].fam >= 0 && pe.h >= 0) {
                 uint32_t c = F.hdr[HDR_OVF + v];
@@ -720,7 +803,7 @@ __global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_const
         if (threadIdx.x < kNumClasses) {
             const int c = threadIdx.x;
             uint32_t run = s_carry[c];
-            for (int w = 0; w < kPlanOvfThreads / 32; w++) {
+            for (int w = 0; w < T / 32; w++) {
                 const uint32_t t = s_warp[w][c];
                 s_warp[w][c] = run;
                 run += t;
@@ -737,12 +820,336 @@ __global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_const
     if (threadIdx.x < kNumClasses) a.pref_ovf[threadIdx.x * stride + n] = s_carry[threadIdx.x];
 }
 
+// k_plan_ovf: plan_ovf_block after k_strip, for k_scan.
+constexpr int kPlanOvfThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_constant__ Args a)
+{
+    plan_ovf_block<kPlanOvfThreads>(a, a.frames);
+}
+
+// ------------------------------------------------------------------------------------------------------------------
+// k_fused: the whole call in one launch, for calls whose views all take the strip kernel and that ask for no E, A or
+// tile hits.  Blocks take tickets from one counter (CTR_TICKET), in this order:
+//   min/max  kFusedQuadsPerTicket quads of one frame's D each (as k_minmax); the block that finishes a frame's last
+//            one writes the frame's plan (Eq. 3: L and h per view) and releases it (HDR_READY);
+//   strips   strip_run after the frame's plan; its kept lines of three or more macro-runs are
+//            published (pool entries plus one completion record) once its O and M are written; the block that
+//            finishes the last strip writes the prefix sums of the lines in the views' lists (CTR_OVF_READY);
+//   workers  one per block: the published lines, one warp each, taken line by line from the completion records in
+//            order (the sort of the warp kernels, counts added to O with global atomics, M set); then, once every
+//            strip is done, the listed lines of every size class.
+// A ticket waits only for tickets handed out before it, and every such ticket is held by a block that is running and
+// waits only for earlier ones, so the launch needs no co-residency: the earliest unfinished ticket always progresses.
+// Every wait is bounded (FusedPlan::wait_ns, from %globaltimer, and a spin count); one that gives up sets ST_TIMEOUT
+// and CTR_ABORT, and every block then stops at its next wait or ticket.  Data written earlier in the launch is read
+// with plain loads after an acquiring wait, never through the read-only cache.
+
+constexpr uint32_t kFusedMaxSpins = 1u << 26;
+constexpr int kFusedSmallFrames = 4;   // launch parameters of a call of at most this many frames
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One thread: gives up the launch (timeout) or sees another block's abort.  Returns true to go on waiting, after a
+// sleep that grows with the spins (128 ns doubling to 8 us), so that waiting blocks leave the memory system to the
+// blocks they wait for.
+__device__ __forceinline__ bool fused_keep_waiting(const Args& a, uint64_t t0, uint32_t it)
+{
+    if (*reinterpret_cast<volatile uint32_t*>(a.status + CTR_ABORT)) return false;
+    if ((it & 15u) == 15u && (global_ns() - t0 > a.fz.wait_ns || it > kFusedMaxSpins)) {
+        atomicOr(a.status, ST_TIMEOUT);
+        atomicExch(a.status + CTR_ABORT, 1u);
+        return false;
+    }
+    __nanosleep(128u << min(it, 6u));
+    return true;
+}
+
+// One thread: waits until *p >= target, then acquires (fence).  false: the launch gave up.
+__device__ __forceinline__ bool fused_wait_geq(const Args& a, const uint32_t* p, uint32_t target)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; it++) {
+        if (*reinterpret_cast<const volatile uint32_t*>(p) >= target) {
+            __threadfence();
+            return true;
+        }
+        if (!fused_keep_waiting(a, t0, it)) return false;
+    }
+}
+
+// One thread: marks a ticket done (release) and returns the count before it.
+__device__ __forceinline__ uint32_t fused_done(uint32_t* ctr)
+{
+    __threadfence();
+    return atomicAdd(ctr, 1u);
+}
+
+// The (frame, view) of a listed line: the last i with pref[i] <= item (plain loads: written in this launch).
+__device__ __forceinline__ int fused_owner(const uint32_t* pref, int n, uint32_t item)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (pref[m] <= item) lo = m; else hi = m - 1;
+    }
+    return lo;
+}
+
+// The listed lines of size class CAP, one warp each, from the class's cursor.
+template <int CAP>
+__device__ __forceinline__ void fused_listed(const Args& a, const FrameArg* frames, ScanSmem<CAP>& S, int cls, int lane,
+                                             int& cur_v, unsigned long long& acc_n, unsigned long long& acc_p)
+{
+    const int nfv = a.nf * a.nv;
+    const uint32_t* pref = a.pref_ovf + (int64_t)cls * (nfv + 1);
+    const uint32_t total = pref[nfv];
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(a.status + CTR_OVF_CURSOR + cls, 1u);
+        item = __shfl_sync(kFullMask, item, 0);
+        if (item >= total) break;
+        const int i = fused_owner(pref, nfv, item);
+        const FrameArg& F = frames[i / a.nv];
+        const uint32_t cw = F.cand[(int64_t)(i % a.nv) * F.cap + (item - pref[i])];
+        scan_item<CAP>(a, frames, S, lane, i, cw, cur_v, acc_n, acc_p);
+    }
+}
+
+// One published line for a worker warp (lane 0 decides, the warp gets the result): the next pool entry from the
+// claim counter, once it carries this launch's tag.  Returns 1 with the line in *line, 0 when every strip is done and
+// no published entry is left, -1 when the launch gave up.
+__device__ __forceinline__ int fused_next_published(const Args& a, uint2* line)
+{
+    const uint32_t epoch = fused_tag(a);
+    int res = -1;
+    uint2 q = make_uint2(0u, 0u);
+    if ((threadIdx.x & 31) == 0) {
+        const uint32_t j = atomicAdd(a.status + CTR_CLAIM, 1u);
+        const uint64_t t0 = global_ns();
+        for (uint32_t it = 0;; it++) {
+            if (j < a.fz.pool_cap && *reinterpret_cast<const volatile uint32_t*>(&a.fz.pool[j].z) == epoch) {
+                __threadfence();
+                q = make_uint2(a.fz.pool[j].x, a.fz.pool[j].y);
+                res = 1;
+                break;
+            }
+            // Every strip done: every entry is reserved and written, and one past them (or past the pool) is none.
+            if (*reinterpret_cast<const volatile uint32_t*>(a.status + CTR_STRIPS) >= a.strip_total) {
+                __threadfence();
+                if (j >= a.fz.pool_cap || j >= *reinterpret_cast<const volatile uint32_t*>(a.status + CTR_POOL)) {
+                    res = 0;
+                    break;
+                }
+            }
+            if (!fused_keep_waiting(a, t0, it)) break;
+        }
+    }
+    res = __shfl_sync(kFullMask, res, 0);
+    line->x = __shfl_sync(kFullMask, q.x, 0);
+    line->y = __shfl_sync(kFullMask, q.y, 0);
+    return res;
+}
+
+// A worker block (see k_fused).  smem: the block's dynamic shared memory (bytes), slot: its global warp buffer.
+__device__ __noinline__ void fused_worker(const Args& a, const FrameArg* frames, unsigned char* smem, size_t bytes,
+                                          unsigned char* slot)
+{
+    __shared__ int s_got;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int cur_v = -1;
+    unsigned long long acc_n = 0, acc_p = 0;
+    const int slots0 = min(kStripWarps, (int)(bytes / sizeof(ScanSmem<256>)));
+    ScanSmem<256>& S0 = reinterpret_cast<ScanSmem<256>*>(smem)[warp < slots0 ? warp : 0];
+
+    // Published lines, every warp on its own (no block barrier until they are used up).
+    bool gave_up = false;
+    if (warp < slots0) {
+        for (;;) {
+            uint2 q;
+            const int got = fused_next_published(a, &q);
+            if (got <= 0) {
+                gave_up = got < 0;
+                break;
+            }
+            const int f = (int)(q.y >> 8), v = (int)(q.y & 255u);
+            scan_item<256>(a, frames, S0, lane, f * a.nv + v, q.x, cur_v, acc_n, acc_p);
+        }
+    }
+    if (__syncthreads_or(gave_up)) return;
+
+    // The views' lists, once the last strip has written their prefix sums; size classes in turn.  A class's warps
+    // use the shared memory while their buffers fit it, else warp 0 uses the block's global slot.
+    if (tid == 0) s_got = fused_wait_geq(a, a.status + CTR_OVF_READY, 1u) ? 1 : 0;
+    __syncthreads();
+    if (s_got) {
+        if (warp < slots0) fused_listed<256>(a, frames, S0, 0, lane, cur_v, acc_n, acc_p);
+        __syncthreads();   // the next class's buffers overlap this one's
+        const int slots1 = min(kStripWarps, (int)(bytes / sizeof(ScanSmem<1024>)));
+        if (warp < slots1) {
+            fused_listed<1024>(a, frames, reinterpret_cast<ScanSmem<1024>*>(smem)[warp], 1, lane, cur_v, acc_n, acc_p);
+        } else if (slots1 == 0 && warp == 0) {
+            fused_listed<1024>(a, frames, *reinterpret_cast<ScanSmem<1024>*>(slot), 1, lane, cur_v, acc_n, acc_p);
+        }
+        __syncthreads();
+        const int slots2 = min(kStripWarps, (int)(bytes / sizeof(ScanSmem<4096>)));
+        if (warp < slots2) {
+            fused_listed<4096>(a, frames, reinterpret_cast<ScanSmem<4096>*>(smem)[warp], 2, lane, cur_v, acc_n, acc_p);
+        } else if (slots2 == 0 && warp == 0) {
+            fused_listed<4096>(a, frames, *reinterpret_cast<ScanSmem<4096>*>(slot), 2, lane, cur_v, acc_n, acc_p);
+        }
+    }
+    flush_item_stats(frames, a.nv, lane, cur_v, acc_n, acc_p);
+}
+
+// A strip of the fused kernel.
+__device__ __forceinline__ void fused_strip(const Args& a, const FrameArg* frames, uint32_t sid)
+{
+    strip_run<false, true>(a, frames, sid);
+}
+
+template <int NF>
+__global__ void __launch_bounds__(kStripThreads, 5) k_fused(const __grid_constant__ Args a,
+                                                             const __grid_constant__ FusedFrames<NF> fr)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ uint32_t s_t;
+    __shared__ int s_go;
+    __shared__ float s_lo[kStripWarps], s_hi[kStripWarps];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const FrameArg* frames = fr.f;
+    for (;;) {
+        if (tid == 0)
+            s_t = *reinterpret_cast<volatile uint32_t*>(a.status + CTR_ABORT) ? 0xFFFFFFFFu
+                                                                               : atomicAdd(a.status + CTR_TICKET, 1u);
+        __syncthreads();
+        const uint32_t t = s_t;
+        __syncthreads();
+        if (t >= a.fz.end) break;
+        if (t < a.fz.mm_end) {
+            int f = 0;
+            {
+                int lo = 0, hi = a.nf - 1;
+                while (lo < hi) {
+                    const int m = (lo + hi + 1) >> 1;
+                    if (fr.mm0[m] <= t) lo = m; else hi = m - 1;
+                }
+                f = lo;
+            }
+            const FrameArg& F = frames[f];
+            const int QW = (F.W + 3) >> 2;
+            const int64_t nq = (int64_t)F.H * QW;
+            const bool vec = ((F.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(F.D) & 15) == 0);
+            const int64_t q0 = (int64_t)(t - fr.mm0[f]) * kFusedQuadsPerTicket;
+            const int64_t q1 = min(nq, q0 + kFusedQuadsPerTicket);
+            float lo = INFINITY, hi = -INFINITY;
+            bool bad = false;
+            for (int64_t q = q0 + tid; q < q1; q += kStripThreads) minmax_quad(F.D, F.pitch, F.W, QW, vec, q, lo, hi, bad);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(kFullMask, lo, off));
+                hi = fmaxf(hi, __shfl_xor_sync(kFullMask, hi, off));
+            }
+            if (tid == 0) s_bad = 0;
+            __syncthreads();
+            if (__any_sync(kFullMask, bad) && lane == 0) s_bad = 1;
+            if (lane == 0) {
+                s_lo[warp] = lo;
+                s_hi[warp] = hi;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                float blo = INFINITY, bhi = -INFINITY;
+                for (int w = 0; w < kStripWarps; w++) {
+                    blo = fminf(blo, s_lo[w]);
+                    bhi = fmaxf(bhi, s_hi[w]);
+                }
+                if (blo <= bhi) {
+                    atomicMax(&F.hdr[HDR_MAX], f2ord(bhi));
+                    atomicMax(&F.hdr[HDR_NEGMIN], ~f2ord(blo));
+                }
+                if (s_bad) atomicOr(&F.hdr[HDR_STATUS], ST_NONFINITE);
+                const uint32_t before = fused_done(&F.hdr[HDR_MMDONE]);
+                s_go = before + 1 == fr.mm0[f + 1] - fr.mm0[f];
+                if (s_go) __threadfence();
+            }
+            __syncthreads();
+            if (s_go) {
+                // The frame's plan (as k_plan): L and h per view (Eq. 3), the size class of its lines.
+                const uint32_t st = *reinterpret_cast<volatile uint32_t*>(&F.hdr[HDR_STATUS]);
+                const uint32_t hmax = *reinterpret_cast<volatile uint32_t*>(&F.hdr[HDR_MAX]);
+                const uint32_t hneg = *reinterpret_cast<volatile uint32_t*>(&F.hdr[HDR_NEGMIN]);
+                for (int v = tid; v < a.nv; v += kStripThreads) {
+                    PlanEntry pe{-1, 0, 0u, 0u};
+                    if (!(st & ST_NONFINITE)) {
+                        const int L = scan_length(a, hmax, hneg, a.view[v].r);
+                        if (L < 0) {
+                            atomicOr(&F.hdr[HDR_STATUS], ST_SCAN_TOO_LONG);
+                            atomicOr(a.status, ST_SCAN_TOO_LONG);
+                        } else {
+                            F.hdr[HDR_L + v] = (uint32_t)L;
+                            pe.h = (L + 1) / 2;
+                            const int nk = 2 * pe.h + 1;
+                            pe.cls = nk <= 256 ? 0 : (nk <= 1024 ? 1 : 2);   // kClassCap
+                        }
+                    }
+                    a.plan[f * a.nv + v] = pe;
+                }
+                if (tid == 0 && st) atomicOr(a.status, st);
+                __syncthreads();
+                if (tid == 0 && !a.fz.hold) {
+                    __threadfence();
+                    atomicExch(&F.hdr[HDR_READY], 1u);
+                }
+            }
+        } else if (t < a.fz.strip_end) {
+            const uint32_t sid = t - a.fz.mm_end;
+            if (tid == 0) {
+                int lo = 0, hi = a.nf - 1;
+                while (lo < hi) {
+                    const int m = (lo + hi + 1) >> 1;
+                    if (frames[m].strip0 <= sid) lo = m; else hi = m - 1;
+                }
+                s_go = fused_wait_geq(a, &frames[lo].hdr[HDR_READY], 1u);
+            }
+            __syncthreads();
+            if (!s_go) break;
+            fused_strip(a, frames, sid);
+            __syncthreads();
+            if (tid == 0) {
+                s_go = fused_done(a.status + CTR_STRIPS) + 1 == a.strip_total;
+                if (s_go) __threadfence();
+            }
+            __syncthreads();
+            if (s_go) {
+                plan_ovf_block<kStripThreads>(a, frames);
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    atomicExch(a.status + CTR_OVF_READY, 1u);
+                }
+            }
+        } else {
+            fused_worker(a, frames, smem, strip_smem_bytes(a.strip_px),
+                         a.fz.slots + (size_t)blockIdx.x * sizeof(ScanSmem<4096>));
+            break;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && atomicAdd(a.status + CTR_EXIT, 1u) == gridDim.x - 1) atomicAdd(a.status + CTR_EPOCH, 1u);
+}
+
 }  // namespace
 
 size_t strip_smem(int strip_px)
 {
-    return 16 + (size_t)strip_px * 4 + (size_t)strip_px * 4 + (size_t)strip_px / 4 + sizeof(uint2) * kStripQueue +
-           sizeof(uint32_t) * kStripQueue;
+    return strip_smem_bytes(strip_px);
 }
 
 cudaError_t configure_strip()
@@ -750,7 +1157,54 @@ cudaError_t configure_strip()
     const int mx = (int)strip_smem(OCC_STRIP_PX_MAX);
     cudaError_t e = cudaFuncSetAttribute(k_strip<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_strip<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused<kFusedSmallFrames>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused<kFusedMaxFrames>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
     return e;
+}
+
+size_t fused_slot_bytes()
+{
+    return sizeof(ScanSmem<4096>);
+}
+
+int fused_blocks_per_sm(int strip_px)
+{
+    // Per strip size (a multiple of 64 up to OCC_STRIP_PX_MAX), computed once: the occupancy does not change.
+    static std::atomic<int> cache[OCC_STRIP_PX_MAX / 64 + 1];
+    const int key = strip_px / 64;
+    if (strip_px <= 0 || strip_px > OCC_STRIP_PX_MAX || strip_px % 64) return 0;
+    int b = cache[key].load(std::memory_order_relaxed);
+    if (b > 0) return b;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused<kFusedMaxFrames>, kStripThreads,
+                                                      strip_smem(strip_px)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cache[key].store(b, std::memory_order_relaxed);
+    return b;
+}
+
+namespace {
+template <int NF>
+cudaError_t launch_fused_n(const Args& a, const FrameArg* f, const uint32_t* mm0, int nf, int grid, cudaStream_t st)
+{
+    FusedFrames<NF> fr;
+    std::memset(&fr, 0, sizeof(fr));
+    for (int i = 0; i < nf; i++) {
+        fr.f[i] = f[i];
+        fr.mm0[i] = mm0[i];
+    }
+    fr.mm0[nf] = mm0[nf];
+    k_fused<NF><<<grid, kStripThreads, strip_smem(a.strip_px), st>>>(a, fr);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_fused(const Args& a, const FrameArg* f, const uint32_t* mm0, int nf, int grid, cudaStream_t st)
+{
+    if (nf < 1 || nf > kFusedMaxFrames || grid < 1) return cudaErrorInvalidValue;
+    if (nf <= kFusedSmallFrames) return launch_fused_n<kFusedSmallFrames>(a, f, mm0, nf, grid, st);
+    return launch_fused_n<kFusedMaxFrames>(a, f, mm0, nf, grid, st);
 }
 
 cudaError_t launch_strip(const Args& a, cudaStream_t st)

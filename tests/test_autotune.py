@@ -24,6 +24,8 @@ def test_candidates_cover_every_mapping():
     assert {t["warp_lines_per_block"] for t in c} == {4, 8}
     assert all(1 <= t["line_blocks_per_sm"] <= 3 for t in c)
     assert {t["strip_px"] for t in c} == {0, *autotune.STRIP_SHAPES}
+    assert {(t["strip_px"], t["fused"]) for t in c if t["strip_px"]} == {(px, f) for px in autotune.STRIP_SHAPES
+                                                                       for f in (0, 1)}
     assert len({autotune.tuning_name(t) for t in c}) == len(c)
 
 
@@ -62,3 +64,6 @@ def test_every_tuning_gives_the_same_result(tmp_path):
             with pytest.raises(occ.OccError):
                 occ.occ_set_tuning(ctx, {"line_max_runs": 2, "line_blocks_per_sm": 1, "warp_lines_per_block": 8,
                                          "strip_px": px})
+        with pytest.raises(occ.OccError):
+            occ.occ_set_tuning(ctx, {"line_max_runs": 2, "line_blocks_per_sm": 1, "warp_lines_per_block": 8,
+                                     "strip_px": 4096, "fused": 2})

@@ -346,13 +346,14 @@ def test_nonfinite_input_status(ctx):
 
 def test_candidate_overflow_status():
     # A list-path view (10 degrees) with more candidates than the list holds; a strip view (0 degrees) whose scan lines
-    # of three or more macro-runs (uniform noise) exceed it; a constant map has none.
+    # of three or more macro-runs (uniform noise) exceed it: with L = 300 they are longer than the strip kernel keeps
+    # for its own warps, and all go to the list.  A constant map has none.
     c = occ.occ_create(0, max_pixels=64 * 64, max_views=2, max_candidates=10)
     try:
         D = noisy_map(64, 64, seed=2, scale=20)
         assert run_gpu(c, D, [(10.0, 1.0)])["status"] == occ.OCC_ERR_CAPACITY
         U = np.random.default_rng(3).uniform(0, 40, (64, 64)).astype(np.float32)
-        assert run_gpu(c, U, [(0.0, 1.0)])["status"] == occ.OCC_ERR_CAPACITY
+        assert run_gpu(c, U, [(0.0, 1.0)], both_params(L=300)[1])["status"] == occ.OCC_ERR_CAPACITY
         assert run_gpu(c, np.full((64, 64), 1.0, np.float32), [(0.0, 1.0)])["status"] == occ.OCC_OK
     finally:
         c.close()
