@@ -161,7 +161,7 @@ def strip_views(views, tuning: dict, N: int = 8, max_side: int = 1920):
 def fused_call(views, tuning: dict, N: int = 8, max_side: int = 1920) -> bool:
     """An occ_detect without E, A or tile outputs runs as the one fused launch: every view on strips, fused on (and
     room in the context's scratch, which the bench's contexts have)."""
-    return all(strip_views(views, tuning, N, max_side)) and bool(tuning.get("fused", 1))
+    return all(strip_views(views, tuning, N, max_side)) and bool(tuning.get("fused", 0))
 
 
 def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -> int:

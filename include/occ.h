@@ -192,11 +192,11 @@ int occ_get_stats(occ_ctx* ctx, occ_view_stats* out, int32_t n_views);
  *                        it in shared memory and writes O and M once.  0 turns it off (every view takes the
  *                        candidate-list kernels above); otherwise 1024 .. OCC_STRIP_PX_MAX, a multiple of 64,
  *                        raised for a call to its longest row, column or diagonal (default 4096).
- *   fused                1 (default): a call whose views all take the strip kernel and that asks for no E, A or
- *                        tile hits runs as one kernel launch (the min/max of Eq. 3, the plan, the strips and the
- *                        lines of three or more macro-runs, with bounded waits between them; see
- *                        occ_set_wait_limit), when the context's scratch has room for its work lists; 0: the same
- *                        work in separate launches. */
+ *   fused                1: a call whose views all take the strip kernel and that asks for no E, A or tile hits
+ *                        runs as one kernel launch (the min/max of Eq. 3, the plan, the strips and the lines of
+ *                        three or more macro-runs, with bounded waits between them; see occ_set_wait_limit), when
+ *                        the context's scratch has room for its work lists; 0 (default): the same work in separate
+ *                        launches, which measure faster on GB300. */
 #define OCC_STRIP_PX_MAX 16384
 typedef struct {
     int32_t line_max_runs;

@@ -71,7 +71,7 @@ class occ_view_stats(ctypes.Structure):
 class occ_tuning(ctypes.Structure):
     """Mapping of the scan work: line_max_runs (0, 1, 2), line_blocks_per_sm, warp_lines_per_block (4, 8), strip_px
     (0 = no strip kernel, else 1024 .. OCC_STRIP_PX_MAX pixels per strip, a multiple of 64), fused (1 = one launch
-    for calls whose views all take the strip kernel, 0 = separate launches)."""
+    for calls whose views all take the strip kernel, 0 = separate launches, the default)."""
     _fields_ = [("line_max_runs", ctypes.c_int32), ("line_blocks_per_sm", ctypes.c_int32),
                 ("warp_lines_per_block", ctypes.c_int32), ("strip_px", ctypes.c_int32), ("fused", ctypes.c_int32)]
 
@@ -492,7 +492,7 @@ def occ_set_tuning(ctx: Context, tuning: dict | None = None):
     if tuning is not None:
         t = occ_tuning(int(tuning["line_max_runs"]), int(tuning["line_blocks_per_sm"]),
                        int(tuning["warp_lines_per_block"]), int(tuning.get("strip_px", STRIP_PX_DEFAULT)),
-                       int(tuning.get("fused", 1)))
+                       int(tuning.get("fused", 0)))
     rc = load().occ_set_tuning(ctx.handle, ctypes.byref(t) if t is not None else None)
     if rc != OCC_OK:
         raise OccError(rc, "occ_set_tuning")

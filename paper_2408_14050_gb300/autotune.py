@@ -53,12 +53,12 @@ def candidates(max_line_bps: int):
                 if runs == 0 and bps != max_line_bps:
                     continue      # the line kernel does not run: its grid is irrelevant
                 out.append({"line_max_runs": runs, "line_blocks_per_sm": bps, "warp_lines_per_block": wpb,
-                            "strip_px": 0, "fused": 1})
+                            "strip_px": 0, "fused": 0})
     return out
 
 
 def tuning_name(t: dict) -> str:
-    return (f"strip{t['strip_px']}{'f' if t.get('fused', 1) else ''}_runs{t['line_max_runs']}"
+    return (f"strip{t['strip_px']}{'f' if t.get('fused', 0) else ''}_runs{t['line_max_runs']}"
             f"_bps{t['line_blocks_per_sm']}_wpb{t['warp_lines_per_block']}")
 
 

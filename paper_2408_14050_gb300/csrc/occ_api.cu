@@ -128,7 +128,7 @@ cudaError_t scratch_grids(Scratch& sc)
     sc.tuning.line_blocks_per_sm = sc.lines_bps_max;
     sc.tuning.warp_lines_per_block = 8;
     sc.tuning.strip_px = kStripPxDefault;
-    sc.tuning.fused = 1;
+    sc.tuning.fused = 0;
     return cudaSuccess;
 }
 
@@ -648,7 +648,7 @@ int occ_detect_batched(occ_ctx* ctx, int32_t n_frames, const float* const* D, co
 int occ_set_tuning(occ_ctx* ctx, const occ_tuning* t)
 {
     if (!ctx) return OCC_ERR_INVALID_ARG;
-    occ_tuning d{2, ctx->sc.lines_bps_max, 8, kStripPxDefault, 1};
+    occ_tuning d{2, ctx->sc.lines_bps_max, 8, kStripPxDefault, 0};
     if (!t) t = &d;
     if (t->line_max_runs < 0 || t->line_max_runs > 2 || t->line_blocks_per_sm < 1 ||
         t->line_blocks_per_sm > ctx->sc.lines_bps_max || (t->warp_lines_per_block != 4 && t->warp_lines_per_block != 8) ||

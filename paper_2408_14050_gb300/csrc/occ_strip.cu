@@ -40,7 +40,7 @@ constexpr unsigned kFullMask = 0xFFFFFFFFu;
 constexpr int kStripThreads = 128;
 constexpr int kStripWarps = kStripThreads / 32;
 constexpr int kStripQueue = 512;           // queue entries of one round
-constexpr int kStripMany = 64;             // fused kernel: lines of three or more macro-runs a strip keeps to publish
+constexpr int kStripMany = 16;             // fused kernel: lines of three or more macro-runs a strip keeps to publish
 constexpr int kStripManyMaxH = 127;        // ... when their 2h + 1 samples fit the 256-sample warp buffers
 
 // Shared memory of a strip block: a 16-byte guard, D_r and the O words of strip_px pixels, two candidate bit maps, the

@@ -26,12 +26,12 @@ def ctx():
     c.close()
 
 
-def tuning(strip_px, fused=1):
+def tuning(strip_px, fused=0):
     return {"line_max_runs": 2, "line_blocks_per_sm": 1, "warp_lines_per_block": 8, "strip_px": strip_px,
             "fused": fused}
 
 
-def detect(ctx, D, views, strip_px, fused=1, **kw):
+def detect(ctx, D, views, strip_px, fused=0, **kw):
     occ.occ_set_tuning(ctx, tuning(strip_px, fused))
     try:
         d = dict(gamma=1.0, zeta=2.0, beta=0.5, L=0, N=8)
@@ -74,9 +74,10 @@ def test_strip_shapes_match_the_oracle(ctx, shape, strip_px, fused):
     assert st == st0
 
 
-def test_full_frame_strip_and_list_paths_agree(ctx):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_full_frame_strip_and_list_paths_agree(ctx, fused):
     D = scenes.array_3x3(frame=2, H=540, W=960).frames[0]
-    M, O, st = detect(ctx, D, OCTANT, occ.STRIP_PX_DEFAULT)
+    M, O, st = detect(ctx, D, OCTANT, occ.STRIP_PX_DEFAULT, fused)
     M0, O0, st0 = detect(ctx, D, OCTANT, 0)
     np.testing.assert_array_equal(O, O0)
     np.testing.assert_array_equal(M, M0)
@@ -89,16 +90,16 @@ def test_full_frame_strip_and_list_paths_agree(ctx):
 def test_lines_of_many_runs_go_to_the_warp_sort(ctx, strip_px, list_view):
     """Uniform noise breaks scan lines into many macro-runs, which the warp sort of the list path takes.  With a view
     off the strip directions (20 degrees) the call runs in separate launches and the strips list these lines for the
-    warp kernel.  Without it the call is one fused launch: with the automatic L (h <= 100) a strip keeps up to 64 such
+    warp kernel.  Without it the call is one fused launch: with the automatic L (h <= 100) a strip keeps up to 16 such
     lines and publishes them for the worker blocks once its O is written, and lists the rest; with a fixed L of 300
-    (h = 150, the 1024 class) it lists them all, for the workers once every strip is done.  Strips of 1024 pixels leave
-    the workers shared room for fewer warp buffers than strips of 4096."""
+    (h = 150, the 1024 class) or 1100 (the 4096 class) it lists them all, for the workers once every strip is done.
+    Strips of 1024 pixels leave the workers shared room for fewer warp buffers than strips of 4096."""
     rng = np.random.default_rng(8)
     D = rng.uniform(0, 40, (64, 160)).astype(np.float32)
     views = [(0.0, 1.0), (45.0, 2.5), (90.0, 1.0), (135.0, 1.0), (180.0, 2.0), (225.0, 1.0), (270.0, 1.0),
              (315.0, 1.5)] + ([(20.0, 1.0)] if list_view else [])
     for L in (0, 300, 1100):
-        M, O, st = detect(ctx, D, views, strip_px, L=L)
+        M, O, st = detect(ctx, D, views, strip_px, 0 if list_view else 1, L=L)
         check_oracle(D, views, M, O, st, L=L)
 
 
@@ -113,9 +114,11 @@ def test_frames_above_the_strip_limit_use_the_lists(ctx):
         check_oracle(D, OCTANT, M, O, st, N=N)
 
 
-def test_strips_in_batches_and_graphs(ctx):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_strips_in_batches_and_graphs(ctx, fused):
     """Uneven frames of one batch (strips of each frame after the previous frame's), captured in a CUDA graph and
-    replayed on new inputs."""
+    replayed on new inputs, in separate launches and in the fused launch (whose published-line entries carry a tag
+    that changes with every launch, replays included)."""
     sizes = [(48, 64), (100, 77), (270, 480), (31, 200), (1, 9), (129, 130)]
     views = OCTANT
     first = [scenes.make_scene(scenes.spec_array(H, W), scenes.seed_of(92, i)) if min(H, W) > 8 else
@@ -124,21 +127,27 @@ def test_strips_in_batches_and_graphs(ctx):
     Ds = [torch.from_numpy(f).cuda() for f in first]
     Ms = [torch.empty((len(views), *D.shape), dtype=torch.uint8, device="cuda") for D in Ds]
     Os = [torch.empty((len(views), *D.shape), dtype=torch.int32, device="cuda") for D in Ds]
-    occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
+    occ.occ_set_tuning(ctx, tuning(occ.STRIP_PX_DEFAULT, fused))
+    try:
         occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)
-    for f_np, D in zip(second, Ds):
-        D.copy_(torch.from_numpy(f_np).cuda())
-    g.replay()
-    torch.cuda.synchronize()
-    assert occ.occ_get_status(ctx) == occ.OCC_OK
-    for f_np, M, O in zip(second, Ms, Os):
-        for v, (a, r) in enumerate(views):
-            Oo, Mo, _ = oracle.detect_view(f_np, a, r)
-            np.testing.assert_array_equal(O[v].cpu().numpy(), Oo)
-            np.testing.assert_array_equal(M[v].cpu().numpy(), Mo)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            occ.occ_detect_batched(ctx, Ds, views, Ms=Ms, Os=Os)
+        # Two replays on different inputs: the second must not take the first one's lines.
+        for inputs in (second, first):
+            for f_np, D in zip(inputs, Ds):
+                D.copy_(torch.from_numpy(f_np).cuda())
+            g.replay()
+            torch.cuda.synchronize()
+            assert occ.occ_get_status(ctx) == occ.OCC_OK
+            for f_np, M, O in zip(inputs, Ms, Os):
+                for v, (a, r) in enumerate(views):
+                    Oo, Mo, _ = oracle.detect_view(f_np, a, r)
+                    np.testing.assert_array_equal(O[v].cpu().numpy(), Oo)
+                    np.testing.assert_array_equal(M[v].cpu().numpy(), Mo)
+    finally:
+        occ.occ_set_tuning(ctx, None)
 
 
 def test_fused_launch_wait_bound_and_recovery(ctx):
@@ -146,7 +155,7 @@ def test_fused_launch_wait_bound_and_recovery(ctx):
     2 ms, every strip's wait gives up, the call reports OCC_ERR_TIMEOUT and the launch ends; the next call, with the
     hook off, is exact again on the same context."""
     D = scenes.make_scene(scenes.spec_array(97, 301), scenes.seed_of(93, 0))
-    occ.occ_set_tuning(ctx, tuning(4096))
+    occ.occ_set_tuning(ctx, tuning(4096, fused=1))
     try:
         occ.occ_set_wait_limit(ctx, 2000, hold=True)
         occ.occ_detect(ctx, torch.from_numpy(D).cuda(), OCTANT)
@@ -154,7 +163,7 @@ def test_fused_launch_wait_bound_and_recovery(ctx):
     finally:
         occ.occ_set_wait_limit(ctx, 0, hold=False)
         occ.occ_set_tuning(ctx, None)
-    M, O, st = detect(ctx, D, OCTANT, occ.STRIP_PX_DEFAULT)
+    M, O, st = detect(ctx, D, OCTANT, occ.STRIP_PX_DEFAULT, fused=1)
     check_oracle(D, OCTANT, M, O, st)
     with pytest.raises(occ.OccError):
         occ.occ_set_wait_limit(ctx, -1)
@@ -170,9 +179,13 @@ def test_fused_batches_of_many_frames(ctx, n_frames):
     Ds = [torch.from_numpy(f).cuda() for f in frames]
     Ms = [torch.empty((len(OCTANT), *D.shape), dtype=torch.uint8, device="cuda") for D in Ds]
     Os = [torch.empty((len(OCTANT), *D.shape), dtype=torch.int32, device="cuda") for D in Ds]
-    occ.occ_detect_batched(ctx, Ds, OCTANT, Ms=Ms, Os=Os)
-    torch.cuda.synchronize()
-    assert occ.occ_get_status(ctx) == occ.OCC_OK
+    occ.occ_set_tuning(ctx, tuning(occ.STRIP_PX_DEFAULT, fused=1))
+    try:
+        occ.occ_detect_batched(ctx, Ds, OCTANT, Ms=Ms, Os=Os)
+        torch.cuda.synchronize()
+        assert occ.occ_get_status(ctx) == occ.OCC_OK
+    finally:
+        occ.occ_set_tuning(ctx, None)
     for f_np, M, O in zip(frames, Ms, Os):
         for v, (a, r) in enumerate(OCTANT):
             Oo, Mo, _ = oracle.detect_view(f_np, a, r)
