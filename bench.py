@@ -73,6 +73,8 @@ def parse():
                          "ncu -k)")
     ap.add_argument("--strip-px", type=int, default=None,
                     help="with --probe detect: occ_tuning.strip_px of the calls (0: list kernels only)")
+    ap.add_argument("--fused", type=int, choices=[0, 1], default=None,
+                    help="with --probe detect: occ_tuning.fused of the calls (1: one fused launch per call)")
     return ap.parse_args()
 
 
@@ -192,7 +194,7 @@ def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -
 # code it was taken on (sha256 prefix of csrc/occ_kernels.cu + csrc/occ_strip.cu without comments and blank space);
 # reported as null otherwise.
 PROFILED_STEPS = 20   # occ_detect calls with per-stage events after the timed region (stage_ms)
-MEASURED_TRAFFIC = {"scan": {"bytes": 62190464, "kernels_sha": "2f0039b2af74c896"}}
+MEASURED_TRAFFIC = {"scan": {"bytes": 56901120, "kernels_sha": "8a38d13aea906c69"}}
 
 
 def code_sha(src: str) -> str:
@@ -295,6 +297,32 @@ def run_ours(args):
     status = occ.occ_get_status(ctx, stream)
     if status != occ.OCC_OK:
         raise RuntimeError(f"detect failed: {occ.occ_status_string(status)}")
+
+    # The same step as one fused launch (tuning.fused = 1; every view of the workload takes the strip kernel), timed
+    # the same way, for comparison with the separate launches above.
+    fused = None
+    if all(strip_views(views, tuning, 8, max(H, W))):
+        occ.occ_set_tuning(ctx, {**tuning, "fused": 1})
+        nf_steps = max(3, min(args.steps, 100))
+        for i in range(args.warmup):
+            step(i)
+        fs = [torch.cuda.Event(enable_timing=True) for _ in range(nf_steps)]
+        fe = [torch.cuda.Event(enable_timing=True) for _ in range(nf_steps)]
+        torch.cuda.synchronize()
+        for i in range(nf_steps):
+            flush.zero_()
+            fs[i].record(stream)
+            step(i)
+            fe[i].record(stream)
+        torch.cuda.synchronize()
+        if occ.occ_get_status(ctx, stream) != occ.OCC_OK:
+            raise RuntimeError("fused detect failed")
+        occ.occ_set_tuning(ctx, tuning)
+        f_ms = sum(a.elapsed_time(b) for a, b in zip(fs, fe)) / nf_steps
+        f_ms = shard.max_over_ranks(f_ms / 1e3, dev) * 1e3
+        fused = {"value": round(world * units_per_step / (f_ms / 1e3) / 1e6, 1), "unit": UNIT,
+                 "ms_per_step": round(f_ms, 4), "steps": nf_steps, "launches_per_step": 1,
+                 "tuning": {**tuning, "fused": 1}}
     # Stage times come from a separate pass with the library's per-stage events switched on (they add events on both
     # streams and a host read-back per call, which the timed steps above do without).
     occ.occ_set_profiling(ctx, True)
@@ -423,6 +451,7 @@ def run_ours(args):
             "clocks": clk,
             "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
             "stage_ms_source": f"{PROFILED_STEPS} calls with per-stage events, after the timed steps",
+            "fused_launch": fused,
             "batched": batched,
             "stress": stress,
             "fusion_and_warp": fusion,
@@ -484,10 +513,32 @@ def run_batched(args, dev, views, rank, world):
     t = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
     if occ.occ_get_status(ctx) != occ.OCC_OK:
         raise RuntimeError("batched detect failed")
+    # The same batch as one fused launch (tuning.fused = 1), its own graph.
+    fused = None
+    if all(strip_views(views, tuning, 8, max(max(D.shape) for D in Ds))):
+        occ.occ_set_tuning(ctx, {**tuning, "fused": 1})
+        occ.occ_detect_batched(ctx, Ds, views, p, Ms=Ms, Os=Os)
+        gf = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gf):
+            occ.occ_detect_batched(ctx, Ds, views, p, Ms=Ms, Os=Os)
+        for _ in range(3):
+            gf.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(steps):
+            gf.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        tf = shard.max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+        if occ.occ_get_status(ctx) != occ.OCC_OK:
+            raise RuntimeError("fused batched detect failed")
+        occ.occ_set_tuning(ctx, tuning)
+        fused = {"value": round(steps * world * px * V / tf / 1e6, 1), "unit": UNIT,
+                 "ms_per_step": round(tf / steps * 1e3, 3), "launches_per_batch": 1, "tuning": {**tuning, "fused": 1}}
     ctx.close()
     return {"value": round(steps * world * px * V / t / 1e6, 1), "unit": UNIT, "ms_per_step": round(t / steps * 1e3, 3),
             "frames": len(Ds), "pixels_per_frame_set": px, "views": V, "steps": steps, "cuda_graph": True,
-            "tuning": tuning, "l2": "inputs and outputs larger than L2", "clocks": clk}
+            "tuning": tuning, "l2": "inputs and outputs larger than L2", "clocks": clk, "fused_launch": fused}
 
 
 def run_stress(args, dev, rank, world):
@@ -881,10 +932,12 @@ def run_probe(args):
         H, W = f.shape
         D = torch.from_numpy(f).cuda()
         with occ.occ_create(0, max_pixels=H * W, max_views=8) as ctx:
+            t = occ.occ_get_tuning(ctx)[0]
             if args.strip_px is not None:
-                t = occ.occ_get_tuning(ctx)[0]
                 t["strip_px"] = args.strip_px
-                occ.occ_set_tuning(ctx, t)
+            if args.fused is not None:
+                t["fused"] = args.fused
+            occ.occ_set_tuning(ctx, t)
             for _ in range(3):
                 occ.occ_detect(ctx, D, views)
             if occ.occ_get_status(ctx) != occ.OCC_OK:
