@@ -15,7 +15,7 @@ torch.distributed.run (127.0.0.1, N processes); every rank runs its own frames (
 and the slowest rank's time is reported.  Rank 0 prints one JSON line.  --dry-run goes through the same launch and
 reduction over a gloo group without touching a GPU (each rank times a fixed host-side wait).
 
-  python bench.py --probe fusion|proposer     # a few launches of the kernels beside the detection, for ncu -k ...
+  python bench.py --probe fusion|proposer|detect|stress   # a few launches of chosen kernels, for ncu -k ...
 """
 from __future__ import annotations
 
@@ -66,10 +66,11 @@ def parse():
                     help="mixed-size frames (640x480 .. 4096x2160) the learned proposer is measured on")
     ap.add_argument("--dry-run", action="store_true",
                     help="launch and reduce over ranks (gloo) without a GPU; prints the JSON line of that run")
-    ap.add_argument("--probe", choices=["fusion", "proposer", "detect"], default=None,
+    ap.add_argument("--probe", choices=["fusion", "proposer", "detect", "stress"], default=None,
                     help="run a few launches of the median fusion and backward warp (fusion), of the learned "
-                         "proposer's forward and training step (proposer), or three occ_detect calls on the "
-                         "1920x1080 3x3-array frame (detect) on bench-sized inputs, then exit (for profiling with "
+                         "proposer's forward and training step (proposer), three occ_detect calls on the "
+                         "1920x1080 3x3-array frame (detect), or four on the stress map at 1024x540 (stress) on "
+                         "bench-sized inputs, then exit (for profiling with "
                          "ncu -k)")
     ap.add_argument("--strip-px", type=int, default=None,
                     help="with --probe detect: occ_tuning.strip_px of the calls (0: list kernels only)")
@@ -940,6 +941,20 @@ def run_probe(args):
             occ.occ_set_tuning(ctx, t)
             for _ in range(3):
                 occ.occ_detect(ctx, D, views)
+            if occ.occ_get_status(ctx) != occ.OCC_OK:
+                raise RuntimeError("detect failed")
+    elif args.probe == "stress":
+        # The stress map at a quarter of its size in each direction (1024x540, 24 views), list kernels only (the
+        # autotuner's pick there), four calls.
+        wl = scenes.stress_5x5(H=540, W=1024)
+        D = torch.from_numpy(wl.frames[0]).cuda()
+        with occ.occ_create(0, max_pixels=540 * 1024, max_views=len(wl.views)) as ctx:
+            t = occ.occ_get_tuning(ctx)[0]
+            t["strip_px"] = 0
+            t["line_max_runs"] = 0
+            occ.occ_set_tuning(ctx, t)
+            for _ in range(4):
+                occ.occ_detect(ctx, D, wl.views)
             if occ.occ_get_status(ctx) != occ.OCC_OK:
                 raise RuntimeError("detect failed")
     elif args.probe == "fusion":

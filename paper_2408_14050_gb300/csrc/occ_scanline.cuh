@@ -26,13 +26,16 @@ namespace {
 
 constexpr int kMaxRuns = 16;
 
+// A warp's shared memory for one line: V by sample, the sorted order as sample indices, and 16 bits of counts per
+// sorted position (W is not stored: W = fl(g - V) is recomputed from the sample's index wherever it is compared, the
+// same operation that defines it), 8 bytes per sample.
 template <int CAP>
 struct ScanSmem {
-    float uw[CAP];      // W by k; after the sort, hit counters
-    float uv[CAP];      // V by k; after the sort, hit counters
-    float sw[CAP];      // sorted W (hit counters when the line is one run; bucket counts during the bucket sort)
-    float sv[CAP];      // sorted V (hit counters when the line is one run)
-    uint16_t sidx[CAP]; // sample index (k - k0) of each sorted position
+    float uv[CAP];        // V by k
+    uint16_t sidx[CAP];   // sample index (k - k0) of each sorted position (unused when the line is one run)
+    uint32_t cnt[CAP / 2];// per sorted position q, 16 bits at (q & 1) * 16 of word q / 2: hits of the sample itself
+                          // (low byte, <= N/2) and from below it (high byte, <= N/2); during the bucket sort, 16-bit
+                          // bucket counts and offsets (at most CAP)
     int32_t runs[kMaxRuns + 2];
     float run_lo[kMaxRuns + 1];   // first (smallest) W of each run
     float run_hi[kMaxRuns + 1];   // last (largest) W of each run
@@ -40,20 +43,22 @@ struct ScanSmem {
     float hi_before[kMaxRuns + 2];// max of run_hi over the runs before run b
 };
 
-// First index in [lo, hi) whose value is > x (upper) or >= x (lower); a[lo..hi) is non-decreasing.
-__device__ __forceinline__ int upper_bound_f(const float* a, int lo, int hi, float x)
+// First index in [lo, hi) whose W is > x (upper) or >= x (lower); W(lo..hi-1) is non-decreasing.
+template <class WF>
+__device__ __forceinline__ int upper_bound_w(const WF& Wat, int lo, int hi, float x)
 {
     while (lo < hi) {
         const int m = (lo + hi) >> 1;
-        if (a[m] <= x) lo = m + 1; else hi = m;
+        if (Wat(m) <= x) lo = m + 1; else hi = m;
     }
     return lo;
 }
-__device__ __forceinline__ int lower_bound_f(const float* a, int lo, int hi, float x)
+template <class WF>
+__device__ __forceinline__ int lower_bound_w(const WF& Wat, int lo, int hi, float x)
 {
     while (lo < hi) {
         const int m = (lo + hi) >> 1;
-        if (a[m] < x) lo = m + 1; else hi = m;
+        if (Wat(m) < x) lo = m + 1; else hi = m;
     }
     return lo;
 }
@@ -63,7 +68,7 @@ __device__ __forceinline__ int lower_bound_f(const float* a, int lo, int hi, flo
 // emit(k, o) is called once for every sample k (0 .. 2h) with o > 0 hits, by the lane that holds it; the caller adds
 // o to O at the sample's pixel (Eq. 6).  Returns the number of samples inside the map, 0 for none, and -1 when they
 // do not form one interval of k (a self-check; positions are monotone in g).  Uses the warp's ScanSmem; lines of at
-// most CAP samples (2h + 1 <= CAP).
+// most CAP samples (2h + 1 <= CAP), N <= 64.
 template <int CAP, class Emit>
 __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float* D, int64_t pitch, int Wd, int Hd,
                                          float c, float s, float r, float fcx, float fcy, int h, int half, float beta,
@@ -75,7 +80,7 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
     const int nk = 2 * h + 1;
     const float fW = (float)Wd, fH = (float)Hd;
 
-    // Eq. 4: positions, bounds, V = D_r at the nearest pixel, W = g - V.
+    // Eq. 4: positions, bounds, V = D_r at the nearest pixel.
     int k0 = -1, kl = -1, n = 0;
     auto record = [&](int base, bool ok) {
         const unsigned b = __ballot_sync(kFull, ok);
@@ -108,11 +113,7 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
             const int base = i * 32;
             if (base >= nk) break;
             const int k = base + lane;
-            if (oks[i]) {
-                const float V = one ? dvs[i] : __fmul_rn(r, dvs[i]);
-                S.uw[k] = __fsub_rn((float)(k - h), V);
-                S.uv[k] = V;
-            }
+            if (oks[i]) S.uv[k] = one ? dvs[i] : __fmul_rn(r, dvs[i]);
             record(base, oks[i]);
         }
     } else {
@@ -126,9 +127,7 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
                 ok = (rx >= 0.0f) && (rx < fW) && (ry >= 0.0f) && (ry < fH);
                 if (ok) {
                     const float dv = __ldg(D + (int64_t)(int)ry * pitch + (int)rx);
-                    const float V = one ? dv : __fmul_rn(r, dv);
-                    S.uw[k] = __fsub_rn(g, V);
-                    S.uv[k] = V;
+                    S.uv[k] = one ? dv : __fmul_rn(r, dv);
                 }
             }
             record(base, ok);
@@ -140,14 +139,15 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
         return n == 0 ? 0 : -1;
     }
     __syncwarp();
-    const float* uw = S.uw + k0;
     const float* uv = S.uv + k0;
+    // W of sample i (k = k0 + i): fl(g - V), g = k - h.
+    auto Wat = [&](int i) { return __fsub_rn((float)(k0 + i - h), uv[i]); };
 
     // Runs: a new run starts after every descent W[i+1] < W[i].
     int R = 1;
     for (int base = 0; base < n - 1; base += 32) {
         const int i = base + lane;
-        const bool dsc = (i < n - 1) && (uw[i + 1] < uw[i]);
+        const bool dsc = (i < n - 1) && (Wat(i + 1) < Wat(i));
         const unsigned b = __ballot_sync(kFull, dsc);
         if (dsc) {
             const int slot = R + __popc(b & lt);
@@ -156,171 +156,168 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
         R += __popc(b);
     }
 
-    const float* sw;
-    const float* sv;
-    int* cnt_own;
-    int* cnt_up;
-    if (R == 1) {
-        sw = uw; sv = uv;
-        cnt_own = reinterpret_cast<int*>(S.sv);
-        cnt_up = reinterpret_cast<int*>(S.sw);
-    } else {
-        sw = S.sw; sv = S.sv;
-        cnt_own = reinterpret_cast<int*>(S.uv);
-        cnt_up = reinterpret_cast<int*>(S.uw);
-        if (R <= kMaxRuns) {
-            if (lane == 0) {
-                S.runs[0] = 0;
-                S.runs[R] = n;
+    if (R > 1 && R <= kMaxRuns) {
+        if (lane == 0) {
+            S.runs[0] = 0;
+            S.runs[R] = n;
+        }
+        __syncwarp();
+        if (lane < R) {
+            S.run_lo[lane] = Wat(S.runs[lane]);
+            S.run_hi[lane] = Wat(S.runs[lane + 1] - 1);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            float m = INFINITY;
+            S.lo_after[R] = m;
+            for (int b = R - 1; b >= 0; b--) {
+                S.lo_after[b] = m;            // min run_lo over runs b+1 .. R-1
+                m = fminf(m, S.run_lo[b]);
             }
-            __syncwarp();
-            if (lane < R) {
-                S.run_lo[lane] = uw[S.runs[lane]];
-                S.run_hi[lane] = uw[S.runs[lane + 1] - 1];
+            float x = -INFINITY;
+            for (int b = 0; b < R; b++) {
+                S.hi_before[b] = x;           // max run_hi over runs 0 .. b-1
+                x = fmaxf(x, S.run_hi[b]);
             }
-            __syncwarp();
-            if (lane == 0) {
-                float m = INFINITY;
-                S.lo_after[R] = m;
-                for (int b = R - 1; b >= 0; b--) {
-                    S.lo_after[b] = m;            // min run_lo over runs b+1 .. R-1
-                    m = fminf(m, S.run_lo[b]);
+        }
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const float wi = Wat(i);
+            int ra = 0;
+            while (ra + 1 < R && S.runs[ra + 1] <= i) ra++;
+            int rank = i;
+            if (S.lo_after[ra] < wi) {        // some later run has smaller W
+                for (int b = ra + 1; b < R; b++) {
+                    if (S.run_lo[b] >= wi) continue;
+                    const int st = S.runs[b], en = S.runs[b + 1];
+                    rank += (S.run_hi[b] < wi) ? en - st : lower_bound_w(Wat, st, en, wi) - st;
                 }
-                float x = -INFINITY;
-                for (int b = 0; b < R; b++) {
-                    S.hi_before[b] = x;           // max run_hi over runs 0 .. b-1
-                    x = fmaxf(x, S.run_hi[b]);
+            }
+            if (S.hi_before[ra] > wi) {       // some earlier run has larger W
+                for (int b = 0; b < ra; b++) {
+                    if (S.run_hi[b] <= wi) continue;
+                    const int st = S.runs[b], en = S.runs[b + 1];
+                    rank -= (S.run_lo[b] > wi) ? en - st : en - upper_bound_w(Wat, st, en, wi);
                 }
             }
-            __syncwarp();
-            for (int i = lane; i < n; i += 32) {
-                const float wi = uw[i];
-                int ra = 0;
-                while (ra + 1 < R && S.runs[ra + 1] <= i) ra++;
-                int rank = i;
-                if (S.lo_after[ra] < wi) {        // some later run has smaller W
-                    for (int b = ra + 1; b < R; b++) {
-                        if (S.run_lo[b] >= wi) continue;
-                        const int st = S.runs[b], en = S.runs[b + 1];
-                        rank += (S.run_hi[b] < wi) ? en - st : lower_bound_f(uw, st, en, wi) - st;
+            S.sidx[rank] = (uint16_t)i;
+        }
+    } else if (R > kMaxRuns) {
+        // Many runs: a counting sort by the bucket (int)(fl(W - W_min) * scale) -- a non-decreasing function of W,
+        // so it orders the samples of different buckets -- then odd-even transposition passes by (W, index) until
+        // none swaps, which orders the samples within a bucket.  Buckets are about one W unit wide, at most CAP of
+        // them, so most hold a sample or two; their counts and offsets are 16-bit halves of the count words.
+        float wlo = INFINITY, whi = -INFINITY;
+        for (int i = lane; i < n; i += 32) {
+            const float w = Wat(i);
+            wlo = fminf(wlo, w);
+            whi = fmaxf(whi, w);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wlo = fminf(wlo, __shfl_xor_sync(kFull, wlo, o));
+            whi = fmaxf(whi, __shfl_xor_sync(kFull, whi, o));
+        }
+        const float span = __fsub_rn(whi, wlo);
+        int B = CAP;
+        float scale = 1.0f;
+        if (span < (float)(CAP - 1)) B = (int)span + 1;
+        else scale = (float)(CAP - 1) / span;
+        auto bucket = [&](float w) { return min((int)(__fsub_rn(w, wlo) * scale), B - 1); };
+        for (int b = lane; b < (B + 1) / 2; b += 32) S.cnt[b] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int b = bucket(Wat(i));
+            atomicAdd(&S.cnt[b >> 1], 1u << ((b & 1) * 16));
+        }
+        __syncwarp();
+        // Exclusive prefix sums of the counts, 32 buckets (16 words) at a time.
+        uint32_t carry = 0;
+        for (int b0 = 0; b0 < B; b0 += 32) {
+            const int b = b0 + lane;
+            const uint32_t cb = b < B ? (S.cnt[b >> 1] >> ((b & 1) * 16)) & 0xFFFFu : 0u;
+            uint32_t incl = cb;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t ex = carry + incl - cb;
+            const uint32_t ex_next = __shfl_down_sync(kFull, ex, 1);
+            __syncwarp();   // every lane has read its count before its pair's word is rewritten
+            if (!(lane & 1) && b < B) S.cnt[b >> 1] = ex | (ex_next << 16);
+            carry += __shfl_sync(kFull, incl, 31);
+        }
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+            const int b = bucket(Wat(i));
+            const int sh = (b & 1) * 16;
+            const uint32_t old = atomicAdd(&S.cnt[b >> 1], 1u << sh);
+            S.sidx[(old >> sh) & 0xFFFFu] = (uint16_t)i;
+        }
+        __syncwarp();
+        for (;;) {
+            bool swapped = false;
+#pragma unroll
+            for (int par = 0; par < 2; par++) {
+                for (int i = 2 * lane + par; i + 1 < n; i += 64) {
+                    const int ia = S.sidx[i], ib = S.sidx[i + 1];
+                    const float wa = Wat(ia), wb = Wat(ib);
+                    if (wa > wb || (wa == wb && ia > ib)) {
+                        S.sidx[i] = (uint16_t)ib;
+                        S.sidx[i + 1] = (uint16_t)ia;
+                        swapped = true;
                     }
                 }
-                if (S.hi_before[ra] > wi) {       // some earlier run has larger W
-                    for (int b = 0; b < ra; b++) {
-                        if (S.run_hi[b] <= wi) continue;
-                        const int st = S.runs[b], en = S.runs[b + 1];
-                        rank -= (S.run_lo[b] > wi) ? en - st : en - upper_bound_f(uw, st, en, wi);
-                    }
-                }
-                S.sw[rank] = wi;
-                S.sv[rank] = uv[i];
-                S.sidx[rank] = (uint16_t)i;
+                __syncwarp();
             }
-        } else {
-            // Many runs: a counting sort by the bucket (int)(fl(W - W_min) * scale) -- a non-decreasing function of W,
-            // so it orders the samples of different buckets -- then odd-even transposition passes by (W, index)
-            // until none swaps, which orders the samples within a bucket.  Buckets are about one W unit wide, at
-            // most CAP of them, so most hold a sample or two.
-            float wlo = INFINITY, whi = -INFINITY;
-            for (int i = lane; i < n; i += 32) {
-                wlo = fminf(wlo, uw[i]);
-                whi = fmaxf(whi, uw[i]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                wlo = fminf(wlo, __shfl_xor_sync(kFull, wlo, o));
-                whi = fmaxf(whi, __shfl_xor_sync(kFull, whi, o));
-            }
-            const float span = __fsub_rn(whi, wlo);
-            int B = CAP;
-            float scale = 1.0f;
-            if (span < (float)(CAP - 1)) B = (int)span + 1;
-            else scale = (float)(CAP - 1) / span;
-            auto bucket = [&](float w) { return min((int)(__fsub_rn(w, wlo) * scale), B - 1); };
-            int* cnt = reinterpret_cast<int*>(S.sw);
-            for (int b = lane; b < B; b += 32) cnt[b] = 0;
-            __syncwarp();
-            for (int i = lane; i < n; i += 32) atomicAdd(&cnt[bucket(uw[i])], 1);
-            __syncwarp();
-            // Exclusive prefix sums of the counts, 32 buckets at a time.
-            int carry = 0;
-            for (int b0 = 0; b0 < B; b0 += 32) {
-                const int b = b0 + lane;
-                const int c = b < B ? cnt[b] : 0;
-                int incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (b < B) cnt[b] = carry + incl - c;
-                carry += __shfl_sync(kFull, incl, 31);
-            }
-            __syncwarp();
-            for (int i = lane; i < n; i += 32) S.sidx[atomicAdd(&cnt[bucket(uw[i])], 1)] = (uint16_t)i;
-            __syncwarp();
-            for (;;) {
-                bool swapped = false;
-#pragma unroll
-                for (int par = 0; par < 2; par++) {
-                    for (int i = 2 * lane + par; i + 1 < n; i += 64) {
-                        const int ia = S.sidx[i], ib = S.sidx[i + 1];
-                        const float wa = uw[ia], wb = uw[ib];
-                        if (wa > wb || (wa == wb && ia > ib)) {
-                            S.sidx[i] = (uint16_t)ib;
-                            S.sidx[i + 1] = (uint16_t)ia;
-                            swapped = true;
-                        }
-                    }
-                    __syncwarp();
-                }
-                if (!__any_sync(kFull, swapped)) break;
-            }
-            for (int q = lane; q < n; q += 32) {
-                const int idx = S.sidx[q];
-                S.sw[q] = uw[idx];
-                S.sv[q] = uv[idx];
-            }
+            if (!__any_sync(kFull, swapped)) break;
         }
     }
     __syncwarp();
 
-    // Eq. 5, every pair once from its lower sorted end.
-    for (int q = lane; q < n; q += 32) cnt_up[q] = 0;
+    // Eq. 5, every pair once from its lower sorted end; the counts of sorted position q in its 16-bit half word.
+    const bool sorted = R == 1;
+    auto at = [&](int q) { return sorted ? q : (int)S.sidx[q]; };
+    for (int w = lane; w < (n + 1) / 2; w += 32) S.cnt[w] = 0u;
     __syncwarp();
     for (int q = lane; q < n; q += 32) {
-        const float wq = sw[q];
-        const float vq = sv[q];
+        const int iq = at(q);
+        const float wq = Wat(iq);
+        const float vq = uv[iq];
         const float vbq = __fadd_rn(vq, beta);
         int o = 0;
         if (half <= 4) {
 #pragma unroll
             for (int d = 1; d <= 4; d++) {
                 if (d <= half && q + d < n) {
-                    const float wd = sw[q + d];
-                    const float vd = sv[q + d];
+                    const int id = at(q + d);
+                    const float wd = Wat(id);
+                    const float vd = uv[id];
                     const bool close = fabsf(__fsub_rn(wq, wd)) < zeta;
                     o += (close && vbq < vd) ? 1 : 0;
-                    if (close && __fadd_rn(vd, beta) < vq) atomicAdd(&cnt_up[q + d], 1);
+                    if (close && __fadd_rn(vd, beta) < vq)
+                        atomicAdd(&S.cnt[(q + d) >> 1], 1u << (((q + d) & 1) * 16 + 8));
                 }
             }
         } else {
             for (int d = 1; d <= half && q + d < n; d++) {
-                const float wd = sw[q + d];
+                const int id = at(q + d);
+                const float wd = Wat(id);
                 if (!(fabsf(__fsub_rn(wq, wd)) < zeta)) break;
-                const float vd = sv[q + d];
+                const float vd = uv[id];
                 o += (vbq < vd) ? 1 : 0;
-                if (__fadd_rn(vd, beta) < vq) atomicAdd(&cnt_up[q + d], 1);
+                if (__fadd_rn(vd, beta) < vq) atomicAdd(&S.cnt[(q + d) >> 1], 1u << (((q + d) & 1) * 16 + 8));
             }
         }
-        cnt_own[q] = o;
+        if (o) atomicAdd(&S.cnt[q >> 1], (uint32_t)o << ((q & 1) * 16));
     }
-    __syncwarp();
     __syncwarp();
     // Eq. 6 is the caller's: every sample's count, with its k.
     for (int q = lane; q < n; q += 32) {
-        const int o = cnt_own[q] + cnt_up[q];
-        if (o) emit(k0 + (R == 1 ? q : (int)S.sidx[q]), o);
+        const uint32_t w = S.cnt[q >> 1] >> ((q & 1) * 16);
+        const int o = (int)(w & 0xFFu) + (int)((w >> 8) & 0xFFu);
+        if (o) emit(k0 + at(q), o);
     }
     return n;
 }
