@@ -276,9 +276,62 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
     }
     __syncwarp();
 
-    // Eq. 5, every pair once from its lower sorted end; the counts of sorted position q in its 16-bit half word.
+    // Eq. 5.  Sorted positions (q, q + d), d <= N/2, are the pairs tested; |fl(W_q - W_{q+d})| is symmetric.
     const bool sorted = R == 1;
     auto at = [&](int q) { return sorted ? q : (int)S.sidx[q]; };
+    if (half <= 4) {
+        // N <= 8: chunks of 32 sorted positions, one per lane, each lane counting the hits of its own position from
+        // both sides (q hit by q + d when V_q + beta < V_{q+d}, and by q - d when V_q + beta < V_{q-d}) with the
+        // neighbours' W and V from the lanes d away, or from the previous or next chunk at the chunk's ends: every
+        // pair is tested from both of its ends, with no shared counters.  W = +inf past either end (never close).
+        const float kInf = __int_as_float(0x7f800000);
+        auto load = [&](int q, int& i, float& w, float& v) {
+            if (q < n) {
+                i = at(q);
+                v = uv[i];
+                w = Wat(i);
+            } else {
+                i = 0;
+                v = 0.0f;
+                w = kInf;
+            }
+        };
+        int ci;
+        float cw, cv, pw = kInf, pv = 0.0f;
+        load(lane, ci, cw, cv);
+        for (int base = 0; base < n; base += 32) {
+            int ni;
+            float nw, nv;
+            load(base + 32 + lane, ni, nw, nv);
+            const float vbq = __fadd_rn(cv, beta);
+            int o = 0;
+#pragma unroll
+            for (int d = 1; d <= 4; d++) {
+                const int up = (lane + d) & 31, dn = (lane - d) & 31;
+                const float aw_c = __shfl_sync(kFull, cw, up), av_c = __shfl_sync(kFull, cv, up);
+                const float aw_n = __shfl_sync(kFull, nw, up), av_n = __shfl_sync(kFull, nv, up);
+                const float bw_c = __shfl_sync(kFull, cw, dn), bv_c = __shfl_sync(kFull, cv, dn);
+                const float bw_p = __shfl_sync(kFull, pw, dn), bv_p = __shfl_sync(kFull, pv, dn);
+                if (d <= half) {
+                    const bool wrap_up = lane + d >= 32, wrap_dn = lane < d;
+                    const float aw = wrap_up ? aw_n : aw_c, av = wrap_up ? av_n : av_c;
+                    const float bw = wrap_dn ? bw_p : bw_c, bv = wrap_dn ? bv_p : bv_c;
+                    o += (fabsf(__fsub_rn(cw, aw)) < zeta && vbq < av) ? 1 : 0;
+                    o += (fabsf(__fsub_rn(bw, cw)) < zeta && vbq < bv) ? 1 : 0;
+                }
+            }
+            // Eq. 6 is the caller's: every sample's count, with its k.
+            if (base + lane < n && o) emit(k0 + ci, o);
+            pw = cw;
+            pv = cv;
+            ci = ni;
+            cw = nw;
+            cv = nv;
+        }
+        return n;
+    }
+    // N > 8: every pair once from its lower sorted end, up to the first that is not close; the counts of sorted
+    // position q in its 16-bit half word.
     for (int w = lane; w < (n + 1) / 2; w += 32) S.cnt[w] = 0u;
     __syncwarp();
     for (int q = lane; q < n; q += 32) {
@@ -287,28 +340,13 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
         const float vq = uv[iq];
         const float vbq = __fadd_rn(vq, beta);
         int o = 0;
-        if (half <= 4) {
-#pragma unroll
-            for (int d = 1; d <= 4; d++) {
-                if (d <= half && q + d < n) {
-                    const int id = at(q + d);
-                    const float wd = Wat(id);
-                    const float vd = uv[id];
-                    const bool close = fabsf(__fsub_rn(wq, wd)) < zeta;
-                    o += (close && vbq < vd) ? 1 : 0;
-                    if (close && __fadd_rn(vd, beta) < vq)
-                        atomicAdd(&S.cnt[(q + d) >> 1], 1u << (((q + d) & 1) * 16 + 8));
-                }
-            }
-        } else {
-            for (int d = 1; d <= half && q + d < n; d++) {
-                const int id = at(q + d);
-                const float wd = Wat(id);
-                if (!(fabsf(__fsub_rn(wq, wd)) < zeta)) break;
-                const float vd = uv[id];
-                o += (vbq < vd) ? 1 : 0;
-                if (__fadd_rn(vd, beta) < vq) atomicAdd(&S.cnt[(q + d) >> 1], 1u << (((q + d) & 1) * 16 + 8));
-            }
+        for (int d = 1; d <= half && q + d < n; d++) {
+            const int id = at(q + d);
+            const float wd = Wat(id);
+            if (!(fabsf(__fsub_rn(wq, wd)) < zeta)) break;
+            const float vd = uv[id];
+            o += (vbq < vd) ? 1 : 0;
+            if (__fadd_rn(vd, beta) < vq) atomicAdd(&S.cnt[(q + d) >> 1], 1u << (((q + d) & 1) * 16 + 8));
         }
         if (o) atomicAdd(&S.cnt[q >> 1], (uint32_t)o << ((q & 1) * 16));
     }
