@@ -39,7 +39,9 @@ def workload_key(device_name: str, shapes, views, L: int, N: int) -> str:
     return f"{device_name}|{size_class(shapes)}|{scan_bucket(L)}|{angle_class(views)}|N{N}"
 
 
-STRIP_SHAPES = (2048, 3072, 4096, 6144)   # pixels per strip of the strip kernel
+# Pixels per strip of the strip kernel.  4352 holds two 2160-pixel columns or diagonals (4096x2160 frames) at five
+# blocks per multiprocessor.
+STRIP_SHAPES = (2048, 3072, 4096, 4352, 6144)
 
 
 def candidates(max_line_bps: int):
