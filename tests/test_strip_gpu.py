@@ -197,7 +197,7 @@ def test_fused_option_falls_back_without_room():
     """A context too small for the fused launch's work lists (its warp buffers) takes the separate launches with
     fused = 1, with the same results."""
     D = scenes.make_scene(scenes.spec_array(64, 96), scenes.seed_of(95, 0))
-    c = occ.occ_create(0, max_pixels=64 * 96, max_views=8, max_candidates=256)
+    c = occ.occ_create(0, max_pixels=64 * 96, max_views=8, max_candidates=4096)
     try:
         M, O, st = detect(c, D, OCTANT, occ.STRIP_PX_DEFAULT, fused=1)
         check_oracle(D, OCTANT, M, O, st)
