@@ -168,30 +168,30 @@ def fused_call(views, tuning: dict, N: int = 8, max_side: int = 1920) -> bool:
 
 
 def launches_per_detect(views, tuning: dict, N: int = 8, max_side: int = 1920) -> int:
-    """Kernels one occ_detect queues (no E, A or tile outputs).  Views whose scan lines stay on a row, column or
-    diagonal (alpha a multiple of 45 degrees) take the strip kernel when N = 8 and the tuning enables it.  All views
-    on strips: one fused launch, or (fused off) frame table, min/max with the position tables, plan, strips, prefix
-    sums of the listed long lines, the three warp scan classes.  Otherwise: frame table, position tables (when some
-    kernel uses them), edges and candidates, plan, the strips and their prefix sums (if any view takes them), the
-    line-per-thread scan and its merge (when line_max_runs > 0), the three warp scan classes, the mask."""
+    """Kernels one occ_detect queues (one frame, no E, A or tile outputs).  Views whose scan lines stay on a row,
+    column or diagonal (alpha a multiple of 45 degrees) take the strip kernel when N = 8 and the tuning enables it.
+    All views on strips: one fused launch, or (fused off) min/max with the frame table and the plan, the strips
+    (whose last block writes the listed long lines' prefix sums), the three warp scan classes.  Otherwise: frame
+    table, position tables (when the line kernels run), edges and candidates, plan, the strips (if any view takes
+    them), the line-per-thread scan and its merge (when line_max_runs > 0), the three warp scan classes, the mask."""
     strip = strip_views(views, tuning, N, max_side)
     lines = tuning.get("line_max_runs", 2) > 0 and N <= 8
     if fused_call(views, tuning, N, max_side):
         return 1
     if all(strip):
-        return 8
+        return 5
     n = 1 + 1 + 1 + 3 + 1          # frames, edges, plan, three warp classes, mask
     if any(strip):
-        n += 2
+        n += 1
     if lines:
         n += 2
-    if lines or any(strip):
+    if lines:
         n += 1                     # tables
     return n
 
 
-# DRAM bytes (read + write) per detect call of the scan stage (all its launches: the strip kernel, the prefix sums of
-# its listed lines and the warp kernels) from the ncu launch list summarised in profiles/, valid only for the kernel
+# DRAM bytes (read + write) per detect call of the scan stage (all its launches: the strip kernel and the warp
+# kernels) from the ncu launch list summarised in profiles/, valid only for the kernel
 # code it was taken on (sha256 prefix of csrc/occ_kernels.cu + csrc/occ_strip.cu without comments and blank space);
 # reported as null otherwise.
 PROFILED_STEPS = 20   # occ_detect calls with per-stage events after the timed region (stage_ms)
@@ -364,8 +364,8 @@ def run_ours(args):
                 "kernel": ("k_fused: the whole call in one launch (min/max of Eq. 3, plan, Eq. 1-6 on strips of rows, "
                            "columns and diagonals, lines of three or more macro-runs)"
                            if fused_call(views, tuning, 8, max(H, W)) else
-                           "scan stage: k_strip + k_plan_ovf + k_scan<256|1024|4096> (Eq. 1-6 on strips of rows, "
-                           "columns and diagonals)" if tuning.get("strip_px", 0) else
+                           "scan stage: k_strip + k_scan<256|1024|4096> (Eq. 1-6 on strips of rows, columns and "
+                           "diagonals)" if tuning.get("strip_px", 0) else
                            "scan stage: k_scan_lines + k_merge_lines + k_scan<256|1024|4096> (Eq. 4-6)"),
                 "launch_ms": round(scan_ms, 4),
                 "peak_source": "152 SMs x 128 lanes x 2.07 GHz", "ops_per_launch": ops}

@@ -281,6 +281,9 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     FusedLayout fl;
     const bool fused = minmax_only && sc.tuning.fused && fused_layout(sc, fr, nf, a, fl);
     FrameArg* fused_frames = fused ? fl.frames : nullptr;
+    // All-strip calls of at most kFramesPerChunk frames: the frame records go to k_minmax's parameters, which also
+    // writes the frame table.
+    const bool param_frames = minmax_only && !fused && nf <= kFramesPerChunk;
 
     // Frame records: lists and flags laid out frame after frame in the pools.
     FrameChunk chunk;
@@ -323,6 +326,11 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
         if (px > a.max_px) a.max_px = px;
         if (fused_frames) {
             fused_frames[f] = F;
+        } else if (param_frames) {
+            if (f == nf - 1) {
+                chunk.first = 0;
+                chunk.count = nf;
+            }
         } else if (f % kFramesPerChunk == kFramesPerChunk - 1 || f == nf - 1) {
             chunk.first = f - f % kFramesPerChunk;
             chunk.count = f % kFramesPerChunk + 1;
@@ -364,14 +372,16 @@ int run_frames(const Scratch& sc, const FrameIn* fr, int nf, Args& a, cudaStream
     }
     if (!mark(0)) return OCC_ERR_CUDA;
     if (minmax_only) {
-        if (launch_minmax(a, st) != cudaSuccess) return OCC_ERR_CUDA;
-    } else if ((lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess) {
+        // min/max and the plan in one launch (and the frame table, for a call of one chunk).
+        if (launch_minmax(a, param_frames ? &chunk : nullptr, st) != cudaSuccess) return OCC_ERR_CUDA;
+    } else if ((lines && launch_tables(a, st) != cudaSuccess) || launch_edges(a, st) != cudaSuccess ||
+               launch_plan(a, st) != cudaSuccess) {
         return OCC_ERR_CUDA;
     }
-    if (launch_plan(a, st) != cudaSuccess || !mark(1)) return OCC_ERR_CUDA;
+    if (!mark(1)) return OCC_ERR_CUDA;
     // The strip views: O and M written once per strip; the lines of three or more macro-runs are listed for the warp
-    // kernels below, which add their counts to O and M.
-    if (n_strip && (launch_strip(a, st) != cudaSuccess || launch_plan_ovf(a, st) != cudaSuccess)) return OCC_ERR_CUDA;
+    // kernels below, which add their counts to O and M (the last strip block writes their prefix sums).
+    if (n_strip && launch_strip(a, st) != cudaSuccess) return OCC_ERR_CUDA;
     const int lgrid = sc.sms * sc.tuning.line_blocks_per_sm;
     if (lines && launch_scan_lines(a, lgrid, wide, st) != cudaSuccess) return OCC_ERR_CUDA;
     // k_scan_lines has flagged every line the warp kernels take, and the merge kernel and the warp kernels only add

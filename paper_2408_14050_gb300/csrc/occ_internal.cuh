@@ -154,7 +154,8 @@ enum : int {
     CTR_POOL = 16,           // fused: entries of the published-line pool reserved
     CTR_CLAIM = 17,          // fused: entries of the pool taken by the workers
     CTR_EXIT = 18,           // fused: blocks that have ended
-    CTR_WORDS = 19,
+    CTR_MINMAX = 19,         // k_minmax: blocks done (the last one writes the plan)
+    CTR_WORDS = 20,
     CTR_EPOCH = 32,          // fused: launches so far (kept across calls): the tag of this launch's pool entries
 };
 constexpr size_t kStatusBytes = 256;   // bytes of the status region in every scratch layout
@@ -234,8 +235,10 @@ struct FrameChunk {
 cudaError_t launch_frames(const FrameChunk& c, cudaStream_t st);
 cudaError_t launch_tables(const Args& a, cudaStream_t st);
 cudaError_t launch_edges(const Args& a, cudaStream_t st);
-// k_edges' min/max and non-finite check alone: for calls with no candidate-list view and no E, A or tile hit outputs.
-cudaError_t launch_minmax(const Args& a, cudaStream_t st);
+// k_edges' min/max and non-finite check alone, then the plan (k_plan's work, by the last block): for calls with no
+// candidate-list view and no E, A or tile hit outputs.  c: the call's frame records (at most kFramesPerChunk), which
+// the kernel also writes to the frame table in place of k_frames; null when k_frames has written them.
+cudaError_t launch_minmax(const Args& a, const FrameChunk* c, cudaStream_t st);
 cudaError_t launch_plan(const Args& a, cudaStream_t st);
 // The line-per-thread scan over every view; wide = true when some frame's offsets need 64 bits.
 cudaError_t launch_scan_lines(const Args& a, int grid, bool wide, cudaStream_t st);
@@ -243,10 +246,9 @@ cudaError_t launch_merge_lines(const Args& a, int grid, bool wide, cudaStream_t 
 // cls = kNumClasses launches the class-0 kernel with 4-warp blocks.
 cudaError_t launch_scan(const Args& a, int cls, int grid, cudaStream_t st);
 cudaError_t launch_mask(const Args& a, cudaStream_t st);
-// Strip kernel (occ_strip.cu): the views with a strip family, every strip of the call; then the prefix sums of the
-// lines it listed for the warp kernels.
+// Strip kernel (occ_strip.cu): the views with a strip family, every strip of the call; its last block writes the prefix
+// sums of the lines the strips listed for the warp kernels.
 cudaError_t launch_strip(const Args& a, cudaStream_t st);
-cudaError_t launch_plan_ovf(const Args& a, cudaStream_t st);
 size_t strip_smem(int strip_px);
 cudaError_t configure_strip();
 // The fused launch of an all-strip call (a.fz filled in, the status region and frame headers cleared), on `grid`

@@ -23,6 +23,7 @@
 // round-to-nearest binary32 intrinsic (__fmul_rn, __fadd_rn, __fsub_rn, __fsqrt_rn) and the file is compiled with
 // --fmad=false, so the results are bit-identical to a plain one-operation-at-a-time binary32 evaluation.
 #include <cstdint>
+#include <cstring>
 
 #include "occ_internal.cuh"
 #include "occ_common.cuh"
@@ -313,17 +314,125 @@ __global__ void __launch_bounds__(kEdgeThreads) k_edges(const __grid_constant__ 
     }
 }
 
+constexpr int kMinMaxThreads = 256;   // k_minmax (below, after k_plan, whose work its last block does)
+
+
 // ------------------------------------------------------------------------------------------------------------------
-// k_minmax: what k_edges does when no view takes the candidate lists and neither E, A nor tile hit flags are asked
-// for -- the min/max of D (Eq. 3) and the non-finite check, one read of D, four pixels per thread and step.
+// k_frames: copies a chunk of frame records from the launch parameters into the device frame table.
 
-constexpr int kMinMaxThreads = 256;
+__global__ void k_frames(const __grid_constant__ FrameChunk c)
+{
+    for (int i = threadIdx.x; i < c.count; i += blockDim.x) c.dst[c.first + i] = c.f[i];
+}
 
-__global__ void __launch_bounds__(kMinMaxThreads) k_minmax(const __grid_constant__ Args a)
+// ------------------------------------------------------------------------------------------------------------------
+// k_plan: per (frame, view) the scan length (Eq. 3 on D_r unless L is fixed), the size class of the scan lines and
+// the candidate count; then the prefix sums that number the scan work items of all (frame, view)s and of each size
+// class.  One block.
+
+constexpr int kPlanThreads = 1024;
+
+// The plan (see k_plan) by one block of T threads; frames: the call's frame records.  The frame headers are read
+// through L2 (they may have been written by other blocks of the same launch, ahead of a releasing count).
+template <int T>
+__device__ __forceinline__ void plan_block(const Args& a, const FrameArg* frames)
+{
+    __shared__ uint32_t s_carry[1 + kNumClasses];
+    __shared__ uint32_t s_warp[T / 32][1 + kNumClasses];
+    const int n = a.nf * a.nv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 1 + kNumClasses) s_carry[threadIdx.x] = 0;
+    uint32_t st_all = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += T) {
+        const int i = base + threadIdx.x;
+        uint32_t cnt[1 + kNumClasses] = {0, 0, 0, 0};
+        if (i < n) {
+            const int f = i / a.nv, v = i - f * a.nv;
+            const FrameArg& F = frames[f];
+            const uint32_t st = __ldcg(&F.hdr[HDR_STATUS]);
+            PlanEntry pe{-1, 0, 0u, 0u};
+            if (!(st & ST_NONFINITE)) {
+                const int L = scan_length(a, __ldcg(&F.hdr[HDR_MAX]), __ldcg(&F.hdr[HDR_NEGMIN]), a.view[v].r);
+                if (L < 0) {
+                    atomicOr(&F.hdr[HDR_STATUS], ST_SCAN_TOO_LONG);
+                    st_all |= ST_SCAN_TOO_LONG;
+                } else {
+                    F.hdr[HDR_L + v] = (uint32_t)L;
+                    pe.h = (L + 1) / 2;
+                    const int nk = 2 * pe.h + 1;
+                    pe.cls = nk <= 256 ? 0 : (nk <= 1024 ? 1 : 2);   // kClassCap
+                    uint32_t c = __ldcg(&F.hdr[HDR_COUNT + v]);
+                    if ((int64_t)c > F.cap) c = (uint32_t)F.cap;
+                    pe.count = c;
+                    cnt[0] = c;
+                    cnt[1 + pe.cls] = c;
+                }
+            }
+            st_all |= st;
+            a.plan[i] = pe;
+        }
+        // Block-wide exclusive scans of the four count vectors.
+        uint32_t incl[1 + kNumClasses];
+#pragma unroll
+        for (int c = 0; c <= kNumClasses; c++) {
+            uint32_t x = cnt[c];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, x, off);
+                if (lane >= off) x += y;
+            }
+            incl[c] = x;
+            if (lane == 31) s_warp[warp][c] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 1 + kNumClasses) {
+            const int c = threadIdx.x;
+            uint32_t run = s_carry[c];
+            for (int w = 0; w < T / 32; w++) {
+                const uint32_t t = s_warp[w][c];
+                s_warp[w][c] = run;
+                run += t;
+            }
+            s_carry[c] = run;
+        }
+        __syncthreads();
+        if (i < n) {
+            const int stride = n + 1;
+            a.pref_all[i] = s_warp[warp][0] + incl[0] - cnt[0];
+#pragma unroll
+            for (int c = 0; c < kNumClasses; c++) a.pref_cls[c * stride + i] = s_warp[warp][1 + c] + incl[1 + c] - cnt[1 + c];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int stride = n + 1;
+        a.pref_all[n] = s_carry[0];
+        for (int c = 0; c < kNumClasses; c++) a.pref_cls[c * stride + n] = s_carry[1 + c];
+    }
+    st_all = __reduce_or_sync(kFull, st_all);
+    if (lane == 0 && st_all) atomicOr(a.status, st_all);
+}
+
+__global__ void __launch_bounds__(kPlanThreads) k_plan(const __grid_constant__ Args a)
+{
+    plan_block<kPlanThreads>(a, a.frames);
+}
+
+// k_minmax: the min/max of D (Eq. 3) and the non-finite check, one read of D, four pixels per thread and step, for
+// calls with no candidate-list view and no E, A or tile hit outputs; the block that finishes last (a releasing count
+// over the grid) writes the plan, as k_plan would.  kParam: the frame records come in the launch parameters (calls of
+// at most kFramesPerChunk frames), and block (0, 0) also writes them to the frame table, as k_frames would.
+template <bool kParam>
+__global__ void __launch_bounds__(kMinMaxThreads) k_minmax(const __grid_constant__ Args a,
+                                                           const __grid_constant__ FrameChunk c)
 {
     __shared__ float s_lo[kMinMaxThreads / 32], s_hi[kMinMaxThreads / 32];
-    __shared__ int s_bad;
-    const FrameArg& F = a.frames[blockIdx.y];
+    __shared__ int s_bad, s_last;
+    const FrameArg* frames = kParam ? c.f : a.frames;
+    if (kParam && blockIdx.x == 0 && blockIdx.y == 0)
+        for (int i = threadIdx.x; i < c.count; i += kMinMaxThreads) c.dst[c.first + i] = c.f[i];
+    const FrameArg& F = frames[blockIdx.y];
     const int W = F.W, H = F.H;
     const float* const Dp = F.D;
     const int64_t pitch = F.pitch;
@@ -359,101 +468,12 @@ __global__ void __launch_bounds__(kMinMaxThreads) k_minmax(const __grid_constant
             atomicMax(&F.hdr[HDR_NEGMIN], ~f2ord(blo));
         }
         if (s_bad) atomicOr(&F.hdr[HDR_STATUS], ST_NONFINITE);
+        __threadfence();
+        s_last = atomicAdd(a.status + CTR_MINMAX, 1u) + 1 == gridDim.x * gridDim.y;
+        if (s_last) __threadfence();
     }
-}
-
-// ------------------------------------------------------------------------------------------------------------------
-// k_frames: copies a chunk of frame records from the launch parameters into the device frame table.
-
-__global__ void k_frames(const __grid_constant__ FrameChunk c)
-{
-    for (int i = threadIdx.x; i < c.count; i += blockDim.x) c.dst[c.first + i] = c.f[i];
-}
-
-// ------------------------------------------------------------------------------------------------------------------
-// k_plan: per (frame, view) the scan length (Eq. 3 on D_r unless L is fixed), the size class of the scan lines and
-// the candidate count; then the prefix sums that number the scan work items of all (frame, view)s and of each size
-// class.  One block.
-
-constexpr int kPlanThreads = 1024;
-
-__global__ void __launch_bounds__(kPlanThreads) k_plan(const __grid_constant__ Args a)
-{
-    __shared__ uint32_t s_carry[1 + kNumClasses];
-    __shared__ uint32_t s_warp[kPlanThreads / 32][1 + kNumClasses];
-    const int n = a.nf * a.nv;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 1 + kNumClasses) s_carry[threadIdx.x] = 0;
-    uint32_t st_all = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += kPlanThreads) {
-        const int i = base + threadIdx.x;
-        uint32_t cnt[1 + kNumClasses] = {0, 0, 0, 0};
-        if (i < n) {
-            const int f = i / a.nv, v = i - f * a.nv;
-            const FrameArg& F = a.frames[f];
-            const uint32_t st = F.hdr[HDR_STATUS];
-            PlanEntry pe{-1, 0, 0u, 0u};
-            if (!(st & ST_NONFINITE)) {
-                const int L = scan_length(a, F.hdr[HDR_MAX], F.hdr[HDR_NEGMIN], a.view[v].r);
-                if (L < 0) {
-                    atomicOr(&F.hdr[HDR_STATUS], ST_SCAN_TOO_LONG);
-                    st_all |= ST_SCAN_TOO_LONG;
-                } else {
-                    F.hdr[HDR_L + v] = (uint32_t)L;
-                    pe.h = (L + 1) / 2;
-                    const int nk = 2 * pe.h + 1;
-                    pe.cls = nk <= 256 ? 0 : (nk <= 1024 ? 1 : 2);   // kClassCap
-                    uint32_t c = F.hdr[HDR_COUNT + v];
-                    if ((int64_t)c > F.cap) c = (uint32_t)F.cap;
-                    pe.count = c;
-                    cnt[0] = c;
-                    cnt[1 + pe.cls] = c;
-                }
-            }
-            st_all |= st;
-            a.plan[i] = pe;
-        }
-        // Block-wide exclusive scans of the four count vectors.
-        uint32_t incl[1 + kNumClasses];
-#pragma unroll
-        for (int c = 0; c <= kNumClasses; c++) {
-            uint32_t x = cnt[c];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, x, off);
-                if (lane >= off) x += y;
-            }
-            incl[c] = x;
-            if (lane == 31) s_warp[warp][c] = x;
-        }
-        __syncthreads();
-        if (threadIdx.x < 1 + kNumClasses) {
-            const int c = threadIdx.x;
-            uint32_t run = s_carry[c];
-            for (int w = 0; w < kPlanThreads / 32; w++) {
-                const uint32_t t = s_warp[w][c];
-                s_warp[w][c] = run;
-                run += t;
-            }
-            s_carry[c] = run;
-        }
-        __syncthreads();
-        if (i < n) {
-            const int stride = n + 1;
-            a.pref_all[i] = s_warp[warp][0] + incl[0] - cnt[0];
-#pragma unroll
-            for (int c = 0; c < kNumClasses; c++) a.pref_cls[c * stride + i] = s_warp[warp][1 + c] + incl[1 + c] - cnt[1 + c];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const int stride = n + 1;
-        a.pref_all[n] = s_carry[0];
-        for (int c = 0; c < kNumClasses; c++) a.pref_cls[c * stride + n] = s_carry[1 + c];
-    }
-    st_all = __reduce_or_sync(kFull, st_all);
-    if (lane == 0 && st_all) atomicOr(a.status, st_all);
+    if (s_last) plan_block<kMinMaxThreads>(a, frames);
 }
 
 // The (frame, view) index of a scan work item: the last i with pref[i] <= item (pref non-decreasing, pref[0] = 0,
@@ -1313,12 +1333,18 @@ cudaError_t launch_edges(const Args& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_minmax(const Args& a, cudaStream_t st)
+cudaError_t launch_minmax(const Args& a, const FrameChunk* c, cudaStream_t st)
 {
     int bx = (a.max_quads + kMinMaxThreads - 1) / kMinMaxThreads;
     if (bx > 1024) bx = 1024;
     if (bx < 1) bx = 1;
-    k_minmax<<<dim3(bx, a.nf), kMinMaxThreads, 0, st>>>(a);
+    if (c) {
+        k_minmax<true><<<dim3(bx, a.nf), kMinMaxThreads, 0, st>>>(a, *c);
+    } else {
+        FrameChunk none;
+        std::memset(&none, 0, sizeof(none));
+        k_minmax<false><<<dim3(bx, a.nf), kMinMaxThreads, 0, st>>>(a, none);
+    }
     return cudaGetLastError();
 }
 

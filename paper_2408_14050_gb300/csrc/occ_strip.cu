@@ -756,11 +756,6 @@ __device__ __forceinline__ void strip_run(const Args& a, const FrameArg* frames,
     }
 }
 
-template <bool kHits>
-__global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constant__ Args a)
-{
-    strip_run<kHits, false>(a, a.frames, blockIdx.x);
-}
 
 // The prefix sums over (frame, view), per size class, of the lines the strips listed (clamped to the list capacity),
 // for the warp kernels: one block of T threads, one (frame, view) per thread and iteration.
@@ -782,7 +777,7 @@ __device__ __forceinline__ void plan_ovf_block(const Args& a, const FrameArg* fr
             const FrameArg& F = frames[f];
             const PlanEntry pe = a.plan[i];
             if (a.view[v].fam >= 0 && pe.h >= 0) {
-                uint32_t c = F.hdr[HDR_OVF + v];
+                uint32_t c = __ldcg(&F.hdr[HDR_OVF + v]);
                 if ((int64_t)c > F.cap) c = (uint32_t)F.cap;
                 cnt[pe.cls] = c;
             }
@@ -820,12 +815,27 @@ __device__ __forceinline__ void plan_ovf_block(const Args& a, const FrameArg* fr
     if (threadIdx.x < kNumClasses) a.pref_ovf[threadIdx.x * stride + n] = s_carry[threadIdx.x];
 }
 
-// k_plan_ovf: plan_ovf_block after k_strip, for k_scan.
-constexpr int kPlanOvfThreads = 1024;
-
-__global__ void __launch_bounds__(kPlanOvfThreads) k_plan_ovf(const __grid_constant__ Args a)
+// plan_ovf_block for the last strip block, out of line (one block of a launch runs it).
+__device__ __noinline__ void strip_plan_ovf(const Args& a)
 {
-    plan_ovf_block<kPlanOvfThreads>(a, a.frames);
+    plan_ovf_block<kStripThreads>(a, a.frames);
+}
+
+// k_strip: one strip per block; the block that ends last (a releasing count over the grid) writes the prefix sums of
+// the lines the strips listed, for the warp kernels.
+template <bool kHits>
+__global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constant__ Args a)
+{
+    __shared__ int s_last;
+    strip_run<kHits, false>(a, a.frames, blockIdx.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.status + CTR_STRIPS, 1u) + 1 == gridDim.x;
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) strip_plan_ovf(a);
 }
 
 // ------------------------------------------------------------------------------------------------------------------
@@ -1216,10 +1226,5 @@ cudaError_t launch_strip(const Args& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_plan_ovf(const Args& a, cudaStream_t st)
-{
-    k_plan_ovf<<<1, kPlanOvfThreads, 0, st>>>(a);
-    return cudaGetLastError();
-}
 
 }  // namespace occ
