@@ -167,8 +167,8 @@ int strip_family(float c, float s)
     return -1;
 }
 
-// The fused launch of a call: its tickets, grid, and the completion records, published-line pool and per-block warp
-// buffers it keeps in the merge kernel's list pool (which an all-strip call does not use).
+// The fused launch of a call: its tickets, grid, and the published-line pool and per-block warp buffers it keeps in
+// the merge kernel's list pool (which an all-strip call does not use).
 struct FusedLayout {
     FusedPlan plan;
     int grid;

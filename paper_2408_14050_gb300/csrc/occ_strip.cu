@@ -843,12 +843,12 @@ __global__ void __launch_bounds__(kStripThreads, 5) k_strip(const __grid_constan
 // tile hits.  Blocks take tickets from one counter (CTR_TICKET), in this order:
 //   min/max  kFusedQuadsPerTicket quads of one frame's D each (as k_minmax); the block that finishes a frame's last
 //            one writes the frame's plan (Eq. 3: L and h per view) and releases it (HDR_READY);
-//   strips   strip_run after the frame's plan; its kept lines of three or more macro-runs are
-//            published (pool entries plus one completion record) once its O and M are written; the block that
+//   strips   strip_run after the frame's plan; its kept lines of three or more macro-runs are published in
+//            entries of a pool (the launch's tag written last) once its O and M are written; the block that
 //            finishes the last strip writes the prefix sums of the lines in the views' lists (CTR_OVF_READY);
-//   workers  one per block: the published lines, one warp each, taken line by line from the completion records in
-//            order (the sort of the warp kernels, counts added to O with global atomics, M set); then, once every
-//            strip is done, the listed lines of every size class.
+//   workers  one per block: the published lines, one warp each, claimed entry by entry in reservation order (the
+//            sort of the warp kernels, counts added to O with global atomics, M set); then, once every strip is done,
+//            the listed lines of every size class.
 // A ticket waits only for tickets handed out before it, and every such ticket is held by a block that is running and
 // waits only for earlier ones, so the launch needs no co-residency: the earliest unfinished ticket always progresses.
 // Every wait is bounded (FusedPlan::wait_ns, from %globaltimer, and a spin count); one that gives up sets ST_TIMEOUT
