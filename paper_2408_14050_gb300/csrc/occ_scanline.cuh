@@ -27,10 +27,13 @@ namespace {
 constexpr int kMaxRuns = 16;
 
 // A warp's shared memory for one line: V by sample, the sorted order as sample indices, and 16 bits of counts per
-// sorted position (W is not stored: W = fl(g - V) is recomputed from the sample's index wherever it is compared, the
-// same operation that defines it), 8 bytes per sample.
+// sorted position, 8 bytes per sample.  W is stored only for the 256-sample class, whose warps are limited by registers
+// rather than shared memory; otherwise W = fl(g - V) is recomputed from the sample's index wherever it is compared,
+// the same operation that defines it.
 template <int CAP>
 struct ScanSmem {
+    static constexpr bool kKeepW = CAP <= 256;   // lines of the 256-sample class also keep W by k (1 KB per warp)
+    float uw[kKeepW ? CAP : 1];   // W by k (kKeepW)
     float uv[CAP];        // V by k
     uint16_t sidx[CAP];   // sample index (k - k0) of each sorted position (unused when the line is one run)
     uint32_t cnt[CAP / 2];// per sorted position q, 16 bits at (q & 1) * 16 of word q / 2: hits of the sample itself
@@ -113,7 +116,11 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
             const int base = i * 32;
             if (base >= nk) break;
             const int k = base + lane;
-            if (oks[i]) S.uv[k] = one ? dvs[i] : __fmul_rn(r, dvs[i]);
+            if (oks[i]) {
+                const float V = one ? dvs[i] : __fmul_rn(r, dvs[i]);
+                S.uv[k] = V;
+                if constexpr (ScanSmem<CAP>::kKeepW) S.uw[k] = __fsub_rn((float)(k - h), V);
+            }
             record(base, oks[i]);
         }
     } else {
@@ -140,8 +147,12 @@ __device__ __forceinline__ int scan_line(ScanSmem<CAP>& S, int lane, const float
     }
     __syncwarp();
     const float* uv = S.uv + k0;
-    // W of sample i (k = k0 + i): fl(g - V), g = k - h.
-    auto Wat = [&](int i) { return __fsub_rn((float)(k0 + i - h), uv[i]); };
+    const float* uw = S.uw + (ScanSmem<CAP>::kKeepW ? k0 : 0);
+    // W of sample i (k = k0 + i): fl(g - V), g = k - h; kept by k for the 256-sample class, else recomputed.
+    auto Wat = [&](int i) {
+        if constexpr (ScanSmem<CAP>::kKeepW) return uw[i];
+        else return __fsub_rn((float)(k0 + i - h), uv[i]);
+    };
 
     // Runs: a new run starts after every descent W[i+1] < W[i].
     int R = 1;
